@@ -1,0 +1,180 @@
+"""Seeded synthetic inputs for the mEVP momentum subcycle.
+
+This module only builds inputs: mesh vertices, ice height/concentration
+fields, the nodal wind stress of a moving cyclone, and the parameter set.  It
+holds none of the method's arithmetic (no strain, stress, divergence, mass or
+velocity update), so both the CUDA path and the CPU oracle can take their
+inputs from it.
+
+The paper validates on the moving-cyclone benchmark over a 512 km square
+(Sec. 4); its definition is not reproduced here.  These are our own seeded
+constructions with the same domain, resolution range and magnitudes.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Parameter set (P*, C, e, Delta_min from the paper's stress update, Sec. 3 /
+# App. A; alpha = beta = 300, dt = 120 s = 1 h / 30 advection steps, Sec. 4;
+# the remaining constants are typical literature values).
+DEFAULT_PARAMS = dict(
+    Pstar=27500.0, C=20.0, e=2.0, DeltaMin=2e-9, alpha=300.0, beta=300.0, dt=120.0,
+    rho_ice=900.0, rho_water=1026.0, Cw=5.5e-3, coriolis_f=1.46e-4)
+RHO_AIR = 1.3
+C_AIR = 1.2e-3
+DOMAIN_M = 512e3
+
+# Workloads: mesh size, DG stress dofs, subcycles per outer step, ice recipe.
+CONFIGS = {
+    # 32x32 quads, DG1 stress, iid H ~ U[0.3,2], A ~ U[0.8,1], 100 subcycles
+    "mesh32_dg1": dict(nx=32, ny=32, n_s=3, n_a=1, n_sub=100, ice="iid", seeds=(1,),
+                       wind_seed=11),
+    # 256x256 quads, DG2 stress, Gaussian-random H/A with 5 km correlation, 500 subcycles
+    "mesh256_dg2": dict(nx=256, ny=256, n_s=6, n_a=1, n_sub=500, ice="grf", seeds=(2, 3),
+                        wind_seed=12),
+    # 1024x1024 quads, DG2 stress, same recipe, 500 subcycles
+    "mesh1024_dg2": dict(nx=1024, ny=1024, n_s=6, n_a=1, n_sub=500, ice="grf", seeds=(4, 5),
+                         wind_seed=13),
+    # 256x256 quads, DG1 stress, 100 subcycles
+    "mesh256_dg1": dict(nx=256, ny=256, n_s=3, n_a=1, n_sub=100, ice="grf", seeds=(7, 8),
+                        wind_seed=14),
+}
+
+
+def sizes(nx: int, ny: int):
+    """(elements, CG2 nodes, vertices)."""
+    return nx * ny, (2 * nx + 1) * (2 * ny + 1), (nx + 1) * (ny + 1)
+
+
+def uniform_vertices(nx: int, ny: int, Lx: float = DOMAIN_M, Ly: float = DOMAIN_M):
+    """Vertices (N_v, 2), vertex id = jy*(nx+1) + jx, of a uniform quad mesh."""
+    xs = np.linspace(0.0, Lx, nx + 1)
+    ys = np.linspace(0.0, Ly, ny + 1)
+    X, Y = np.meshgrid(xs, ys)
+    return np.stack([X.ravel(), Y.ravel()], axis=1).copy()
+
+
+def node_coords_uniform(nx: int, ny: int, Lx: float = DOMAIN_M, Ly: float = DOMAIN_M):
+    """Coordinates (2, N_n) of the CG2 nodes of a uniform mesh (node = iy*(2nx+1)+ix)."""
+    xs = np.linspace(0.0, Lx, 2 * nx + 1)
+    ys = np.linspace(0.0, Ly, 2 * ny + 1)
+    X, Y = np.meshgrid(xs, ys)
+    return np.stack([X.ravel(), Y.ravel()])
+
+
+def ice_iid(nx: int, ny: int, seed: int):
+    """DG0 H ~ U[0.3, 2] m and A ~ U[0.8, 1], iid per element; shapes (1, N_e)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ne = nx * ny
+    H = rng.uniform(0.3, 2.0, ne)
+    A = rng.uniform(0.8, 1.0, ne)
+    return H[None, :].copy(), A[None, :].copy()
+
+
+def gaussian_random_field(nx: int, ny: int, h_m: float, corr_m: float, seed: int):
+    """Unit-variance field on the element grid: white noise filtered in Fourier
+    space by a Gaussian kernel of standard deviation corr_m (periodic)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = rng.standard_normal((ny, nx))
+    kx = np.fft.fftfreq(nx, d=h_m) * 2.0 * math.pi
+    ky = np.fft.fftfreq(ny, d=h_m) * 2.0 * math.pi
+    KX, KY = np.meshgrid(kx, ky)
+    filt = np.exp(-0.5 * (KX ** 2 + KY ** 2) * corr_m ** 2)
+    g = np.fft.ifft2(np.fft.fft2(w) * filt).real
+    s = g.std()
+    return (g - g.mean()) / (s if s > 0 else 1.0)
+
+
+def ice_grf(nx: int, ny: int, seeds, L: float = DOMAIN_M, corr_m: float = 5e3):
+    """DG0 H = clip(1.15 + 0.3 g1, 0.3, 2), A = clip(0.9 + 0.05 g2, 0.8, 1)."""
+    h = L / nx
+    g1 = gaussian_random_field(nx, ny, h, corr_m, seeds[0]).ravel()
+    g2 = gaussian_random_field(nx, ny, h, corr_m, seeds[1]).ravel()
+    H = np.clip(1.15 + 0.3 * g1, 0.3, 2.0)
+    A = np.clip(0.9 + 0.05 * g2, 0.8, 1.0)
+    return H[None, :].copy(), A[None, :].copy()
+
+
+def cyclone_params(seed: int, L: float = DOMAIN_M):
+    """Moving cyclone: centre uniform in the middle half of the domain, heading
+    uniform, translation speed U[5,10] m/s, radius U[60,120] km."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c0 = rng.uniform(0.25 * L, 0.75 * L, 2)
+    heading = rng.uniform(0.0, 2.0 * math.pi)
+    speed = rng.uniform(5.0, 10.0)
+    R = rng.uniform(60e3, 120e3)
+    return dict(c0=c0, u=speed * np.array([math.cos(heading), math.sin(heading)]), R=R,
+                umax=15.0)
+
+
+def cyclone_wind_stress(node_xy, cyc, t: float = 0.0):
+    """Nodal wind stress (2, N_n) = rho_air C_air |u_a| u_a of the cyclone at time t.
+
+    Tangential, counter-clockwise wind |u_a| = umax (r/R) exp((1 - r^2/R^2)/2),
+    maximal (umax) at r = R."""
+    c = cyc["c0"] + cyc["u"] * t
+    dx = node_xy[0] - c[0]
+    dy = node_xy[1] - c[1]
+    r = np.sqrt(dx * dx + dy * dy)
+    R = cyc["R"]
+    speed = cyc["umax"] * (r / R) * np.exp(0.5 * (1.0 - (r / R) ** 2))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ux = np.where(r > 0, -dy / r, 0.0) * speed
+        uy = np.where(r > 0, dx / r, 0.0) * speed
+    mag = np.sqrt(ux * ux + uy * uy)
+    return np.stack([RHO_AIR * C_AIR * mag * ux, RHO_AIR * C_AIR * mag * uy])
+
+
+def smooth_velocity(nx: int, ny: int, seed: int, amp: float = 0.1, L: float = DOMAIN_M):
+    """A smooth seeded velocity field (2, N_n), zero on the boundary, for tests
+    that start from a moving state: sum of a few random sine modes."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xy = node_coords_uniform(nx, ny, L, L)
+    X, Y = xy[0] / L, xy[1] / L
+    out = np.zeros_like(xy)
+    for c in range(2):
+        for _ in range(4):
+            kx, ky = rng.integers(1, 5, 2)
+            out[c] += rng.uniform(-1, 1) * np.sin(math.pi * kx * X) * np.sin(math.pi * ky * Y)
+    out = amp * out / max(np.abs(out).max(), 1e-30)
+    nw, nh = 2 * nx + 1, 2 * ny + 1
+    grid = out.reshape(2, nh, nw)
+    grid[:, 0, :] = 0.0
+    grid[:, -1, :] = 0.0
+    grid[:, :, 0] = 0.0
+    grid[:, :, -1] = 0.0
+    return out
+
+
+def make_case(name: str, L: float = DOMAIN_M, params: dict | None = None):
+    """Inputs of a named workload: dict with nx, ny, n_s, n_a, n_sub, xy, H, A,
+    tau, vel0 (zeros), S0 (zeros), params."""
+    cfg = dict(CONFIGS[name])
+    nx, ny = cfg["nx"], cfg["ny"]
+    ne, nn, nv = sizes(nx, ny)
+    if cfg["ice"] == "iid":
+        H, A = ice_iid(nx, ny, cfg["seeds"][0])
+    else:
+        H, A = ice_grf(nx, ny, cfg["seeds"], L)
+    tau = cyclone_wind_stress(node_coords_uniform(nx, ny, L, L), cyclone_params(cfg["wind_seed"], L))
+    return dict(name=name, nx=nx, ny=ny, n_s=cfg["n_s"], n_a=cfg["n_a"], n_sub=cfg["n_sub"],
+                L=L, xy=uniform_vertices(nx, ny, L, L), H=H, A=A, tau=tau,
+                vel0=np.zeros((2, nn)), S0=np.zeros((3, cfg["n_s"], ne)),
+                params=dict(DEFAULT_PARAMS if params is None else params))
+
+
+def small_case(nx: int, ny: int, n_s: int, seed: int, L: float = DOMAIN_M, moving: bool = True,
+               params: dict | None = None):
+    """A small seeded case of any size (iid ice, cyclone wind, optional smooth
+    initial velocity and random initial stress) for parity tests."""
+    ne, nn, nv = sizes(nx, ny)
+    H, A = ice_iid(nx, ny, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    tau = cyclone_wind_stress(node_coords_uniform(nx, ny, L, L), cyclone_params(seed + 2000, L))
+    vel0 = smooth_velocity(nx, ny, seed + 3000, L=L) if moving else np.zeros((2, nn))
+    S0 = rng.uniform(-5e3, 5e3, (3, n_s, ne)) if moving else np.zeros((3, n_s, ne))
+    return dict(name=f"small{nx}x{ny}_dg{n_s}", nx=nx, ny=ny, n_s=n_s, n_a=1, n_sub=10, L=L,
+                xy=uniform_vertices(nx, ny, L, L), H=H, A=A, tau=tau, vel0=vel0, S0=S0,
+                params=dict(DEFAULT_PARAMS if params is None else params))

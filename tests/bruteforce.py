@@ -1,0 +1,221 @@
+"""Independent brute-force restatement of the mEVP subcycle for tiny meshes.
+
+Written from the mathematics, not from the oracle: numpy's Legendre module
+for the quadrature (a 10x10 rule for every linear stage, so its results only
+agree with the oracle if the oracle's NGP rule is exact as claimed) and for a
+differently normalised DG basis (shifted Legendre P_i(2xi-1) P_j(2eta-1),
+i + j <= degree), power-series Lagrange polynomials for Q2, global
+vectorised assembly, complex arithmetic for the velocity update.  DG fields
+are compared through their values at sample points, which do not depend on
+the basis.
+
+The stress update evaluates the nonlinear rheology at the method's own
+NGP x NGP Gauss points (the paper's quadrature-based update), so that stage
+uses numpy's leggauss(NGP).
+"""
+import numpy as np
+from numpy.polynomial import legendre as Lg
+from numpy.polynomial import polynomial as Pl
+
+DEG = {3: 1, 6: 2}
+NGP = {3: 2, 6: 3}
+
+
+def gauss01(n):
+    x, w = Lg.leggauss(n)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def _lagrange():
+    nodes = [0.0, 0.5, 1.0]
+    out = []
+    for a in range(3):
+        c = Pl.polyfromroots([nodes[b] for b in range(3) if b != a])
+        out.append(c / Pl.polyval(nodes[a], c))
+    return out
+
+
+LAG = _lagrange()
+DLAG = [Pl.polyder(c) for c in LAG]
+
+
+def q2(xi, eta):
+    """Values and reference gradients, shape (..., 9); j = a + 3b."""
+    lx = [Pl.polyval(xi, c) for c in LAG]
+    ly = [Pl.polyval(eta, c) for c in LAG]
+    dx = [Pl.polyval(xi, c) for c in DLAG]
+    dy = [Pl.polyval(eta, c) for c in DLAG]
+    phi = np.stack([lx[a] * ly[b] for b in range(3) for a in range(3)], -1)
+    gx = np.stack([dx[a] * ly[b] for b in range(3) for a in range(3)], -1)
+    gy = np.stack([lx[a] * dy[b] for b in range(3) for a in range(3)], -1)
+    return phi, gx, gy
+
+
+def dg_bf(n_s, xi, eta):
+    """Brute-force DG basis: shifted Legendre products of total degree <= k."""
+    k = {1: 0, 3: 1, 6: 2}[n_s]
+    cols = []
+    for i in range(k + 1):
+        for j in range(k + 1 - i):
+            ei = np.zeros(i + 1); ei[i] = 1.0
+            ej = np.zeros(j + 1); ej[j] = 1.0
+            cols.append(Lg.legval(2 * xi - 1, ei) * Lg.legval(2 * eta - 1, ej))
+    return np.stack(cols, -1)
+
+
+def dg_documented(n_s, xi, eta):
+    """The library's documented coefficient convention (xh = xi-1/2, eh = eta-1/2):
+    {1, xh, eh, xh^2-1/12, xh eh, eh^2-1/12}[:n_s]."""
+    xh, eh = xi - 0.5, eta - 0.5
+    allb = [np.ones_like(xh), xh, eh, xh * xh - 1 / 12, xh * eh, eh * eh - 1 / 12]
+    return np.stack(allb[:n_s], -1)
+
+
+class Mesh:
+    def __init__(self, nx, ny, xy, n_s):
+        self.nx, self.ny, self.n_s = nx, ny, n_s
+        self.ne = nx * ny
+        self.nw, self.nh = 2 * nx + 1, 2 * ny + 1
+        self.nn = self.nw * self.nh
+        xy = np.asarray(xy, dtype=np.float64).reshape(ny + 1, nx + 1, 2)
+        kx, ky = np.meshgrid(np.arange(nx), np.arange(ny))
+        kx, ky = kx.ravel(), ky.ravel()
+        self.X00, self.X10 = xy[ky, kx], xy[ky, kx + 1]
+        self.X01, self.X11 = xy[ky + 1, kx], xy[ky + 1, kx + 1]
+        self.nodes = np.stack([(2 * ky + b) * self.nw + 2 * kx + a
+                               for b in range(3) for a in range(3)], -1)  # (ne, 9)
+        self.rule_exact = self._rule(*self._tensor(gauss01(10)))
+        self.rule_method = self._rule(*self._tensor(gauss01(NGP[n_s])))
+        sp = np.array([0.1, 0.35, 0.6, 0.9])
+        XI, ET = np.meshgrid(sp, sp)
+        self.sample = (XI.ravel(), ET.ravel())
+
+    @staticmethod
+    def _tensor(rule):
+        x, w = rule
+        XI, ET = np.meshgrid(x, x)
+        W = np.outer(w, w)
+        return XI.ravel(), ET.ravel(), W.ravel()
+
+    def _map(self, xi, eta):
+        """Jacobian entries (ne, nq) of the bilinear map."""
+        X00, X10, X01, X11 = (v[:, None, :] for v in (self.X00, self.X10, self.X01, self.X11))
+        e = eta[None, :, None]
+        x = xi[None, :, None]
+        dxi = (X10 - X00) * (1 - e) + (X11 - X01) * e
+        deta = (X01 - X00) * (1 - x) + (X11 - X10) * x
+        return dxi[..., 0], deta[..., 0], dxi[..., 1], deta[..., 1]
+
+    def _rule(self, xi, eta, w):
+        J00, J01, J10, J11 = self._map(xi, eta)
+        det = J00 * J11 - J01 * J10
+        phi, gxi, geta = q2(xi, eta)
+        # physical gradients (ne, nq, 9)
+        dx = (J11[..., None] * gxi[None] - J10[..., None] * geta[None]) / det[..., None]
+        dy = (-J01[..., None] * gxi[None] + J00[..., None] * geta[None]) / det[..., None]
+        psi = dg_bf(self.n_s, xi, eta)  # (nq, nb)
+        wdet = w[None] * det  # (ne, nq)
+        M = np.einsum("kq,qs,qt->kst", wdet, psi, psi)
+        return dict(xi=xi, eta=eta, wdet=wdet, phi=phi, dx=dx, dy=dy, psi=psi,
+                    Minv=np.linalg.inv(M))
+
+    # --- DG conversions ---------------------------------------------------
+    def values(self, coef_bf):
+        """(3, ne, nb) brute-force coefficients -> values (3, ne, nsample)."""
+        psi = dg_bf(self.n_s, *self.sample)
+        return np.einsum("cks,qs->ckq", coef_bf, psi)
+
+    def values_documented(self, S):
+        """(3, n_s, ne) coefficients in the documented basis -> values (3, ne, nsample)."""
+        psi = dg_documented(self.n_s, *self.sample)
+        return np.einsum("csk,qs->ckq", S, psi)
+
+    def from_documented(self, S):
+        psi_bf = dg_bf(self.n_s, *self.sample)
+        vals = self.values_documented(S)
+        sol = np.linalg.lstsq(psi_bf, vals.reshape(-1, vals.shape[-1]).T, rcond=None)[0]
+        return sol.T.reshape(3, self.ne, -1)
+
+    # --- stages ------------------------------------------------------------
+    def strain(self, vel):
+        r = self.rule_exact
+        u = vel[0][self.nodes]  # (ne, 9)
+        v = vel[1][self.nodes]
+        ux = np.einsum("kqj,kj->kq", r["dx"], u)
+        uy = np.einsum("kqj,kj->kq", r["dy"], u)
+        vx = np.einsum("kqj,kj->kq", r["dx"], v)
+        vy = np.einsum("kqj,kj->kq", r["dy"], v)
+        eps = np.stack([ux, 0.5 * (uy + vx), vy])  # (3, ne, nq)
+        rhs = np.einsum("kq,qs,ckq->cks", r["wdet"], r["psi"], eps)
+        return np.einsum("kst,ckt->cks", r["Minv"], rhs)
+
+    def stress(self, Ebf, H, A, Sbf, p):
+        r = self.rule_method
+        e = np.einsum("cks,qs->ckq", Ebf, r["psi"])  # (3, ne, nq)
+        e11, e12, e22 = e
+        h = np.maximum(0.0, H[0])[:, None]
+        a = np.clip(A[0], 0.0, 1.0)[:, None]
+        P = p["Pstar"] * h * np.exp(-p["C"] * (1.0 - a))
+        # Hibler's viscous-plastic law: zeta = P/(2 Delta), eta = zeta/e^2,
+        # sigma = 2 eta eps + (zeta - eta) tr(eps) I - P/2 I
+        ecc = p["e"]
+        delta = np.sqrt(p["DeltaMin"] ** 2 + (e11 ** 2 + e22 ** 2) * (1 + ecc ** -2)
+                        + 4 * ecc ** -2 * e12 ** 2 + 2 * (1 - ecc ** -2) * e11 * e22)
+        zeta = P / (2 * delta)
+        eta = zeta / ecc ** 2
+        tr = e11 + e22
+        s = np.stack([2 * eta * e11 + (zeta - eta) * tr - P / 2, 2 * eta * e12,
+                      2 * eta * e22 + (zeta - eta) * tr - P / 2])
+        rhs = np.einsum("kq,qs,ckq->cks", r["wdet"], r["psi"], s)
+        proj = np.einsum("kst,ckt->cks", r["Minv"], rhs)
+        return (1 - 1 / p["alpha"]) * Sbf + proj / p["alpha"]
+
+    def divergence(self, Sbf):
+        r = self.rule_exact
+        sig = np.einsum("cks,qs->ckq", Sbf, r["psi"])
+        fx = -np.einsum("kq,kq,kqj->kj", r["wdet"], sig[0], r["dx"]) \
+             - np.einsum("kq,kq,kqj->kj", r["wdet"], sig[1], r["dy"])
+        fy = -np.einsum("kq,kq,kqj->kj", r["wdet"], sig[1], r["dx"]) \
+             - np.einsum("kq,kq,kqj->kj", r["wdet"], sig[2], r["dy"])
+        F = np.zeros((2, self.nn))
+        np.add.at(F[0], self.nodes, fx)
+        np.add.at(F[1], self.nodes, fy)
+        return F
+
+    def lumped(self, H, rho):
+        r = self.rule_exact
+        h = np.maximum(0.0, H[0])
+        m = np.zeros(self.nn)
+        l = np.zeros(self.nn)
+        np.add.at(l, self.nodes, np.einsum("kq,qj->kj", r["wdet"], r["phi"]))
+        np.add.at(m, self.nodes, rho * h[:, None] * np.einsum("kq,qj->kj", r["wdet"], r["phi"]))
+        return m, l
+
+    def boundary(self):
+        ix = np.arange(self.nn) % self.nw
+        iy = np.arange(self.nn) // self.nw
+        return (ix == 0) | (iy == 0) | (ix == self.nw - 1) | (iy == self.nh - 1)
+
+    def velocity(self, F, vprev, vn, tau, m, l, p):
+        """Complex form: (m(1+beta)/dt + c + i m f) v = (m/dt)(beta v^{p-1} + v^n) + F + l tau."""
+        z = vprev[0] + 1j * vprev[1]
+        zn = vn[0] + 1j * vn[1]
+        c = l * p["Cw"] * p["rho_water"] * np.abs(z)
+        lhs = m * (1 + p["beta"]) / p["dt"] + c + 1j * m * p["coriolis_f"]
+        rhs = m / p["dt"] * (p["beta"] * z + zn) + (F[0] + 1j * F[1]) + l * (tau[0] + 1j * tau[1])
+        out = np.where(lhs != 0, rhs / np.where(lhs != 0, lhs, 1), 0)
+        out[self.boundary()] = 0
+        return np.stack([out.real, out.imag])
+
+    def subcycles(self, vel0, S0_documented, H, A, tau, p, n_sub, vn=None):
+        vel = np.array(vel0, dtype=np.float64)
+        vn = vel.copy() if vn is None else np.asarray(vn)
+        S = self.from_documented(S0_documented)
+        m, l = self.lumped(H, p["rho_ice"])
+        E = None
+        for _ in range(n_sub):
+            E = self.strain(vel)
+            S = self.stress(E, H, A, S, p)
+            F = self.divergence(S)
+            vel = self.velocity(F, vel, vn, tau, m, l, p)
+        return vel, S, E

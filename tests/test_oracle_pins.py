@@ -1,0 +1,450 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the
+mathematics (no GPU).  Each test names what pins it: printed constants,
+closed forms, invariants, textbook quadrature, or the independent brute-force
+restatement in ``bruteforce.py``."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_00466_gb300 import workloads as W
+from tests import bruteforce as BF
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+P0 = dict(W.DEFAULT_PARAMS)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    n = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (n if n > 0 else 1.0)
+
+
+def perturbed_vertices(nx, ny, L, seed, amp=0.2):
+    """Non-affine quads: interior vertices moved by up to amp*h."""
+    xy = W.uniform_vertices(nx, ny, L, L).reshape(ny + 1, nx + 1, 2)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = L / nx
+    xy[1:-1, 1:-1] += rng.uniform(-amp * h, amp * h, xy[1:-1, 1:-1].shape)
+    return xy.reshape(-1, 2).copy()
+
+
+# --------------------------------------------------------------------------
+# Quadrature (App. A: NGP = 2 for 3 stress dofs, 3 for 6 or 8)
+# --------------------------------------------------------------------------
+def test_ngp_rule_matches_paper():
+    for k, v in GOLD["ngp"].items():
+        if k.startswith("_"):
+            continue
+        assert oracle.ngp(int(k)) == v
+    for bad in (0, 1, 2, 4, 5, 7, 9):
+        assert oracle.ngp(bad) == -1
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_gauss_textbook(n):
+    x, w = oracle.gauss(n)
+    xr, wr = BF.gauss01(n)  # numpy's Golub-Welsch based rule
+    assert np.allclose(x, xr, rtol=0, atol=1e-15) and np.allclose(w, wr, rtol=0, atol=1e-15)
+    closed = {2: ([0.5 - 0.5 / math.sqrt(3), 0.5 + 0.5 / math.sqrt(3)], [0.5, 0.5]),
+              3: ([0.5 - 0.5 * math.sqrt(0.6), 0.5, 0.5 + 0.5 * math.sqrt(0.6)],
+                  [5 / 18, 8 / 18, 5 / 18])}
+    if n in closed:
+        assert np.allclose(x, closed[n][0], atol=1e-15) and np.allclose(w, closed[n][1], atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_gauss_exact_to_degree_2n_minus_1(n):
+    x, w = oracle.gauss(n)
+    for a in range(2 * n):
+        for b in range(2 * n):
+            q = np.sum(np.outer(w, w) * np.outer(x ** b, x ** a))
+            assert abs(q - 1.0 / ((a + 1) * (b + 1))) < 1e-15
+    # and not beyond: degree 2n is integrated inexactly
+    assert abs(np.sum(w * x ** (2 * n)) - 1.0 / (2 * n + 1)) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Bases
+# --------------------------------------------------------------------------
+def test_dg_basis_orthogonal_closed_form_mass():
+    x, w = BF.gauss01(6)
+    XI, ET = np.meshgrid(x, x)
+    Wt = np.outer(w, w)
+    phi = np.array([[oracle.dg_basis(8, a, b) for a, b in zip(r1, r2)] for r1, r2 in zip(XI, ET)])
+    M = np.einsum("ij,ijs,ijt->st", Wt, phi, phi)
+    expect = np.diag([1, 1 / 12, 1 / 12, 1 / 180, 1 / 144, 1 / 180, 1 / 2160, 1 / 2160])
+    assert np.allclose(M, expect, atol=1e-15)
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+def test_dg_basis_spans_total_degree(n_s):
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(0, 1, (30, 2))
+    mine = np.array([oracle.dg_basis(n_s, a, b) for a, b in pts])
+    other = np.array([BF.dg_bf(n_s, np.array(a), np.array(b)) for a, b in pts])
+    # same span: least-squares fit of one by the other is exact
+    coef = np.linalg.lstsq(mine, other, rcond=None)[0]
+    assert np.allclose(mine @ coef, other, atol=1e-13)
+    assert np.linalg.matrix_rank(mine) == n_s
+
+
+def test_q2_lagrange_partition_and_gradients():
+    nodes = [0.0, 0.5, 1.0]
+    for b in range(3):
+        for a in range(3):
+            phi, _, _ = oracle.q2_basis(nodes[a], nodes[b])
+            e = np.zeros(9); e[a + 3 * b] = 1.0
+            assert np.allclose(phi, e, atol=1e-15)
+    rng = np.random.default_rng(1)
+    for xi, eta in rng.uniform(0, 1, (20, 2)):
+        phi, dx, de = oracle.q2_basis(xi, eta)
+        assert abs(phi.sum() - 1) < 1e-14 and abs(dx.sum()) < 1e-13 and abs(de.sum()) < 1e-13
+        # reproduces the biquadratic p = xi^2 eta^2 + 3 xi eta and its gradient
+        nv = np.array([(nodes[j % 3], nodes[j // 3]) for j in range(9)])
+        pv = nv[:, 0] ** 2 * nv[:, 1] ** 2 + 3 * nv[:, 0] * nv[:, 1]
+        assert abs(phi @ pv - (xi ** 2 * eta ** 2 + 3 * xi * eta)) < 1e-14
+        assert abs(dx @ pv - (2 * xi * eta ** 2 + 3 * eta)) < 1e-13
+        assert abs(de @ pv - (2 * xi ** 2 * eta + 3 * xi)) < 1e-13
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("affine", [True, False])
+def test_projection_matrix_is_left_inverse(n_s, affine):
+    """iMJwPSI applied to the Gauss values of a DG function returns its coefficients."""
+    nx = ny = 3
+    L = 3e3
+    xy = W.uniform_vertices(nx, ny, L, L) if affine else perturbed_vertices(nx, ny, L, 5)
+    g = oracle.ngp(n_s)
+    x, _ = oracle.gauss(g)
+    XI, ET = np.meshgrid(x, x)
+    psi = np.array([oracle.dg_basis(n_s, a, b) for a, b in zip(XI.ravel(), ET.ravel())])  # (ng, ns)
+    for K in range(nx * ny):
+        det, m = oracle.element_map(nx, ny, xy, n_s, K)
+        assert np.allclose(m @ psi, np.eye(n_s), atol=1e-12)
+        if affine:
+            assert np.allclose(det, (L / nx) ** 2, rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Strain (stage 1)
+# --------------------------------------------------------------------------
+def _node_xy(nx, ny, xy):
+    """CG2 node coordinates through the bilinear map (test-side)."""
+    V = np.asarray(xy).reshape(ny + 1, nx + 1, 2)
+    nw = 2 * nx + 1
+    out = np.zeros((2, (2 * nx + 1) * (2 * ny + 1)))
+    for iy in range(2 * ny + 1):
+        for ix in range(nw):
+            kx, ky = min(ix // 2, nx - 1), min(iy // 2, ny - 1)
+            xi, eta = ix / 2 - kx, iy / 2 - ky
+            p = ((1 - xi) * (1 - eta) * V[ky, kx] + xi * (1 - eta) * V[ky, kx + 1]
+                 + (1 - xi) * eta * V[ky + 1, kx] + xi * eta * V[ky + 1, kx + 1])
+            out[:, iy * nw + ix] = p
+    return out
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("affine", [True, False])
+def test_strain_linear_field_exact(n_s, affine):
+    nx, ny, L = 4, 3, 8e3
+    xy = W.uniform_vertices(nx, ny, L, L) if affine else perturbed_vertices(nx, ny, L, 7)
+    nxy = _node_xy(nx, ny, xy)
+    a, b, c, d = 1.3e-6, -0.7e-6, 2.1e-6, -0.4e-6
+    vel = np.stack([a * nxy[0] + b * nxy[1], c * nxy[0] + d * nxy[1]])
+    E = oracle.strain(nx, ny, xy, n_s, vel)
+    const = np.array([a, (b + c) / 2, d])
+    assert np.allclose(E[:, 0, :], const[:, None], rtol=1e-11, atol=0)
+    assert np.abs(E[:, 1:, :]).max() < 1e-11 * abs(a)
+
+
+def test_strain_rigid_rotation_zero():
+    nx, ny, L = 3, 3, 3e3
+    xy = perturbed_vertices(nx, ny, L, 9)
+    nxy = _node_xy(nx, ny, xy)
+    w = 1e-5
+    vel = np.stack([-w * nxy[1], w * nxy[0]])
+    E = oracle.strain(nx, ny, xy, 6, vel)
+    assert np.abs(E).max() < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Stress (stage 2): paper constants, clamps, closed forms
+# --------------------------------------------------------------------------
+def _one_element_stress(n_s, E0, H, A, S0, params):
+    """1x1 mesh with a constant strain: the Gauss values all equal E0."""
+    L = 1e3
+    xy = W.uniform_vertices(1, 1, L, L)
+    E = np.zeros((3, n_s, 1)); E[:, 0, 0] = E0
+    S = np.zeros((3, n_s, 1)); S[:, 0, 0] = S0
+    return oracle.stress(1, 1, xy, n_s, 1, params, E, np.array([[H]]), np.array([[A]]), S)
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+def test_stress_single_point_matches_printed_constants(n_s):
+    d, s, st = GOLD["delta"], GOLD["stress"], GOLD["strength"]
+    p = dict(P0, Pstar=st["Pstar"], C=st["C"], e=2.0)
+    e11, e12, e22 = 3e-7, -1.1e-7, -2e-7
+    H, A = 1.4, 0.93
+    S0 = np.array([-1200.0, 300.0, -800.0])
+    out = _one_element_stress(n_s, [e11, e12, e22], H, A, S0, p)
+    P = st["Pstar"] * H * math.exp(-st["C"] * (1 - A))
+    D = math.sqrt(p["DeltaMin"] ** 2 + d["sq"] * (e11 ** 2 + e22 ** 2) + d["mix"] * e11 * e22
+                  + d["shear"] * e12 ** 2)
+    ai = 1 / p["alpha"]
+    expect = np.array([
+        (1 - ai) * S0[0] + ai * (P / D * (s["a"] * e11 + s["b"] * e22) - s["p"] * P),
+        (1 - ai) * S0[1] + ai * (P / D * s["c"] * e12),
+        (1 - ai) * S0[2] + ai * (P / D * (s["a"] * e22 + s["b"] * e11) - s["p"] * P)])
+    assert np.allclose(out[:, 0, 0], expect, rtol=1e-13)
+    assert np.abs(out[:, 1:, 0]).max() < 1e-9  # higher coefficients stay zero
+
+
+def test_stress_general_ellipse_is_hibler_law():
+    p = dict(P0, e=1.7)
+    e11, e12, e22 = 2e-7, 1.5e-7, -3e-7
+    out = _one_element_stress(3, [e11, e12, e22], 1.0, 1.0, np.zeros(3), p)
+    P = p["Pstar"]
+    ecc = p["e"]
+    D = math.sqrt(p["DeltaMin"] ** 2 + (e11 ** 2 + e22 ** 2) * (1 + ecc ** -2)
+                  + 4 * ecc ** -2 * e12 ** 2 + 2 * (1 - ecc ** -2) * e11 * e22)
+    zeta = P / (2 * D)
+    eta = zeta / ecc ** 2
+    tr = e11 + e22
+    svp = np.array([2 * eta * e11 + (zeta - eta) * tr - P / 2, 2 * eta * e12,
+                    2 * eta * e22 + (zeta - eta) * tr - P / 2])
+    assert np.allclose(out[:, 0, 0], svp / p["alpha"], rtol=1e-13)
+
+
+def test_stress_clamps():
+    p = dict(P0)
+    # negative H -> h = 0 -> no strength, the stress only decays
+    out = _one_element_stress(3, [1e-7, 0, 0], -0.5, 0.9, np.array([100.0, 50, -20]), p)
+    assert np.allclose(out[:, 0, 0], np.array([100.0, 50, -20]) * (1 - 1 / p["alpha"]), rtol=1e-14)
+    # A > 1 clamps to 1 (exp(0) = 1), A < 0 clamps to 0
+    hi = _one_element_stress(3, [0, 0, 0], 1.0, 1.7, np.zeros(3), p)
+    one = _one_element_stress(3, [0, 0, 0], 1.0, 1.0, np.zeros(3), p)
+    assert np.array_equal(hi, one)
+    lo = _one_element_stress(3, [0, 0, 0], 1.0, -0.3, np.zeros(3), p)
+    zero = _one_element_stress(3, [0, 0, 0], 1.0, 0.0, np.zeros(3), p)
+    assert np.array_equal(lo, zero)
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+def test_stress_relaxation_closed_form(n_s):
+    """E = 0, uniform H, A: S11_0^p = S22_0^p = -(P/2)(1 - (1-1/alpha)^p), S12 = 0."""
+    p = dict(P0)
+    nx = ny = 2
+    xy = W.uniform_vertices(nx, ny, 4e3, 4e3)
+    H = np.full((1, 4), 1.2); A = np.full((1, 4), 0.95)
+    S = np.zeros((3, n_s, 4)); E = np.zeros((3, n_s, 4))
+    P = p["Pstar"] * 1.2 * math.exp(-p["C"] * 0.05)
+    for k in range(1, 41):
+        S = oracle.stress(nx, ny, xy, n_s, 1, p, E, H, A, S)
+        ref = -(P / 2) * (1 - (1 - 1 / p["alpha"]) ** k)
+        assert np.allclose(S[0, 0], ref, rtol=1e-12) and np.allclose(S[2, 0], ref, rtol=1e-12)
+        assert np.abs(S[1]).max() == 0 and np.abs(S[:, 1:]).max() < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Divergence (stage 3)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n_s", [3, 6])
+def test_divergence_constant_stress(n_s):
+    """Constant sigma: interior nodes feel nothing; boundary nodes feel -sigma.n
+    times the 1-D Q2 edge weights (h/6, 4h/6, h/6); the total is zero."""
+    nx, ny = 3, 2
+    hx, hy = 2e3, 3e3
+    xy = W.uniform_vertices(nx, ny, nx * hx, ny * hy)
+    s11, s12, s22 = -1500.0, 400.0, -900.0
+    S = np.zeros((3, n_s, nx * ny))
+    S[0, 0], S[1, 0], S[2, 0] = s11, s12, s22
+    F = oracle.divergence(nx, ny, xy, n_s, S)
+    nw, nh = 2 * nx + 1, 2 * ny + 1
+    Fx = F[0].reshape(nh, nw); Fy = F[1].reshape(nh, nw)
+    scale = 1500.0 * 3e3
+    assert np.abs(Fx[1:-1, 1:-1]).max() < 1e-12 * scale
+    assert np.abs(Fy[1:-1, 1:-1]).max() < 1e-12 * scale
+
+    def edge_w(n, h):
+        w = np.zeros(2 * n + 1)
+        for k in range(n):
+            w[2 * k] += h / 6; w[2 * k + 1] += 4 * h / 6; w[2 * k + 2] += h / 6
+        return w
+    wy, wx = edge_w(ny, hy), edge_w(nx, hx)
+    # left edge, outward normal (-1, 0): force = -sigma.n * weight = (s11, s12) w
+    assert np.allclose(Fx[:, 0], s11 * wy + np.r_[s12 * hx / 6, np.zeros(nh - 2), -s12 * hx / 6],
+                       atol=1e-9 * scale)
+    assert np.allclose(F.sum(axis=1), 0, atol=1e-9 * scale)
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("affine", [True, False])
+def test_divergence_matches_bruteforce(n_s, affine):
+    nx, ny, L = 3, 2, 6e3
+    xy = W.uniform_vertices(nx, ny, L, L) if affine else perturbed_vertices(nx, ny, L, 3)
+    rng = np.random.default_rng(4)
+    S = rng.uniform(-1e3, 1e3, (3, n_s, nx * ny))
+    F = oracle.divergence(nx, ny, xy, n_s, S)
+    M = BF.Mesh(nx, ny, xy, n_s)
+    Fb = M.divergence(M.from_documented(S))
+    assert rel(F, Fb) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Lumped mass
+# --------------------------------------------------------------------------
+def test_lumped_closed_form():
+    nx, ny, h = 3, 3, 1e3
+    xy = W.uniform_vertices(nx, ny, nx * h, ny * h)
+    H = np.full((1, 9), 1.5)
+    m, l = oracle.lumped(nx, ny, xy, 3, 1, P0, H)
+    nw = 2 * nx + 1
+    L2 = l.reshape(nw, nw)
+    assert abs(l.sum() - 9 * h * h) < 1e-6
+    assert abs(L2[2, 2] - 4 * h * h / 36) < 1e-9          # interior vertex: 4 x 1/36
+    assert abs(L2[1, 2] - 2 * h * h * 4 / 36) < 1e-9      # edge midpoint: 2 x 4/36
+    assert abs(L2[1, 1] - h * h * 16 / 36) < 1e-9         # element centre: 16/36
+    assert np.allclose(m, P0["rho_ice"] * 1.5 * l, rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Velocity (stage 4) and the whole subcycle
+# --------------------------------------------------------------------------
+def _free_drift_case(nx=4, ny=4, n_sub=1, dt=120.0, f=1.46e-4, H0=1.3, tau0=(0.21, -0.13)):
+    p = dict(P0, Pstar=0.0, dt=dt, coriolis_f=f)
+    L = nx * 2e3
+    xy = W.uniform_vertices(nx, ny, L, L)
+    ne, nn, _ = W.sizes(nx, ny)
+    H = np.full((1, ne), H0); A = np.full((1, ne), 0.9)
+    tau = np.stack([np.full(nn, tau0[0]), np.full(nn, tau0[1])])
+    return p, xy, H, A, tau
+
+
+def test_rest_stays_at_rest():
+    """Zero forcing, zero velocity and stress, uniform H and A: v stays 0 and the
+    stress relaxes to -P/2 I.  On a 16 km mesh, where the mEVP iteration is
+    stable at alpha = beta = 300 (on a 2 km mesh it amplifies rounding)."""
+    nx = ny = 4
+    ne, nn, _ = W.sizes(nx, ny)
+    xy = W.uniform_vertices(nx, ny, 64e3, 64e3)
+    H = np.full((1, ne), 1.1); A = np.full((1, ne), 0.97)
+    vel, S = oracle.subcycles(nx, ny, xy, 6, 1, P0, H, A, np.zeros((2, nn)), np.zeros((2, nn)),
+                              np.zeros((3, 6, ne)), 50)
+    assert np.abs(vel).max() < 1e-16
+    P = P0["Pstar"] * 1.1 * math.exp(-P0["C"] * 0.03)
+    assert np.allclose(S[0, 0], -(P / 2) * (1 - (1 - 1 / P0["alpha"]) ** 50), rtol=1e-12)
+
+
+def test_free_drift_recurrence():
+    """P* = 0: sigma = 0; uniform H and tau make every interior node follow the
+    same complex recurrence (m/l = rho H at every node)."""
+    p, xy, H, A, tau = _free_drift_case()
+    nx = ny = 4
+    ne, nn, _ = W.sizes(nx, ny)
+    n_sub = 30
+    vel, _ = oracle.subcycles(nx, ny, xy, 3, 1, p, H, A, tau, np.zeros((2, nn)),
+                              np.zeros((3, 3, ne)), n_sub)
+    rhoH = p["rho_ice"] * 1.3
+    z, zn = 0j, 0j
+    t = complex(0.21, -0.13)
+    for _ in range(n_sub):
+        c = p["Cw"] * p["rho_water"] * abs(z)
+        z = (rhoH / p["dt"] * (p["beta"] * z + zn) + t) / (rhoH * (1 + p["beta"]) / p["dt"] + c
+                                                            + 1j * rhoH * p["coriolis_f"])
+    nw = 2 * nx + 1
+    grid = vel.reshape(2, nw, nw)[:, 1:-1, 1:-1]
+    assert np.allclose(grid[0], z.real, rtol=1e-13) and np.allclose(grid[1], z.imag, rtol=1e-13)
+    assert np.all(vel.reshape(2, nw, nw)[:, 0, :] == 0)
+
+
+def test_converged_subcycle_is_implicit_euler():
+    """Many subcycles converge to the implicit Euler step of free drift:
+    (rho H/dt + Cw rho_w s + i rho H f) v = tau, s = |v| (solved by bisection)."""
+    p, xy, H, A, tau = _free_drift_case(nx=2, ny=2)
+    ne, nn, _ = W.sizes(2, 2)
+    vel, _ = oracle.subcycles(2, 2, xy, 3, 1, p, H, A, tau, np.zeros((2, nn)),
+                              np.zeros((3, 3, ne)), 20000)
+    rhoH = p["rho_ice"] * 1.3
+    t = complex(0.21, -0.13)
+    k = p["Cw"] * p["rho_water"]
+
+    def g(s):
+        return abs(t) / abs(rhoH / p["dt"] + k * s + 1j * rhoH * p["coriolis_f"]) - s
+    lo, hi = 0.0, 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if g(mid) > 0 else (lo, mid)
+    s = 0.5 * (lo + hi)
+    v = t / (rhoH / p["dt"] + k * s + 1j * rhoH * p["coriolis_f"])
+    centre = vel[:, 2 * 5 + 2]
+    assert abs(centre[0] - v.real) < 1e-12 and abs(centre[1] - v.imag) < 1e-12
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("affine", [True, False])
+def test_whole_subcycle_matches_bruteforce(n_s, affine):
+    nx, ny = 2, 2
+    case = W.small_case(nx, ny, n_s, seed=21)
+    L = case["L"]
+    xy = case["xy"] if affine else perturbed_vertices(nx, ny, L, 31, amp=0.15)
+    p = case["params"]
+    n_sub = 6
+    vel, S, E, F, fel = oracle.subcycles(nx, ny, xy, n_s, 1, p, case["H"], case["A"], case["tau"],
+                                         case["vel0"], case["S0"], n_sub, want_last=True)
+    M = BF.Mesh(nx, ny, xy, n_s)
+    vb, Sb, Eb = M.subcycles(case["vel0"], case["S0"], case["H"], case["A"], case["tau"], p, n_sub)
+    assert rel(vel, vb) < 1e-12
+    assert rel(M.values_documented(S), M.values(Sb)) < 1e-12
+    assert rel(M.values_documented(E), M.values(Eb)) < 1e-12
+
+
+def test_mirror_symmetry():
+    """Mirroring the inputs in x (f = 0) mirrors the outputs: u -> -u, s12 -> -s12,
+    and DG coefficients odd in xi - 1/2 change sign."""
+    nx, ny, n_s = 4, 3, 6
+    case = W.small_case(nx, ny, n_s, seed=5)
+    p = dict(case["params"], coriolis_f=0.0)
+    ne, nn, _ = W.sizes(nx, ny)
+    nw, nh = 2 * nx + 1, 2 * ny + 1
+
+    def mnode(a):
+        return a.reshape(-1, nh, nw)[:, :, ::-1].reshape(a.shape)
+
+    def melem(a):
+        return a.reshape(a.shape[:-1] + (ny, nx))[..., ::-1].reshape(a.shape)
+    odd = np.array([1, -1, 1, 1, -1, 1])[:n_s]
+    comp_sign = np.array([1, -1, 1])
+    vel0, S0, tau = case["vel0"], case["S0"], case["tau"]
+    vel0m = mnode(vel0) * np.array([-1, 1])[:, None]
+    taum = mnode(tau) * np.array([-1, 1])[:, None]
+    S0m = melem(S0) * comp_sign[:, None, None] * odd[None, :, None]
+    args = (nx, ny, case["xy"], n_s, 1, p)
+    v1, S1 = oracle.subcycles(*args, case["H"], case["A"], tau, vel0, S0, 8)
+    v2, S2 = oracle.subcycles(*args, melem(case["H"]), melem(case["A"]), taum, vel0m, S0m, 8)
+    assert rel(mnode(v2) * np.array([-1, 1])[:, None], v1) < 1e-12
+    assert rel(melem(S2) * comp_sign[:, None, None] * odd[None, :, None], S1) < 1e-12
+
+
+def test_deterministic_and_openmp_identical():
+    case = W.small_case(6, 5, 6, seed=8)
+    args = (case["nx"], case["ny"], case["xy"], 6, 1, case["params"], case["H"], case["A"],
+            case["tau"], case["vel0"], case["S0"], 5)
+    a = oracle.subcycles(*args)
+    b = oracle.subcycles(*args)
+    c = oracle.subcycles(*args, openmp=True)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+def test_bad_arguments_rejected():
+    xy = W.uniform_vertices(2, 2, 1e3, 1e3)
+    with pytest.raises(ValueError):
+        oracle.strain(2, 2, xy, 1, np.zeros((2, 25)))  # DG0 stress unsupported
+    bad = xy.copy().reshape(3, 3, 2)
+    bad[1, 1] = bad[2, 2] + 10.0  # folded element: det J <= 0
+    with pytest.raises(ValueError):
+        oracle.strain(2, 2, bad.reshape(-1, 2), 3, np.zeros((2, 25)))
