@@ -1,0 +1,197 @@
+/*
+ * mevp.h -- C ABI of the GB300 mEVP momentum-subcycle library (libmevp.so).
+ *
+ * The library advances the viscous-plastic sea-ice momentum equation (Eq. 2 of
+ * Jendersie, Lessig, Richter, "Towards a GPU-Parallelization of the neXtSIM-DG
+ * Dynamical Core", PASC'24) with the mEVP pseudo-time iteration (Eq. 3) on one
+ * GPU.  One subcycle is the four stages of the paper's Table 1 -- strain,
+ * stress, divergence, velocity -- fused into two kernel launches.  The
+ * discretisation is the one of Sec. 2.1: CG2 (Q2) velocity on a structured
+ * quadrilateral mesh, tensor-valued DG stress (DG1 = 3 or DG2 = 6 dofs per
+ * component), DG0 ice height H and concentration A.  The stress update per
+ * element is the one printed in Listing 1 / App. A (generalised to any
+ * ellipse ratio e), with the inverse element map computed on the fly from the
+ * mesh vertices (Sec. 3.2, "on-the-fly map").
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an int status (MEVP_OK or a negative MEVP_ERR_*);
+ *     no C++ exception crosses this boundary.  mevp_last_error() returns a
+ *     thread-local, human-readable message for the last failing call of the
+ *     calling thread (valid until that thread's next failing call).
+ *   - Argument checks are synchronous.  Kernel launches are asynchronous on
+ *     the state's CUDA stream; an asynchronous CUDA error surfaces as
+ *     MEVP_ERR_CUDA at the next call that synchronises (mevp_sync,
+ *     mevp_read_field to host) or checks for launch errors.
+ *   - Handles are created and freed by the library; destroying NULL is a
+ *     no-op.  Input pointers are borrowed only for the duration of the call.
+ *   - "on_device" = 0: the pointer is host memory; the data are copied on the
+ *     state's stream and the call returns after the copy completed.
+ *     "on_device" = 1: the pointer is device memory of the state's device; the
+ *     copy is enqueued on the state's stream (the caller keeps the buffer
+ *     alive and unmodified until the stream reaches it).
+ *
+ * External array layouts (fixed, independent of the internal layout):
+ *   N_e = nx*ny elements, element id K = ky*nx + kx;
+ *   N_n = (2nx+1)(2ny+1) CG2 nodes, node id = iy*(2nx+1) + ix;
+ *   N_v = (nx+1)(ny+1) vertices, vertex id = jy*(nx+1) + jx.
+ *   velocity, wind stress, ocean velocity, forces: [2][N_n] (x row, then y)
+ *   stress, strain: [3][n_stress][N_e], component order 11, 12, 22
+ *   H, A: [n_adv][N_e]
+ *   vertex coordinates: [N_v][2] (x, y) pairs
+ * DG coefficients refer to the orthogonal basis on the reference square,
+ * with xh = xi - 1/2, eh = eta - 1/2:
+ *   {1, xh, eh, xh^2 - 1/12, xh*eh, eh^2 - 1/12}   (first 3 for DG1)
+ * Values at points, forces and velocities do not depend on this choice.
+ */
+#ifndef MEVP_GB300_C_ABI_H
+#define MEVP_GB300_C_ABI_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define MEVP_API __attribute__((visibility("default")))
+#else
+#define MEVP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mevp_mesh mevp_mesh;   /* opaque, library-owned */
+typedef struct mevp_state mevp_state; /* opaque, library-owned */
+
+/* Physical and iteration parameters.  Pstar, C, e (hard-coded 2 in the
+ * paper's code) and DeltaMin enter the stress update of Listing 1 / App. A;
+ * alpha is the stress relaxation of Eq. 3 in the relaxation form of the
+ * paper's code, S <- (1 - 1/alpha) S + (1/alpha) M^-1 (...); beta, dt,
+ * rho_ice, rho_water, Cw and coriolis_f enter the velocity update of Eq. 2. */
+typedef struct {
+  double Pstar;      /* ice strength P* [N/m^2] (> = 0)                  */
+  double C;          /* ice strength concentration parameter (>= 0)      */
+  double e;          /* yield-ellipse aspect ratio (> 0)                 */
+  double DeltaMin;   /* Delta_min [1/s] (> 0)                            */
+  double alpha;      /* stress relaxation (>= 1)                         */
+  double beta;       /* velocity relaxation (>= 0)                       */
+  double dt;         /* outer time step [s] (> 0)                        */
+  double rho_ice;    /* ice density [kg/m^3] (> 0)                       */
+  double rho_water;  /* water density [kg/m^3] (>= 0)                    */
+  double Cw;         /* ocean drag coefficient (>= 0)                    */
+  double coriolis_f; /* Coriolis parameter [1/s]                         */
+} mevp_params;
+
+enum { MEVP_FP64 = 0, MEVP_MIXED = 1 };
+
+enum {
+  MEVP_OK = 0,
+  MEVP_ERR_ARG = -1,         /* invalid argument (synchronous)                */
+  MEVP_ERR_CUDA = -2,        /* CUDA runtime or launch error                  */
+  MEVP_ERR_OOM = -3,         /* allocation failed or workspace too small      */
+  MEVP_ERR_STATE = -4,       /* call out of order (e.g. run before set_params) */
+  MEVP_ERR_NAN = -5,         /* non-finite value detected                     */
+  MEVP_ERR_TIMEOUT = -6,     /* bounded device wait gave up                   */
+  MEVP_ERR_UNSUPPORTED = -7  /* valid input this build does not handle        */
+};
+
+enum mevp_field {
+  MEVP_U = 0,          /* velocity x   [N_n]                                 */
+  MEVP_V = 1,          /* velocity y   [N_n]                                 */
+  MEVP_S11 = 2,        /* stress 11    [n_stress][N_e]                       */
+  MEVP_S12 = 3,        /* stress 12    [n_stress][N_e]                       */
+  MEVP_S22 = 4,        /* stress 22    [n_stress][N_e]                       */
+  MEVP_E11 = 5,        /* strain rate 11 of the current velocity [n_stress][N_e] */
+  MEVP_E12 = 6,        /* strain rate 12 (tensor component)                  */
+  MEVP_E22 = 7,        /* strain rate 22                                     */
+  MEVP_FORCE_X = 8,    /* nodal stress-divergence force of the current stress [N_n] */
+  MEVP_FORCE_Y = 9,
+  MEVP_H = 10,         /* ice height  [n_adv][N_e]                           */
+  MEVP_A = 11,         /* ice concentration [n_adv][N_e]                     */
+  MEVP_NODAL_MASS = 12 /* lumped nodal mass rho_ice int max(0,H) phi_j [N_n] (after begin_step) */
+};
+
+/* Create a structured nx x ny quadrilateral mesh (Sec. 2.1).  vertex_xy is
+ * [N_v][2] host memory, or NULL for a uniform mesh of [0,Lx] x [0,Ly]
+ * (Lx, Ly ignored when vertex_xy is given).  This build handles rectilinear
+ * meshes (vertex x depends only on jx, y only on jy, strictly increasing);
+ * other vertex sets return MEVP_ERR_UNSUPPORTED.  No device memory is
+ * allocated.  nx, ny >= 1 and (2nx+1)(2ny+1) < 2^31. */
+MEVP_API int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_xy,
+                     mevp_mesh **out);
+MEVP_API void mevp_mesh_destroy(mevp_mesh *mesh);
+
+/* Device workspace a state needs, in bytes (all internal buffers). */
+MEVP_API int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
+                               size_t *bytes);
+
+/* Create a state for n_stress in {3, 6} (DG1/DG2 stress; Gauss rule 2x2 or
+ * 3x3 as in App. A), n_adv = 1 (DG0 H, A) and precision MEVP_FP64 or
+ * MEVP_MIXED, bound to the current CUDA device and to cuda_stream
+ * (a cudaStream_t; NULL = legacy default stream).  workspace: device memory
+ * of at least mevp_state_workspace_bytes(), 256-byte aligned, owned by the
+ * caller and kept alive until mevp_state_destroy; or NULL, in which case the
+ * library allocates (cudaMalloc) and frees it.  The mesh must outlive the
+ * state.  All fields start at zero; parameters must be set before running. */
+MEVP_API int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
+                      void *cuda_stream, void *workspace, size_t workspace_bytes,
+                      mevp_state **out);
+MEVP_API void mevp_state_destroy(mevp_state *state);
+
+/* Parameters (copied).  Takes effect at the next mevp_begin_step. */
+MEVP_API int mevp_set_params(mevp_state *state, const mevp_params *params);
+
+/* H and A, [n_adv][N_e] FP64 each.  Takes effect at the next mevp_begin_step. */
+MEVP_API int mevp_set_ice(mevp_state *state, const double *H, const double *A, int on_device);
+
+/* Nodal wind stress tau [2][N_n] (N/m^2) and ocean velocity [2][N_n] (m/s)
+ * or NULL for an ocean at rest.  Takes effect at the next mevp_begin_step. */
+MEVP_API int mevp_set_forcing(mevp_state *state, const double *tau, const double *v_ocean,
+                     int on_device);
+
+/* Velocity [2][N_n]; boundary entries are stored as given but every
+ * subcycle writes 0 there (Dirichlet).  Does not change v^n. */
+MEVP_API int mevp_set_velocity(mevp_state *state, const double *uv, int on_device);
+
+/* Stress [3][n_stress][N_e]. */
+MEVP_API int mevp_set_stress(mevp_state *state, const double *S, int on_device);
+
+/* Start an outer time step: v^n := current velocity, and recompute from H, A,
+ * the forcing and the parameters the per-element ice strength
+ * P = P* max(0,H) exp(-C (1 - clamp(A,0,1))) and the per-node constants of
+ * the velocity update (lumped mass, forcing).  Asynchronous. */
+MEVP_API int mevp_begin_step(mevp_state *state);
+
+/* n >= 0 mEVP subcycles (Sec. 2: the momentum equation and Eq. 3 subcycled
+ * within one outer step) from the current velocity and stress, with v^n and
+ * the forcing of the last mevp_begin_step.  Asynchronous on the state's
+ * stream; two kernel launches per subcycle. */
+MEVP_API int mevp_run_subcycles(mevp_state *state, int n);
+
+/* Copy a field (enum mevp_field) to dst, FP64, `count` = number of doubles
+ * of dst (must be >= the field's size).  The strain and force fields are
+ * computed from the current velocity / stress by diagnostic kernels.  With
+ * on_device = 0 the call waits for the state's stream. */
+MEVP_API int mevp_read_field(mevp_state *state, int field, double *dst, size_t count, int on_device);
+
+/* Wait for all work on the state's stream; reports asynchronous errors. */
+MEVP_API int mevp_sync(mevp_state *state);
+
+/* Per-kernel timing with CUDA events, for benchmarks.  With on != 0 every
+ * launch of mevp_run_subcycles is bracketed by events on the state's stream.
+ * mevp_timing_read waits for the stream and returns, for kernel 0 (element
+ * kernel) and kernel 1 (node kernel), the summed milliseconds and the number
+ * of timed launches since the last read (or since timing was switched on),
+ * then resets both.  ms and launches point to 2 host values each. */
+MEVP_API int mevp_timing_enable(mevp_state *state, int on);
+MEVP_API int mevp_timing_read(mevp_state *state, double *ms, long long *launches);
+
+/* Thread-local message of the calling thread's last failing call. */
+MEVP_API const char *mevp_last_error(void);
+
+/* Library version string. */
+MEVP_API const char *mevp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEVP_GB300_C_ABI_H */

@@ -1,0 +1,484 @@
+// mevp_capi.cu -- the C ABI declared in include/mevp.h.
+//
+// Host-side bookkeeping only: argument checks, the workspace layout, copies
+// on the state's stream, and the launch sequence of a subcycle.  Every
+// arithmetic step of the method runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "mevp_internal.cuh"
+
+using mevp::DevState;
+using mevp::Rheo;
+
+struct mevp_state {
+  const mevp_mesh *mesh = nullptr;
+  int ns = 0, na = 0, prec = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = false;
+  DevState d{};
+  int cur = 0;
+  mevp_params prm{};
+  Rheo rheo{};
+  bool have_params = false;
+  bool prepared = false;
+  bool has_vo = false;
+  // event timing (benchmarks)
+  bool timing = false;
+  std::vector<cudaEvent_t> events;  // pool, 3 per timed subcycle
+  size_t ev_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(MEVP_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define MEVP_CUDA(call, what)                    \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t xline, yline, vel0, vel1, S, S32, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+      total;
+};
+
+Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
+  Layout L{};
+  const size_t ne = (size_t)m->nx * m->ny;
+  const size_t nn = (size_t)(2 * m->nx + 1) * (2 * m->ny + 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L.xline = take(sizeof(double) * (m->nx + 1));
+  L.yline = take(sizeof(double) * (m->ny + 1));
+  L.vel0 = take(sizeof(double) * 2 * nn);
+  L.vel1 = take(sizeof(double) * 2 * nn);
+  L.S = take(prec == MEVP_FP64 ? sizeof(double) * 3 * ns * ne : 0);
+  L.S32 = take(prec == MEVP_MIXED ? sizeof(float) * 3 * ns * ne : 0);
+  L.H = take(sizeof(double) * na * ne);
+  L.A = take(sizeof(double) * na * ne);
+  L.tau = take(sizeof(double) * 2 * nn);
+  L.vo = take(sizeof(double) * 2 * nn);
+  L.Pe = take(sizeof(double) * ne);
+  L.nodec = take(sizeof(double) * 6 * nn);
+  L.mass = take(sizeof(double) * nn);
+  L.fbuf = take(prec == MEVP_FP64 ? sizeof(double) * 18 * ne : 0);
+  L.fbuf32 = take(prec == MEVP_MIXED ? sizeof(float) * 18 * ne : 0);
+  const size_t dg = sizeof(double) * 3 * ns * ne, nd = sizeof(double) * 2 * nn;
+  L.diag = take(dg > nd ? dg : nd);
+  L.total = off;
+  return L;
+}
+
+bool finite_all(const double *p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+int check_state(const mevp_state *s) {
+  if (!s) return fail(MEVP_ERR_ARG, "state is NULL");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != s->device)
+    return fail(MEVP_ERR_STATE, "current device %d is not the state's device %d", dev, s->device);
+  return MEVP_OK;
+}
+
+// Copy n doubles into device buffer dst on the state's stream.
+int copy_in(mevp_state *s, double *dst, const double *src, size_t n, int on_device,
+            const char *what) {
+  if (!src) return fail(MEVP_ERR_ARG, "%s: NULL pointer", what);
+  if (!on_device && !finite_all(src, n))
+    return fail(MEVP_ERR_NAN, "%s: non-finite value in host input", what);
+  MEVP_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s->stream),
+            what);
+  if (!on_device) MEVP_CUDA(cudaStreamSynchronize(s->stream), what);
+  return MEVP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mevp_last_error(void) { return g_err.c_str(); }
+
+const char *mevp_version(void) { return "mevp-gb300 0.1 (sm_103a)"; }
+
+int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_xy,
+                     mevp_mesh **out) {
+  if (!out) return fail(MEVP_ERR_ARG, "mesh_create: out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1) return fail(MEVP_ERR_ARG, "mesh_create: nx=%d ny=%d must be >= 1", nx, ny);
+  const long long nn = (long long)(2 * (long long)nx + 1) * (2 * (long long)ny + 1);
+  if (nn >= (1LL << 31) - 1) return fail(MEVP_ERR_ARG, "mesh_create: too many nodes (%lld)", nn);
+  mevp_mesh *m = new (std::nothrow) mevp_mesh;
+  if (!m) return fail(MEVP_ERR_OOM, "mesh_create: host allocation failed");
+  m->nx = nx;
+  m->ny = ny;
+  m->xline.resize(nx + 1);
+  m->yline.resize(ny + 1);
+  if (!vertex_xy) {
+    if (!(std::isfinite(Lx) && std::isfinite(Ly) && Lx > 0 && Ly > 0)) {
+      delete m;
+      return fail(MEVP_ERR_ARG, "mesh_create: Lx, Ly must be finite and > 0");
+    }
+    for (int i = 0; i <= nx; ++i) m->xline[i] = Lx * i / nx;
+    for (int j = 0; j <= ny; ++j) m->yline[j] = Ly * j / ny;
+  } else {
+    const int vw = nx + 1;
+    for (int i = 0; i <= nx; ++i) m->xline[i] = vertex_xy[2 * i];
+    for (int j = 0; j <= ny; ++j) m->yline[j] = vertex_xy[2 * (j * vw) + 1];
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i <= nx; ++i) {
+        const double x = vertex_xy[2 * (j * vw + i)], y = vertex_xy[2 * (j * vw + i) + 1];
+        if (!std::isfinite(x) || !std::isfinite(y)) {
+          delete m;
+          return fail(MEVP_ERR_ARG, "mesh_create: non-finite vertex %d", j * vw + i);
+        }
+        if (x != m->xline[i] || y != m->yline[j]) {
+          delete m;
+          return fail(MEVP_ERR_UNSUPPORTED,
+                      "mesh_create: vertex (%d,%d) breaks the rectilinear layout; this build "
+                      "handles rectilinear meshes only",
+                      i, j);
+        }
+      }
+  }
+  for (int i = 0; i < nx; ++i)
+    if (!(m->xline[i + 1] > m->xline[i])) {
+      delete m;
+      return fail(MEVP_ERR_ARG, "mesh_create: x coordinates must increase (column %d)", i);
+    }
+  for (int j = 0; j < ny; ++j)
+    if (!(m->yline[j + 1] > m->yline[j])) {
+      delete m;
+      return fail(MEVP_ERR_ARG, "mesh_create: y coordinates must increase (row %d)", j);
+    }
+  *out = m;
+  return MEVP_OK;
+}
+
+void mevp_mesh_destroy(mevp_mesh *mesh) { delete mesh; }
+
+int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
+                               size_t *bytes) {
+  if (!mesh || !bytes) return fail(MEVP_ERR_ARG, "workspace_bytes: NULL argument");
+  if (n_stress != 3 && n_stress != 6)
+    return fail(MEVP_ERR_ARG, "n_stress=%d: DG stress needs 3 or 6 dofs", n_stress);
+  if (n_adv != 1) return fail(MEVP_ERR_UNSUPPORTED, "n_adv=%d: this build handles DG0 (1)", n_adv);
+  if (precision != MEVP_FP64 && precision != MEVP_MIXED)
+    return fail(MEVP_ERR_ARG, "precision=%d unknown", precision);
+  *bytes = make_layout(mesh, n_stress, n_adv, precision).total;
+  return MEVP_OK;
+}
+
+int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
+                      void *cuda_stream, void *workspace, size_t workspace_bytes,
+                      mevp_state **out) {
+  if (!out) return fail(MEVP_ERR_ARG, "state_create: out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = mevp_state_workspace_bytes(mesh, n_stress, n_adv, precision, &need);
+  if (rc) return rc;
+  if (precision == MEVP_MIXED)
+    return fail(MEVP_ERR_UNSUPPORTED, "state_create: mixed precision not built yet");
+  if (workspace && workspace_bytes < need)
+    return fail(MEVP_ERR_OOM, "state_create: workspace %zu bytes < %zu needed", workspace_bytes,
+                need);
+  if (workspace && ((uintptr_t)workspace & 255))
+    return fail(MEVP_ERR_ARG, "state_create: workspace must be 256-byte aligned");
+  mevp_state *s = new (std::nothrow) mevp_state;
+  if (!s) return fail(MEVP_ERR_OOM, "state_create: host allocation failed");
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  s->mesh = mesh;
+  s->ns = n_stress;
+  s->na = n_adv;
+  s->prec = precision;
+  s->stream = (cudaStream_t)cuda_stream;
+  if (workspace) {
+    s->ws = workspace;
+  } else {
+    e = cudaMalloc(&s->ws, need);
+    if (e != cudaSuccess) {
+      delete s;
+      cudaGetLastError();
+      return fail(MEVP_ERR_OOM, "state_create: cudaMalloc(%zu) failed: %s", need,
+                  cudaGetErrorString(e));
+    }
+    s->owns_ws = true;
+  }
+  s->ws_bytes = need;
+  const Layout L = make_layout(mesh, n_stress, n_adv, precision);
+  char *b = (char *)s->ws;
+  DevState &d = s->d;
+  d.nx = mesh->nx;
+  d.ny = mesh->ny;
+  d.ne = mesh->nx * mesh->ny;
+  d.nw = 2 * mesh->nx + 1;
+  d.nh = 2 * mesh->ny + 1;
+  d.nn = d.nw * d.nh;
+  d.ns = n_stress;
+  d.prec = precision;
+  d.xline = (const double *)(b + L.xline);
+  d.yline = (const double *)(b + L.yline);
+  d.vel[0] = (double *)(b + L.vel0);
+  d.vel[1] = (double *)(b + L.vel1);
+  d.S = (double *)(b + L.S);
+  d.S32 = (float *)(b + L.S32);
+  d.H = (double *)(b + L.H);
+  d.A = (double *)(b + L.A);
+  d.tau = (double *)(b + L.tau);
+  d.vo = (double *)(b + L.vo);
+  d.Pe = (double *)(b + L.Pe);
+  d.nodec = (double *)(b + L.nodec);
+  d.mass = (double *)(b + L.mass);
+  d.fbuf = (double *)(b + L.fbuf);
+  d.fbuf32 = (float *)(b + L.fbuf32);
+  d.diag = (double *)(b + L.diag);
+  int r2 = MEVP_OK;
+  e = cudaMemsetAsync(s->ws, 0, need, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)d.xline, mesh->xline.data(), sizeof(double) * (d.nx + 1),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)d.yline, mesh->yline.data(), sizeof(double) * (d.ny + 1),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) r2 = cuda_fail(e, "state_create: initialise workspace");
+  if (r2) {
+    if (s->owns_ws) cudaFree(s->ws);
+    delete s;
+    return r2;
+  }
+  *out = s;
+  return MEVP_OK;
+}
+
+void mevp_state_destroy(mevp_state *s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+  if (s->owns_ws) cudaFree(s->ws);
+  delete s;
+}
+
+int mevp_set_params(mevp_state *s, const mevp_params *p) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (!p) return fail(MEVP_ERR_ARG, "set_params: NULL");
+  const double v[] = {p->Pstar, p->C,  p->e,         p->DeltaMin,  p->alpha,      p->beta,
+                      p->dt,    p->rho_ice, p->rho_water, p->Cw, p->coriolis_f};
+  for (double x : v)
+    if (!std::isfinite(x)) return fail(MEVP_ERR_ARG, "set_params: non-finite parameter");
+  if (p->Pstar < 0 || p->C < 0) return fail(MEVP_ERR_ARG, "set_params: Pstar, C must be >= 0");
+  if (!(p->e > 0)) return fail(MEVP_ERR_ARG, "set_params: e must be > 0");
+  if (!(p->DeltaMin > 0)) return fail(MEVP_ERR_ARG, "set_params: DeltaMin must be > 0");
+  if (!(p->alpha >= 1)) return fail(MEVP_ERR_ARG, "set_params: alpha must be >= 1");
+  if (!(p->beta >= 0)) return fail(MEVP_ERR_ARG, "set_params: beta must be >= 0");
+  if (!(p->dt > 0)) return fail(MEVP_ERR_ARG, "set_params: dt must be > 0");
+  if (!(p->rho_ice > 0)) return fail(MEVP_ERR_ARG, "set_params: rho_ice must be > 0");
+  if (p->rho_water < 0 || p->Cw < 0)
+    return fail(MEVP_ERR_ARG, "set_params: rho_water, Cw must be >= 0");
+  s->prm = *p;
+  const double ie2 = 1.0 / (p->e * p->e);
+  Rheo &r = s->rheo;
+  r.dmin2 = p->DeltaMin * p->DeltaMin;
+  r.k_sq = 1.0 + ie2;
+  r.k_mix = 2.0 * (1.0 - ie2);
+  r.k_sh = 4.0 * ie2;
+  r.c_a = 0.5 * (1.0 + ie2);
+  r.c_b = 0.5 * (1.0 - ie2);
+  r.c_s = ie2;
+  r.ainv = 1.0 / p->alpha;
+  r.fac = 1.0 - r.ainv;
+  s->have_params = true;
+  return MEVP_OK;
+}
+
+int mevp_set_ice(mevp_state *s, const double *H, const double *A, int on_device) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  const size_t n = (size_t)s->na * s->d.ne;
+  if ((rc = copy_in(s, s->d.H, H, n, on_device, "set_ice H"))) return rc;
+  return copy_in(s, s->d.A, A, n, on_device, "set_ice A");
+}
+
+int mevp_set_forcing(mevp_state *s, const double *tau, const double *v_ocean, int on_device) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  const size_t n = 2 * (size_t)s->d.nn;
+  if ((rc = copy_in(s, s->d.tau, tau, n, on_device, "set_forcing tau"))) return rc;
+  if (v_ocean) {
+    if ((rc = copy_in(s, s->d.vo, v_ocean, n, on_device, "set_forcing v_ocean"))) return rc;
+    s->has_vo = true;
+  } else {
+    MEVP_CUDA(cudaMemsetAsync(s->d.vo, 0, n * sizeof(double), s->stream), "set_forcing");
+    s->has_vo = false;
+  }
+  return MEVP_OK;
+}
+
+int mevp_set_velocity(mevp_state *s, const double *uv, int on_device) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  return copy_in(s, s->d.vel[s->cur], uv, 2 * (size_t)s->d.nn, on_device, "set_velocity");
+}
+
+int mevp_set_stress(mevp_state *s, const double *S, int on_device) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (s->prec != MEVP_FP64) return fail(MEVP_ERR_UNSUPPORTED, "set_stress: precision");
+  return copy_in(s, s->d.S, S, 3 * (size_t)s->ns * s->d.ne, on_device, "set_stress");
+}
+
+int mevp_begin_step(mevp_state *s) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (!s->have_params) return fail(MEVP_ERR_STATE, "begin_step: parameters not set");
+  cudaError_t e = mevp::launch_prepare(s->d, s->prm, s->has_vo, s->cur, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "begin_step launch");
+  s->prepared = true;
+  return MEVP_OK;
+}
+
+int mevp_run_subcycles(mevp_state *s, int n) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (n < 0) return fail(MEVP_ERR_ARG, "run_subcycles: n=%d < 0", n);
+  if (!s->prepared) return fail(MEVP_ERR_STATE, "run_subcycles: call mevp_begin_step first");
+  for (int i = 0; i < n; ++i) {
+    cudaEvent_t *ev = nullptr;
+    if (s->timing) {
+      while (s->events.size() < s->ev_used + 3) {
+        cudaEvent_t e;
+        MEVP_CUDA(cudaEventCreate(&e), "run_subcycles timing event");
+        s->events.push_back(e);
+      }
+      ev = &s->events[s->ev_used];
+      s->ev_used += 3;
+    }
+    cudaError_t e = mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, s->cur, s->stream, ev);
+    if (e != cudaSuccess) return cuda_fail(e, "run_subcycles launch");
+    s->cur ^= 1;
+  }
+  return MEVP_OK;
+}
+
+int mevp_timing_enable(mevp_state *s, int on) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  s->timing = on != 0;
+  s->ev_used = 0;
+  return MEVP_OK;
+}
+
+int mevp_timing_read(mevp_state *s, double *ms, long long *launches) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (!ms || !launches) return fail(MEVP_ERR_ARG, "timing_read: NULL output");
+  MEVP_CUDA(cudaStreamSynchronize(s->stream), "timing_read sync");
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  for (size_t i = 0; i + 3 <= s->ev_used; i += 3) {
+    float a = 0.f, b = 0.f;
+    MEVP_CUDA(cudaEventElapsedTime(&a, s->events[i], s->events[i + 1]), "timing_read");
+    MEVP_CUDA(cudaEventElapsedTime(&b, s->events[i + 1], s->events[i + 2]), "timing_read");
+    ms[0] += a;
+    ms[1] += b;
+    launches[0] += 1;
+    launches[1] += 1;
+  }
+  s->ev_used = 0;
+  return MEVP_OK;
+}
+
+int mevp_read_field(mevp_state *s, int field, double *dst, size_t count, int on_device) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (!dst) return fail(MEVP_ERR_ARG, "read_field: dst is NULL");
+  const DevState &d = s->d;
+  const size_t nn = d.nn, ne = d.ne, ns = s->ns;
+  const double *src = nullptr;
+  size_t n = 0;
+  cudaError_t e = cudaSuccess;
+  switch (field) {
+    case MEVP_U: src = d.vel[s->cur]; n = nn; break;
+    case MEVP_V: src = d.vel[s->cur] + nn; n = nn; break;
+    case MEVP_S11: case MEVP_S12: case MEVP_S22:
+      if (s->prec != MEVP_FP64) return fail(MEVP_ERR_UNSUPPORTED, "read_field: precision");
+      src = d.S + (size_t)(field - MEVP_S11) * ns * ne;
+      n = ns * ne;
+      break;
+    case MEVP_E11: case MEVP_E12: case MEVP_E22:
+      e = mevp::launch_strain_diag(d, s->cur, s->stream);
+      src = d.diag + (size_t)(field - MEVP_E11) * ns * ne;
+      n = ns * ne;
+      break;
+    case MEVP_FORCE_X: case MEVP_FORCE_Y:
+      if (s->prec != MEVP_FP64) return fail(MEVP_ERR_UNSUPPORTED, "read_field: precision");
+      e = mevp::launch_force_diag(d, s->stream);
+      src = d.diag + (size_t)(field - MEVP_FORCE_X) * nn;
+      n = nn;
+      break;
+    case MEVP_H: src = d.H; n = (size_t)s->na * ne; break;
+    case MEVP_A: src = d.A; n = (size_t)s->na * ne; break;
+    case MEVP_NODAL_MASS: src = d.mass; n = nn; break;
+    default: return fail(MEVP_ERR_ARG, "read_field: unknown field %d", field);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "read_field diagnostic launch");
+  if (count < n) return fail(MEVP_ERR_ARG, "read_field: count %zu < field size %zu", count, n);
+  MEVP_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            s->stream),
+            "read_field copy");
+  if (!on_device) MEVP_CUDA(cudaStreamSynchronize(s->stream), "read_field sync");
+  return MEVP_OK;
+}
+
+int mevp_sync(mevp_state *s) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  MEVP_CUDA(cudaStreamSynchronize(s->stream), "sync");
+  MEVP_CUDA(cudaGetLastError(), "sync");
+  return MEVP_OK;
+}
+
+}  // extern "C"

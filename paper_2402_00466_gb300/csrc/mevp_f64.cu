@@ -1,0 +1,425 @@
+// mevp_f64.cu -- FP64 kernels of the mEVP momentum subcycle on GB300 (sm_103a).
+//
+// One subcycle (the four stages of Table 1 of Jendersie, Lessig, Richter,
+// PASC'24) runs as two launches:
+//
+//   k_element_f64  one thread per element: gather the 9 CG2 velocities,
+//                  project the symmetric velocity gradient onto the DG stress
+//                  space (strain), evaluate it at the Gauss points, apply the
+//                  viscous-plastic law and the relaxed stress update of
+//                  Listing 1 / App. A (stress), and form the weak divergence
+//                  of the new stress tested with the 9 Q2 functions (element
+//                  part of "divergence").  Writes S and 18 element forces.
+//   k_node_f64     one thread per 2x2 block of CG2 nodes: sum the element
+//                  forces of the (up to four) elements around each node in
+//                  the fixed order SW, SE, NW, NE -- a gather, no atomics --
+//                  and solve the beta-relaxed implicit velocity update with
+//                  ocean drag and Coriolis ("velocity").
+//
+// The element geometry is recomputed on the fly from the mesh lines (the
+// paper's "on-the-fly map", Sec. 3.2), so no per-element matrices are read.
+// On a rectangle the inverse local mass and the Jacobian cancel, leaving the
+// compile-time reference tables of mevp_ref.cuh scaled by 1/hx, 1/hy.
+#include "mevp_internal.cuh"
+#include "mevp_ref.cuh"
+
+namespace mevp {
+
+namespace {
+
+constexpr int kElemBlock = 128;
+constexpr int kNodeBlock = 256;
+
+__device__ __forceinline__ void gather9(const double *__restrict__ f, int nw, int kx, int ky,
+                                        double out[9]) {
+  const double *base = f + (size_t)(2 * ky) * nw + 2 * kx;
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a + 3 * b] = __ldg(base + (size_t)b * nw + a);
+}
+
+// Strain: E_c = M^-1 int phi eps_c(v) on a rectangle hx x hy, through the
+// exact projected reference derivatives (eps12 = (du/dy + dv/dx)/2).
+template <int NS>
+__device__ __forceinline__ void strain_dg(const double u[9], const double v[9], double ihx,
+                                          double ihy, double E11[NS], double E12[NS],
+                                          double E22[NS]) {
+  const double h2x = 0.5 * ihx, h2y = 0.5 * ihy;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double uxi = -0.0, ueta = -0.0, vxi = -0.0, veta = -0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const double cx = dxi(s, j), ce = deta(s, j);
+      if (cx != 0.0) {
+        uxi = fma(cx, u[j], uxi);
+        vxi = fma(cx, v[j], vxi);
+      }
+      if (ce != 0.0) {
+        ueta = fma(ce, u[j], ueta);
+        veta = fma(ce, v[j], veta);
+      }
+    }
+    E11[s] = ihx * uxi;
+    E22[s] = ihy * veta;
+    E12[s] = fma(h2y, ueta, h2x * vxi);
+  }
+}
+
+// Stress: Gauss-point evaluation, viscous-plastic law with ice strength P,
+// relaxed update S <- (1 - 1/alpha) S + M^-1 int phi s_vp / alpha.
+template <int NS>
+__device__ __forceinline__ void stress_update(double S11[NS], double S12[NS], double S22[NS],
+                                              const double E11[NS], const double E12[NS],
+                                              const double E22[NS], double P, const Rheo &r) {
+  constexpr int NGP = DgSpace<NS>::NGP;
+  constexpr int NG = NGP * NGP;
+  double a11[NS], a12[NS], a22[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) a11[s] = a12[s] = a22[s] = -0.0;
+  const double halfP = 0.5 * P;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    double e11 = -0.0, e12 = -0.0, e22 = -0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double ps = psi<NS>(s, g);
+      if (ps != 0.0) {
+        e11 = fma(ps, E11[s], e11);
+        e12 = fma(ps, E12[s], e12);
+        e22 = fma(ps, E22[s], e22);
+      }
+    }
+    const double d2 = r.dmin2 + r.k_sq * (e11 * e11 + e22 * e22) + r.k_mix * e11 * e22 +
+                      r.k_sh * e12 * e12;
+    const double PD = P / sqrt(d2);
+    const double s11 = r.ainv * (PD * (r.c_a * e11 + r.c_b * e22) - halfP);
+    const double s12 = r.ainv * (PD * (r.c_s * e12));
+    const double s22 = r.ainv * (PD * (r.c_a * e22 + r.c_b * e11) - halfP);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double q = proj<NS>(s, g);
+      if (q != 0.0) {
+        a11[s] = fma(q, s11, a11[s]);
+        a12[s] = fma(q, s12, a12[s]);
+        a22[s] = fma(q, s22, a22[s]);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    S11[s] = fma(r.fac, S11[s], a11[s]);
+    S12[s] = fma(r.fac, S12[s], a12[s]);
+    S22[s] = fma(r.fac, S22[s], a22[s]);
+  }
+}
+
+// Element forces f_j = -int sigma : grad phi_j on a rectangle hx x hy.
+template <int NS>
+__device__ __forceinline__ void element_forces(const double S11[NS], const double S12[NS],
+                                               const double S22[NS], double hx, double hy,
+                                               double fx[9], double fy[9]) {
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    double x1 = -0.0, x2 = -0.0, y1 = -0.0, y2 = -0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double gx = gxi(j, s), ge = geta(j, s);
+      if (gx != 0.0) {
+        x1 = fma(gx, S11[s], x1);
+        y1 = fma(gx, S12[s], y1);
+      }
+      if (ge != 0.0) {
+        x2 = fma(ge, S12[s], x2);
+        y2 = fma(ge, S22[s], y2);
+      }
+    }
+    fx[j] = -fma(hy, x1, hx * x2);
+    fy[j] = -fma(hy, y1, hx * y2);
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, int cur) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const double hx = d.xline[kx + 1] - d.xline[kx];
+  const double hy = d.yline[ky + 1] - d.yline[ky];
+  const double ihx = 1.0 / hx, ihy = 1.0 / hy;
+  double u[9], v[9];
+  gather9(d.vel[cur], d.nw, kx, ky, u);
+  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+  double E11[NS], E12[NS], E22[NS];
+  strain_dg<NS>(u, v, ihx, ihy, E11, E12, E22);
+  double S11[NS], S12[NS], S22[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
+    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
+    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+  }
+  stress_update<NS>(S11, S12, S22, E11, E12, E22, __ldg(d.Pe + K), r);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    d.S[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
+    d.S[(size_t)(1 * NS + s) * d.ne + K] = S12[s];
+    d.S[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
+  }
+  double fx[9], fy[9];
+  element_forces<NS>(S11, S12, S22, hx, hy, fx, fy);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    d.fbuf[(size_t)j * d.ne + K] = fx[j];
+    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+  }
+}
+
+// Sum of the element forces at node (ix, iy) over the elements that contain
+// it, in ascending element order (SW, SE, NW, NE), starting from the first.
+__device__ __forceinline__ void gather_force(const double *__restrict__ fb, int ne, int nx,
+                                             int ny, int ix, int iy, double &Fx, double &Fy) {
+  const int kx1 = (ix & 1) ? (ix >> 1) : (ix >> 1) - 1;  // first candidate column
+  const int kx2 = ix >> 1;                                // last candidate column
+  const int ky1 = (iy & 1) ? (iy >> 1) : (iy >> 1) - 1;
+  const int ky2 = iy >> 1;
+  bool first = true;
+  Fx = 0.0;
+  Fy = 0.0;
+  for (int ky = ky1; ky <= ky2; ++ky) {
+    if (ky < 0 || ky >= ny) continue;
+    for (int kx = kx1; kx <= kx2; ++kx) {
+      if (kx < 0 || kx >= nx) continue;
+      const int j = (ix - 2 * kx) + 3 * (iy - 2 * ky);
+      const int K = ky * nx + kx;
+      const double gx = __ldg(fb + (size_t)j * ne + K);
+      const double gy = __ldg(fb + (size_t)(9 + j) * ne + K);
+      if (first) {
+        Fx = gx;
+        Fy = gy;
+        first = false;
+      } else {
+        Fx += gx;
+        Fy += gy;
+      }
+    }
+  }
+}
+
+// Velocity update at an interior node (Eq. 2 with the mEVP beta relaxation;
+// drag coefficient lagged, drag and Coriolis implicit):
+//   a = m(1+beta)/dt + c,  b = m f,  c = l Cw rho_w |v_o - v^{p-1}|
+//   r = m beta/dt v^{p-1} + (m/dt v^n + l tau) + F + c v_o
+//   (a + i b) v^p = r   (complex notation)
+__global__ void __launch_bounds__(kNodeBlock) k_node_f64(DevState d, int cur, int has_vo) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sw = d.nx + 1;
+  if (slot >= sw * (d.ny + 1)) return;
+  const int ky = slot / sw, kx = slot - ky * sw;
+  const double *__restrict__ vp = d.vel[cur];
+  double *__restrict__ vq = d.vel[cur ^ 1];
+  const size_t nn = d.nn;
+  const size_t ne = d.ne;
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy) {
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const int ix = 2 * kx + dx, iy = 2 * ky + dy;
+      if (ix >= d.nw || iy >= d.nh) continue;
+      const size_t node = (size_t)iy * d.nw + ix;
+      if (ix == 0 || iy == 0 || ix == d.nw - 1 || iy == d.nh - 1) {
+        vq[node] = 0.0;
+        vq[nn + node] = 0.0;
+        continue;
+      }
+      const double *__restrict__ fb = d.fbuf;
+      double Fx, Fy;
+      if (dx == 0 && dy == 0) {  // vertex node: 4 elements
+        const size_t Ksw = (size_t)(ky - 1) * d.nx + kx - 1, Kse = Ksw + 1;
+        const size_t Knw = (size_t)ky * d.nx + kx - 1, Kne = Knw + 1;
+        Fx = __ldg(fb + 8 * ne + Ksw) + __ldg(fb + 6 * ne + Kse);
+        Fx = Fx + __ldg(fb + 2 * ne + Knw);
+        Fx = Fx + __ldg(fb + 0 * ne + Kne);
+        Fy = __ldg(fb + 17 * ne + Ksw) + __ldg(fb + 15 * ne + Kse);
+        Fy = Fy + __ldg(fb + 11 * ne + Knw);
+        Fy = Fy + __ldg(fb + 9 * ne + Kne);
+      } else if (dx == 1 && dy == 0) {  // horizontal edge: S then N element
+        const size_t Ks = (size_t)(ky - 1) * d.nx + kx, Kn = (size_t)ky * d.nx + kx;
+        Fx = __ldg(fb + 7 * ne + Ks) + __ldg(fb + 1 * ne + Kn);
+        Fy = __ldg(fb + 16 * ne + Ks) + __ldg(fb + 10 * ne + Kn);
+      } else if (dx == 0 && dy == 1) {  // vertical edge: W then E element
+        const size_t Kw = (size_t)ky * d.nx + kx - 1, Ke = Kw + 1;
+        Fx = __ldg(fb + 5 * ne + Kw) + __ldg(fb + 3 * ne + Ke);
+        Fy = __ldg(fb + 14 * ne + Kw) + __ldg(fb + 12 * ne + Ke);
+      } else {  // element centre
+        const size_t K = (size_t)ky * d.nx + kx;
+        Fx = __ldg(fb + 4 * ne + K);
+        Fy = __ldg(fb + 13 * ne + K);
+      }
+      const double vx = vp[node], vy = vp[nn + node];
+      const double cA = __ldg(d.nodec + 0 * nn + node), cB = __ldg(d.nodec + 1 * nn + node);
+      const double cK = __ldg(d.nodec + 2 * nn + node), qx = __ldg(d.nodec + 3 * nn + node);
+      const double qy = __ldg(d.nodec + 4 * nn + node), cD = __ldg(d.nodec + 5 * nn + node);
+      double ox = 0.0, oy = 0.0;
+      if (has_vo) {
+        ox = __ldg(d.vo + node);
+        oy = __ldg(d.vo + nn + node);
+      }
+      const double dvx = ox - vx, dvy = oy - vy;
+      const double c = cD * sqrt(dvx * dvx + dvy * dvy);
+      const double a = cA + c;
+      const double rx = fma(cK, vx, qx) + Fx + c * ox;
+      const double ry = fma(cK, vy, qy) + Fy + c * oy;
+      const double det = fma(a, a, cB * cB);
+      double ux = 0.0, uy = 0.0;
+      if (det != 0.0) {
+        const double inv = 1.0 / det;
+        ux = fma(a, rx, cB * ry) * inv;
+        uy = fma(a, ry, -cB * rx) * inv;
+      }
+      vq[node] = ux;
+      vq[nn + node] = uy;
+    }
+  }
+}
+
+// ---- outer-step preparation ----------------------------------------------
+__global__ void k_strength(DevState d, double Pstar, double C) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const double h = fmax(0.0, d.H[K]);
+  const double a = fmin(1.0, fmax(0.0, d.A[K]));
+  d.Pe[K] = Pstar * h * exp(-C * (1.0 - a));
+}
+
+// Lumped mass m_j = rho_ice sum_K max(0,H_K) hx hy w_a w_b and area
+// l_j = sum_K hx hy w_a w_b (w = 1/6, 2/3, 1/6), then the node constants.
+__global__ void k_node_constants(DevState d, int cur, mevp_params p, int has_vo) {
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= d.nn) return;
+  const int iy = node / d.nw, ix = node - iy * d.nw;
+  const int kx1 = (ix & 1) ? (ix >> 1) : (ix >> 1) - 1, kx2 = ix >> 1;
+  const int ky1 = (iy & 1) ? (iy >> 1) : (iy >> 1) - 1, ky2 = iy >> 1;
+  double l = 0.0, mh = 0.0;
+  for (int ky = ky1; ky <= ky2; ++ky) {
+    if (ky < 0 || ky >= d.ny) continue;
+    for (int kx = kx1; kx <= kx2; ++kx) {
+      if (kx < 0 || kx >= d.nx) continue;
+      const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
+      const double w = area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
+      l += w;
+      mh += fmax(0.0, d.H[ky * d.nx + kx]) * w;
+    }
+  }
+  const double m = p.rho_ice * mh;
+  const double mdt = m / p.dt;
+  const size_t nn = d.nn;
+  const double *v = d.vel[cur];
+  d.mass[node] = m;
+  d.nodec[0 * nn + node] = mdt * (1.0 + p.beta);
+  d.nodec[1 * nn + node] = m * p.coriolis_f;
+  d.nodec[2 * nn + node] = mdt * p.beta;
+  d.nodec[3 * nn + node] = fma(mdt, v[node], l * d.tau[node]);
+  d.nodec[4 * nn + node] = fma(mdt, v[nn + node], l * d.tau[nn + node]);
+  d.nodec[5 * nn + node] = l * p.Cw * p.rho_water;
+  (void)has_vo;
+}
+
+// ---- diagnostics ------------------------------------------------------------
+template <int NS>
+__global__ void k_strain_diag(DevState d, int cur) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const double ihx = 1.0 / (d.xline[kx + 1] - d.xline[kx]);
+  const double ihy = 1.0 / (d.yline[ky + 1] - d.yline[ky]);
+  double u[9], v[9];
+  gather9(d.vel[cur], d.nw, kx, ky, u);
+  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+  double E11[NS], E12[NS], E22[NS];
+  strain_dg<NS>(u, v, ihx, ihy, E11, E12, E22);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    d.diag[(size_t)(0 * NS + s) * d.ne + K] = E11[s];
+    d.diag[(size_t)(1 * NS + s) * d.ne + K] = E12[s];
+    d.diag[(size_t)(2 * NS + s) * d.ne + K] = E22[s];
+  }
+}
+
+template <int NS>
+__global__ void k_force_elem(DevState d) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const double hx = d.xline[kx + 1] - d.xline[kx];
+  const double hy = d.yline[ky + 1] - d.yline[ky];
+  double S11[NS], S12[NS], S22[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
+    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
+    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+  }
+  double fx[9], fy[9];
+  element_forces<NS>(S11, S12, S22, hx, hy, fx, fy);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    d.fbuf[(size_t)j * d.ne + K] = fx[j];
+    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+  }
+}
+
+__global__ void k_force_gather(DevState d) {
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= d.nn) return;
+  const int iy = node / d.nw, ix = node - iy * d.nw;
+  double Fx, Fy;
+  gather_force(d.fbuf, d.ne, d.nx, d.ny, ix, iy, Fx, Fy);
+  d.diag[node] = Fx;
+  d.diag[(size_t)d.nn + node] = Fy;
+}
+
+inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
+                           cudaStream_t st) {
+  k_strength<<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
+  k_node_constants<<<blocks(d.nn, 256), 256, 0, st>>>(d, cur, p, has_vo ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
+                                cudaStream_t st, cudaEvent_t *ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  if (d.ns == 3)
+    k_element_f64<3><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
+  else
+    k_element_f64<6><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
+  if (ev) cudaEventRecord(ev[1], st);
+  const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
+  k_node_f64<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, cur, has_vo ? 1 : 0);
+  if (ev) cudaEventRecord(ev[2], st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st) {
+  if (d.ns == 3)
+    k_strain_diag<3><<<blocks(d.ne, 128), 128, 0, st>>>(d, cur);
+  else
+    k_strain_diag<6><<<blocks(d.ne, 128), 128, 0, st>>>(d, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_diag(const DevState &d, cudaStream_t st) {
+  if (d.ns == 3)
+    k_force_elem<3><<<blocks(d.ne, 128), 128, 0, st>>>(d);
+  else
+    k_force_elem<6><<<blocks(d.ne, 128), 128, 0, st>>>(d);
+  k_force_gather<<<blocks(d.nn, 256), 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace mevp

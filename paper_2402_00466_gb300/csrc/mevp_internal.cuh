@@ -1,0 +1,61 @@
+// mevp_internal.cuh -- internal data structures and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/mevp.h"
+
+struct mevp_mesh {
+  int nx = 0, ny = 0;
+  std::vector<double> xline;  // nx+1 vertex x coordinates (rectilinear mesh)
+  std::vector<double> yline;  // ny+1 vertex y coordinates
+};
+
+namespace mevp {
+
+// Scalar constants of the stress update, derived once from mevp_params.
+struct Rheo {
+  double dmin2;  // Delta_min^2
+  double k_sq;   // 1 + 1/e^2        (5/4 at e = 2)
+  double k_mix;  // 2 (1 - 1/e^2)    (3/2)
+  double k_sh;   // 4/e^2            (1)
+  double c_a;    // (1 + 1/e^2)/2    (5/8)
+  double c_b;    // (1 - 1/e^2)/2    (3/8)
+  double c_s;    // 1/e^2            (1/4)
+  double ainv;   // 1/alpha
+  double fac;    // 1 - 1/alpha
+};
+
+// Device view of a state (all pointers into the workspace).
+struct DevState {
+  int nx, ny, ne, nw, nh, nn, ns, prec;
+  const double *xline, *yline;
+  double *vel[2];      // [2][nn] ping-pong
+  double *S;           // FP64: [3][ns][ne]
+  float *S32;          // mixed: [3][ns][ne]
+  double *H, *A;       // [ne]
+  double *tau;         // [2][nn]
+  double *vo;          // [2][nn]
+  double *Pe;          // [ne] ice strength per element
+  double *nodec;       // [6][nn] cA, cB, cK, qx, qy, cD
+  double *mass;        // [nn]
+  double *fbuf;        // FP64: [18][ne] per-element nodal forces (scratch)
+  float *fbuf32;       // mixed: [18][ne]
+  double *diag;        // [3][ns][ne] or [2][nn] diagnostic output
+};
+
+// Launchers (return cudaGetLastError of the launch).
+cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
+                           cudaStream_t st);
+// ev: NULL, or 3 events recorded before the element kernel, between the
+// two kernels and after the node kernel.
+cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
+                                cudaStream_t st, cudaEvent_t *ev);
+cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_force_diag(const DevState &d, cudaStream_t st);
+
+}  // namespace mevp

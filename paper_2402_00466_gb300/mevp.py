@@ -1,0 +1,309 @@
+"""Thin Python binding of libmevp.so (the C ABI in include/mevp.h).
+
+Argument marshalling only: every step of the mEVP subcycle runs in the CUDA
+kernels behind the C ABI.  Functions carry the C names; ``State`` bundles a
+mesh, a state and its device workspace (a torch uint8 tensor, so device
+memory comes from torch's caching allocator) on torch's current stream.
+
+There is no CPU fallback: if the library cannot be built or loaded, or no
+CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MEVP_FP64, MEVP_MIXED = 0, 1
+FIELDS = dict(U=0, V=1, S11=2, S12=3, S22=4, E11=5, E12=6, E22=7, FORCE_X=8, FORCE_Y=9, H=10,
+              A=11, NODAL_MASS=12)
+ERRORS = {-1: "MEVP_ERR_ARG", -2: "MEVP_ERR_CUDA", -3: "MEVP_ERR_OOM", -4: "MEVP_ERR_STATE",
+          -5: "MEVP_ERR_NAN", -6: "MEVP_ERR_TIMEOUT", -7: "MEVP_ERR_UNSUPPORTED"}
+PARAM_NAMES = ("Pstar", "C", "e", "DeltaMin", "alpha", "beta", "dt", "rho_ice", "rho_water",
+               "Cw", "coriolis_f")
+
+
+class MevpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mevp_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in PARAM_NAMES]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load libmevp.so (building it with nvcc first if missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_stale else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libmevp.so not found at {path}; run paper_2402_00466_gb300.build")
+        lib = ctypes.CDLL(path)
+        vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        dp = ctypes.POINTER(ctypes.c_double)
+        pvp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "mevp_mesh_create": (i, [i, i, d, d, vp, pvp]),
+            "mevp_mesh_destroy": (None, [vp]),
+            "mevp_state_workspace_bytes": (i, [vp, i, i, i, ctypes.POINTER(sz)]),
+            "mevp_state_create": (i, [vp, i, i, i, vp, vp, sz, pvp]),
+            "mevp_state_destroy": (None, [vp]),
+            "mevp_set_params": (i, [vp, ctypes.POINTER(mevp_params)]),
+            "mevp_set_ice": (i, [vp, vp, vp, i]),
+            "mevp_set_forcing": (i, [vp, vp, vp, i]),
+            "mevp_set_velocity": (i, [vp, vp, i]),
+            "mevp_set_stress": (i, [vp, vp, i]),
+            "mevp_begin_step": (i, [vp]),
+            "mevp_run_subcycles": (i, [vp, i]),
+            "mevp_read_field": (i, [vp, i, vp, sz, i]),
+            "mevp_sync": (i, [vp]),
+            "mevp_timing_enable": (i, [vp, i]),
+            "mevp_timing_read": (i, [vp, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_longlong)]),
+            "mevp_last_error": (ctypes.c_char_p, []),
+            "mevp_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _ = dp
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise MevpError(rc, mevp_last_error())
+
+
+def mevp_last_error() -> str:
+    return load().mevp_last_error().decode()
+
+
+def mevp_version() -> str:
+    return load().mevp_version().decode()
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor of float64."""
+    if a is None:
+        return None, 0, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        if a.dtype != torch.float64:
+            raise TypeError("expected a float64 tensor")
+        a = a.contiguous()
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+def mevp_mesh_create(nx: int, ny: int, Lx: float = 0.0, Ly: float = 0.0, vertex_xy=None):
+    out = ctypes.c_void_p()
+    xy = None if vertex_xy is None else np.ascontiguousarray(vertex_xy, dtype=np.float64)
+    _check(load().mevp_mesh_create(int(nx), int(ny), float(Lx), float(Ly),
+                                   None if xy is None else ctypes.c_void_p(xy.ctypes.data),
+                                   ctypes.byref(out)))
+    return out
+
+
+def mevp_mesh_destroy(mesh):
+    load().mevp_mesh_destroy(mesh)
+
+
+def mevp_state_workspace_bytes(mesh, n_stress: int, n_adv: int, precision: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().mevp_state_workspace_bytes(mesh, n_stress, n_adv, precision, ctypes.byref(b)))
+    return b.value
+
+
+def mevp_state_create(mesh, n_stress, n_adv, precision, stream, workspace, workspace_bytes):
+    out = ctypes.c_void_p()
+    _check(load().mevp_state_create(mesh, n_stress, n_adv, precision, ctypes.c_void_p(stream),
+                                    ctypes.c_void_p(workspace), workspace_bytes,
+                                    ctypes.byref(out)))
+    return out
+
+
+def mevp_state_destroy(state):
+    load().mevp_state_destroy(state)
+
+
+def mevp_set_params(state, params: dict):
+    p = mevp_params(**{k: float(params[k]) for k in PARAM_NAMES})
+    _check(load().mevp_set_params(state, ctypes.byref(p)))
+
+
+def mevp_set_ice(state, H, A):
+    ph, dh, kh = _ptr(H)
+    pa, da, ka = _ptr(A)
+    if dh != da:
+        raise ValueError("H and A must both be host or both device data")
+    _check(load().mevp_set_ice(state, ph, pa, dh))
+
+
+def mevp_set_forcing(state, tau, v_ocean=None):
+    pt, dt, kt = _ptr(tau)
+    po, do, ko = _ptr(v_ocean)
+    if v_ocean is not None and do != dt:
+        raise ValueError("tau and v_ocean must both be host or both device data")
+    _check(load().mevp_set_forcing(state, pt, po, dt))
+
+
+def mevp_set_velocity(state, uv):
+    p, dev, k = _ptr(uv)
+    _check(load().mevp_set_velocity(state, p, dev))
+
+
+def mevp_set_stress(state, S):
+    p, dev, k = _ptr(S)
+    _check(load().mevp_set_stress(state, p, dev))
+
+
+def mevp_begin_step(state):
+    _check(load().mevp_begin_step(state))
+
+
+def mevp_run_subcycles(state, n: int):
+    _check(load().mevp_run_subcycles(state, int(n)))
+
+
+def mevp_read_field(state, field, out):
+    """Copy field (name or enum) into ``out`` (numpy float64 or torch float64)."""
+    f = FIELDS[field] if isinstance(field, str) else int(field)
+    if hasattr(out, "data_ptr"):
+        if not out.is_contiguous():
+            raise ValueError("out must be contiguous")
+        _check(load().mevp_read_field(state, f, ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                      int(out.is_cuda)))
+    else:
+        if out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array")
+        _check(load().mevp_read_field(state, f, ctypes.c_void_p(out.ctypes.data), out.size, 0))
+    return out
+
+
+def mevp_sync(state):
+    _check(load().mevp_sync(state))
+
+
+def mevp_timing_enable(state, on: bool):
+    _check(load().mevp_timing_enable(state, int(bool(on))))
+
+
+def mevp_timing_read(state):
+    """{'element': (ms, launches), 'node': (ms, launches)} since the last read."""
+    ms = (ctypes.c_double * 2)()
+    n = (ctypes.c_longlong * 2)()
+    _check(load().mevp_timing_read(state, ms, n))
+    return {"element": (ms[0], n[0]), "node": (ms[1], n[1])}
+
+
+class State:
+    """A mesh + state + torch-owned device workspace on torch's current stream.
+
+    Host inputs are numpy arrays in the external layouts of include/mevp.h;
+    device inputs are CUDA float64 tensors.
+    """
+
+    def __init__(self, nx, ny, n_stress, *, L=None, vertex_xy=None, n_adv=1,
+                 precision="fp64", params=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("mevp needs a CUDA device (no CPU fallback)")
+        load()
+        self.nx, self.ny, self.n_stress, self.n_adv = nx, ny, n_stress, n_adv
+        self.ne = nx * ny
+        self.nn = (2 * nx + 1) * (2 * ny + 1)
+        self.precision = {"fp64": MEVP_FP64, "mixed": MEVP_MIXED}[precision]
+        Lx = Ly = float(L if L is not None else 0.0)
+        self.mesh = mevp_mesh_create(nx, ny, Lx, Ly, vertex_xy)
+        self.state = None
+        nbytes = mevp_state_workspace_bytes(self.mesh, n_stress, n_adv, self.precision)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.state = mevp_state_create(self.mesh, n_stress, n_adv, self.precision,
+                                       self.stream.cuda_stream, aligned, nbytes)
+        if params is not None:
+            mevp_set_params(self.state, params)
+
+    def close(self):
+        if getattr(self, "state", None) is not None:
+            mevp_state_destroy(self.state)
+            self.state = None
+        if getattr(self, "mesh", None) is not None:
+            mevp_mesh_destroy(self.mesh)
+            self.mesh = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # thin forwards
+    def set_params(self, p): mevp_set_params(self.state, p)
+    def set_ice(self, H, A): mevp_set_ice(self.state, H, A)
+    def set_forcing(self, tau, v_ocean=None): mevp_set_forcing(self.state, tau, v_ocean)
+    def set_velocity(self, uv): mevp_set_velocity(self.state, uv)
+    def set_stress(self, S): mevp_set_stress(self.state, S)
+    def begin_step(self): mevp_begin_step(self.state)
+    def run_subcycles(self, n): mevp_run_subcycles(self.state, n)
+    def sync(self): mevp_sync(self.state)
+    def timing_enable(self, on=True): mevp_timing_enable(self.state, on)
+    def timing_read(self): return mevp_timing_read(self.state)
+
+    def field_shape(self, field):
+        f = FIELDS[field] if isinstance(field, str) else int(field)
+        if f in (0, 1, 8, 9, 12):
+            return (self.nn,)
+        if f in (10, 11):
+            return (self.n_adv, self.ne)
+        return (self.n_stress, self.ne)
+
+    def read(self, field, device=False):
+        shape = self.field_shape(field)
+        if device:
+            import torch
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        else:
+            out = np.empty(shape, dtype=np.float64)
+        return mevp_read_field(self.state, field, out)
+
+    def velocity(self):
+        return np.stack([self.read("U"), self.read("V")])
+
+    def stress(self):
+        return np.stack([self.read("S11"), self.read("S12"), self.read("S22")])
+
+    def strain(self):
+        return np.stack([self.read("E11"), self.read("E12"), self.read("E22")])
+
+    def force(self):
+        return np.stack([self.read("FORCE_X"), self.read("FORCE_Y")])

@@ -1,0 +1,97 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/mevp.h declares, and its host-only calls validate arguments."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2402_00466_gb300 import mevp
+from paper_2402_00466_gb300 import build as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "mevp.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"MEVP_API\s+[\w\s\*]*?\b(mevp_\w+)\s*\(", src)))
+
+
+def test_header_declares_expected_api():
+    names = declared_symbols()
+    for n in ("mevp_mesh_create", "mevp_state_create", "mevp_set_params", "mevp_set_ice",
+              "mevp_set_forcing", "mevp_set_velocity", "mevp_set_stress", "mevp_begin_step",
+              "mevp_run_subcycles", "mevp_read_field", "mevp_sync", "mevp_last_error",
+              "mevp_state_destroy", "mevp_mesh_destroy", "mevp_state_workspace_bytes"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = mevp.load()
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+    # and the exported dynamic symbol table has no stray mevp_ entries
+    out = os.popen(f"nm -D --defined-only {B.LIB}").read()
+    exported = sorted(set(re.findall(r" T (mevp_\w+)", out)))
+    assert exported == declared_symbols()
+
+
+def test_version_string():
+    assert "sm_103a" in mevp.mevp_version()
+
+
+def test_mesh_create_validation():
+    with pytest.raises(mevp.MevpError) as e:
+        mevp.mevp_mesh_create(0, 4, 1.0, 1.0)
+    assert e.value.code == -1 and "nx" in str(e.value)
+    with pytest.raises(mevp.MevpError):
+        mevp.mevp_mesh_create(4, 4, -1.0, 1.0)
+    # non-rectilinear vertices are valid input this build does not handle
+    xy = np.zeros((9, 2))
+    for j in range(3):
+        for i in range(3):
+            xy[j * 3 + i] = (i * 1.0, j * 1.0)
+    xy[4, 0] += 0.1
+    with pytest.raises(mevp.MevpError) as e:
+        mevp.mevp_mesh_create(2, 2, 0, 0, xy)
+    assert e.value.code == -7
+    xy[4, 0] -= 0.1
+    m = mevp.mevp_mesh_create(2, 2, 0, 0, xy)
+    mevp.mevp_mesh_destroy(m)
+    mevp.mevp_mesh_destroy(None)  # destroying NULL is a no-op
+
+
+def test_workspace_bytes_validation():
+    m = mevp.mevp_mesh_create(8, 4, 1e3, 1e3)
+    try:
+        b3 = mevp.mevp_state_workspace_bytes(m, 3, 1, 0)
+        b6 = mevp.mevp_state_workspace_bytes(m, 6, 1, 0)
+        assert b6 > b3 > 0 and b6 % 256 == 0
+        for bad in (1, 2, 4, 8):
+            with pytest.raises(mevp.MevpError):
+                mevp.mevp_state_workspace_bytes(m, bad, 1, 0)
+        with pytest.raises(mevp.MevpError) as e:
+            mevp.mevp_state_workspace_bytes(m, 6, 3, 0)
+        assert e.value.code == -7
+        with pytest.raises(mevp.MevpError):
+            mevp.mevp_state_workspace_bytes(m, 6, 1, 5)
+    finally:
+        mevp.mevp_mesh_destroy(m)
+
+
+def test_null_state_calls_fail_cleanly():
+    lib = mevp.load()
+    assert lib.mevp_run_subcycles(None, 1) == -1
+    assert "NULL" in mevp.mevp_last_error()
+    assert lib.mevp_begin_step(None) == -1
+    lib.mevp_state_destroy(None)
+
+
+def test_oracle_is_not_linked_into_the_library():
+    out = os.popen(f"nm -D {B.LIB}").read()
+    assert "orc_" not in out
+    src_dir = os.path.join(os.path.dirname(B.LIB), "..", "csrc")
+    for f in os.listdir(src_dir):
+        assert "oracle" not in open(os.path.join(src_dir, f)).read().lower() or f.endswith(".md")

