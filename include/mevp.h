@@ -175,6 +175,50 @@ MEVP_API int mevp_read_field(mevp_state *state, int field, double *dst, size_t c
 /* Wait for all work on the state's stream; reports asynchronous errors. */
 MEVP_API int mevp_sync(mevp_state *state);
 
+/* Size of the static device scratch used by mevp_run_subcycles_noalloc. */
+#define MEVP_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* mevp_run_subcycles_noalloc -- one outer step (v^n := vel at entry) of n
+ * mEVP subcycles, in place, WITHOUT allocating any device memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate: a host model or coupler that owns a fixed device-memory
+ * pool and hands this library only raw device pointers, a language runtime
+ * with no binding to a CUDA allocator, or a time-critical loop that must
+ * not call cudaMalloc/cudaFree because they can synchronise the device and
+ * stall other streams.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Results match mevp_begin_step + mevp_run_subcycles on a
+ * state with the same inputs (FP64 only).
+ *
+ * All arrays are device memory of the current device, in the external
+ * layouts above: xline [nx+1] and yline [ny+1] are the strictly increasing
+ * vertex coordinates of a rectilinear mesh; H, A [N_e] (DG0); tau [2][N_n];
+ * v_ocean [2][N_n] or NULL (ocean at rest); vel [2][N_n] and
+ * S [3][n_stress][N_e] are read and overwritten.  params is host memory.
+ * Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without waiting.
+ *
+ * Scratch: a file-scope static device array of MEVP_NOALLOC_SCRATCH_BYTES
+ * (8 MiB), which every process that loads the library holds on every device
+ * it uses until exit.  A mesh needs 19 N_e + 9 N_n doubles (each region
+ * 256-byte aligned): meshes up to 128 x 128 elements fit; larger ones return
+ * MEVP_ERR_ARG with the sizes in the message.  All calls on a device share
+ * that one array and it keeps the last call's contents; every word a call
+ * reads is written by the same call first, so nothing has to be cleared.
+ * Calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on the scratch: serialise them, e.g. on one stream.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before any stream capture on the device.  Errors: MEVP_ERR_ARG
+ * for bad sizes, parameters or non-device pointers; MEVP_ERR_CUDA for a
+ * failed lookup or launch. */
+MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp_params *params,
+                                        const double *xline, const double *yline,
+                                        const double *H, const double *A, const double *tau,
+                                        const double *v_ocean, double *vel, double *S, int n,
+                                        void *cuda_stream);
+
 /* Per-kernel timing with CUDA events, for benchmarks.  With on != 0 every
  * launch of mevp_run_subcycles is bracketed by events on the state's stream.
  * mevp_timing_read waits for the stream and returns, for kernel 0 (element

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -482,3 +483,172 @@ int mevp_sync(mevp_state *s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mevp_run_subcycles_noalloc: the subcycle loop for callers that cannot
+// allocate device memory.  Its scratch (per-element ice strength, per-node
+// constants and mass, per-element nodal forces, and the second velocity
+// buffer) lives in one file-scope device array that every call shares.
+// ---------------------------------------------------------------------------
+static constexpr size_t kNoAllocScratchBytes = (size_t)MEVP_NOALLOC_SCRATCH_BYTES;
+
+// One array per process and device, held from module load until exit.  Host
+// code must not use its name as an address (it is a host-side stand-in);
+// the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// Scratch layout for an nx x ny mesh: offsets (bytes, 256-aligned) of the
+// regions and the total.
+struct NoAllocLayout {
+  size_t Pe, nodec, mass, fbuf, vel2, total;
+};
+
+NoAllocLayout noalloc_layout(size_t ne, size_t nn) {
+  NoAllocLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L.Pe = take(sizeof(double) * ne);
+  L.nodec = take(sizeof(double) * 6 * nn);
+  L.mass = take(sizeof(double) * nn);
+  L.fbuf = take(sizeof(double) * 18 * ne);
+  L.vel2 = take(sizeof(double) * 2 * nn);
+  L.total = off;
+  return L;
+}
+
+// Device address of the scratch array on the current device (looked up once
+// per device, with that device current).
+int noalloc_scratch(int device, void **out) {
+  if (device < 0 || device >= kMaxDevices)
+    return fail(MEVP_ERR_UNSUPPORTED, "run_subcycles_noalloc: device index %d >= %d", device,
+                kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return MEVP_OK;
+}
+
+// True when p is device (or managed) memory usable from `device`.
+bool is_device_ptr(const void *p, int device) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) &&
+         a.device == device;
+}
+
+}  // namespace
+
+extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp_params *p,
+                                          const double *xline, const double *yline,
+                                          const double *H, const double *A, const double *tau,
+                                          const double *v_ocean, double *vel, double *S, int n,
+                                          void *cuda_stream) {
+  if (nx < 1 || ny < 1)
+    return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: nx=%d ny=%d must be >= 1", nx, ny);
+  if (n_stress != 3 && n_stress != 6)
+    return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: n_stress=%d must be 3 or 6", n_stress);
+  if (n < 0) return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: n=%d < 0", n);
+  if (!p) return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: params is NULL");
+  const long long nn_ll = (2LL * nx + 1) * (2LL * ny + 1);
+  if (nn_ll >= (1LL << 31) - 1) return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: mesh too large");
+  const size_t ne = (size_t)nx * ny, nn = (size_t)nn_ll;
+  const NoAllocLayout L = noalloc_layout(ne, nn);
+  if (L.total > kNoAllocScratchBytes)
+    return fail(MEVP_ERR_ARG,
+                "run_subcycles_noalloc: a %dx%d mesh needs %zu scratch bytes, more than the "
+                "%zu-byte static scratch (at most 19*N_e + 9*N_n doubles; 128x128 fits)",
+                nx, ny, L.total, kNoAllocScratchBytes);
+  // parameters: same admissible ranges as mevp_set_params
+  const double pv[] = {p->Pstar, p->C,       p->e,      p->DeltaMin, p->alpha,      p->beta,
+                       p->dt,    p->rho_ice, p->rho_water, p->Cw,    p->coriolis_f};
+  for (double x : pv)
+    if (!std::isfinite(x)) return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: non-finite parameter");
+  if (p->Pstar < 0 || p->C < 0 || !(p->e > 0) || !(p->DeltaMin > 0) || !(p->alpha >= 1) ||
+      !(p->beta >= 0) || !(p->dt > 0) || !(p->rho_ice > 0) || p->rho_water < 0 || p->Cw < 0)
+    return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: parameter out of range");
+  int device = -1;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: cudaGetDevice");
+  const void *ptrs[] = {xline, yline, H, A, tau, vel, S};
+  const char *names[] = {"xline", "yline", "H", "A", "tau", "vel", "S"};
+  for (int i = 0; i < 7; ++i)
+    if (!ptrs[i] || !is_device_ptr(ptrs[i], device))
+      return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: %s must be device memory of device %d",
+                  names[i], device);
+  if (v_ocean && !is_device_ptr(v_ocean, device))
+    return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: v_ocean must be device memory or NULL");
+  void *scratch = nullptr;
+  int rc = noalloc_scratch(device, &scratch);
+  if (rc) return rc;
+
+  const double ie2 = 1.0 / (p->e * p->e);
+  Rheo r{};
+  r.dmin2 = p->DeltaMin * p->DeltaMin;
+  r.k_sq = 1.0 + ie2;
+  r.k_mix = 2.0 * (1.0 - ie2);
+  r.k_sh = 4.0 * ie2;
+  r.c_a = 0.5 * (1.0 + ie2);
+  r.c_b = 0.5 * (1.0 - ie2);
+  r.c_s = ie2;
+  r.ainv = 1.0 / p->alpha;
+  r.fac = 1.0 - r.ainv;
+
+  char *b = (char *)scratch;
+  DevState d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.ne = (int)ne;
+  d.nw = 2 * nx + 1;
+  d.nh = 2 * ny + 1;
+  d.nn = (int)nn;
+  d.ns = n_stress;
+  d.prec = MEVP_FP64;
+  d.xline = xline;
+  d.yline = yline;
+  d.vel[0] = vel;
+  d.vel[1] = (double *)(b + L.vel2);
+  d.S = S;
+  d.H = (double *)H;
+  d.A = (double *)A;
+  d.tau = (double *)tau;
+  d.vo = (double *)v_ocean;
+  d.Pe = (double *)(b + L.Pe);
+  d.nodec = (double *)(b + L.nodec);
+  d.mass = (double *)(b + L.mass);
+  d.fbuf = (double *)(b + L.fbuf);
+  const bool has_vo = v_ocean != nullptr;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // v^n := vel at entry; every scratch word is written before it is read, so
+  // nothing in the shared array has to be cleared first.
+  e = mevp::launch_prepare(d, *p, has_vo, 0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: prepare launch");
+  int cur = 0;
+  for (int i = 0; i < n; ++i) {
+    e = mevp::launch_subcycle_f64(d, r, has_vo, cur, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: subcycle launch");
+    cur ^= 1;
+  }
+  if (cur == 1) {  // odd count: the result sits in the scratch velocity buffer
+    e = cudaMemcpyAsync(vel, d.vel[1], sizeof(double) * 2 * nn, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: copy back");
+  }
+  return MEVP_OK;
+}

@@ -73,6 +73,8 @@ def load(build_if_stale: bool = True):
             "mevp_run_subcycles": (i, [vp, i]),
             "mevp_read_field": (i, [vp, i, vp, sz, i]),
             "mevp_sync": (i, [vp]),
+            "mevp_run_subcycles_noalloc": (i, [i, i, i, ctypes.POINTER(mevp_params), vp, vp, vp,
+                                               vp, vp, vp, vp, vp, i, vp]),
             "mevp_timing_enable": (i, [vp, i]),
             "mevp_timing_read": (i, [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]),
@@ -202,6 +204,27 @@ def mevp_read_field(state, field, out):
 
 def mevp_sync(state):
     _check(load().mevp_sync(state))
+
+
+def mevp_run_subcycles_noalloc(nx, ny, n_stress, params, xline, yline, H, A, tau, v_ocean,
+                               vel, S, n, stream=None):
+    """One outer step of n subcycles on caller-owned CUDA float64 tensors, with
+    the library allocating nothing (its scratch is a fixed static device
+    array; see include/mevp.h).  vel and S are updated in place."""
+    import torch
+    arrs = dict(xline=xline, yline=yline, H=H, A=A, tau=tau, vel=vel, S=S)
+    if v_ocean is not None:
+        arrs["v_ocean"] = v_ocean
+    for k, t in arrs.items():
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError(f"{k} must be a contiguous CUDA float64 tensor")
+    p = mevp_params(**{k: float(params[k]) for k in PARAM_NAMES})
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    _check(load().mevp_run_subcycles_noalloc(
+        int(nx), int(ny), int(n_stress), ctypes.byref(p), ptr(xline), ptr(yline), ptr(H), ptr(A),
+        ptr(tau), ptr(v_ocean), ptr(vel), ptr(S), int(n), ctypes.c_void_p(stream)))
 
 
 def mevp_timing_enable(state, on: bool):
