@@ -35,9 +35,12 @@ from paper_2402_00466_gb300 import workloads as W  # noqa: E402
 METRIC = "mEVP element-subcycles/s & % HBM peak, FP64 vs mixed at stated field error"
 UNIT = "element-subcycles/s"
 
-# Algorithmic work per element and subcycle (counted from the kernel's
-# operator sparsity; FMA = 2 flops, sqrt and divide = 1 each).
-ELEM_FLOPS = {3: 640, 6: 1362}      # element kernel (strain, stress, element forces)
+# Algorithmic work per element and subcycle of the element kernel, counted
+# from its operator sparsity (FMA = 2 flops, mul/add = 1, rsqrt = 1; zero
+# entries skipped, +-1 entries as adds).  DG2: projected derivatives 268,
+# Gauss evaluation 132, rheology 99, projection 240, update 62, element
+# forces 254.  DG1: 153, 36, 44, 63, 32, 146.
+ELEM_FLOPS = {3: 474, 6: 1055}
 NODE_FLOPS_PER_NODE = 32.5          # node kernel (force gather, velocity update)
 # Algorithmic HBM bytes per element-subcycle: state touched once (stress R+W,
 # ice strength, vertices amortised, 4 nodes x (v R, v W, node constants R)).

@@ -200,8 +200,8 @@ MEVP_API int mevp_sync(mevp_state *state);
  *
  * Scratch: a file-scope static device array of MEVP_NOALLOC_SCRATCH_BYTES
  * (8 MiB), which every process that loads the library holds on every device
- * it uses until exit.  A mesh needs 19 N_e + 9 N_n doubles (each region
- * 256-byte aligned): meshes up to 128 x 128 elements fit; larger ones return
+ * it uses until exit.  A mesh needs 19 N_e + 9 N_n + 2 (nx + ny) doubles
+ * (each region 256-byte aligned): meshes up to 128 x 128 elements fit; larger ones return
  * MEVP_ERR_ARG with the sizes in the message.  All calls on a device share
  * that one array and it keeps the last call's contents; every word a call
  * reads is written by the same call first, so nothing has to be cleared.

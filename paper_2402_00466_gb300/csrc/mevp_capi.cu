@@ -66,7 +66,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t xline, yline, vel0, vel1, S, S32, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, lines, vel0, vel1, S, S32, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       total;
 };
 
@@ -82,6 +82,7 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   };
   L.xline = take(sizeof(double) * (m->nx + 1));
   L.yline = take(sizeof(double) * (m->ny + 1));
+  L.lines = take(sizeof(double) * 2 * (m->nx + m->ny));
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(prec == MEVP_FP64 ? sizeof(double) * 3 * ns * ne : 0);
@@ -260,6 +261,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.prec = precision;
   d.xline = (const double *)(b + L.xline);
   d.yline = (const double *)(b + L.yline);
+  d.lines = (double *)(b + L.lines);
   d.vel[0] = (double *)(b + L.vel0);
   d.vel[1] = (double *)(b + L.vel1);
   d.S = (double *)(b + L.S);
@@ -319,17 +321,7 @@ int mevp_set_params(mevp_state *s, const mevp_params *p) {
   if (p->rho_water < 0 || p->Cw < 0)
     return fail(MEVP_ERR_ARG, "set_params: rho_water, Cw must be >= 0");
   s->prm = *p;
-  const double ie2 = 1.0 / (p->e * p->e);
-  Rheo &r = s->rheo;
-  r.dmin2 = p->DeltaMin * p->DeltaMin;
-  r.k_sq = 1.0 + ie2;
-  r.k_mix = 2.0 * (1.0 - ie2);
-  r.k_sh = 4.0 * ie2;
-  r.c_a = 0.5 * (1.0 + ie2);
-  r.c_b = 0.5 * (1.0 - ie2);
-  r.c_s = ie2;
-  r.ainv = 1.0 / p->alpha;
-  r.fac = 1.0 - r.ainv;
+  s->rheo = mevp::make_rheo(*p);
   s->have_params = true;
   return MEVP_OK;
 }
@@ -506,10 +498,10 @@ void *g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, 
 // Scratch layout for an nx x ny mesh: offsets (bytes, 256-aligned) of the
 // regions and the total.
 struct NoAllocLayout {
-  size_t Pe, nodec, mass, fbuf, vel2, total;
+  size_t lines, Pe, nodec, mass, fbuf, vel2, total;
 };
 
-NoAllocLayout noalloc_layout(size_t ne, size_t nn) {
+NoAllocLayout noalloc_layout(size_t nx, size_t ny, size_t ne, size_t nn) {
   NoAllocLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -517,6 +509,7 @@ NoAllocLayout noalloc_layout(size_t ne, size_t nn) {
     off = align256(off + bytes);
     return o;
   };
+  L.lines = take(sizeof(double) * 2 * (nx + ny));
   L.Pe = take(sizeof(double) * ne);
   L.nodec = take(sizeof(double) * 6 * nn);
   L.mass = take(sizeof(double) * nn);
@@ -570,11 +563,11 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
   const long long nn_ll = (2LL * nx + 1) * (2LL * ny + 1);
   if (nn_ll >= (1LL << 31) - 1) return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: mesh too large");
   const size_t ne = (size_t)nx * ny, nn = (size_t)nn_ll;
-  const NoAllocLayout L = noalloc_layout(ne, nn);
+  const NoAllocLayout L = noalloc_layout((size_t)nx, (size_t)ny, ne, nn);
   if (L.total > kNoAllocScratchBytes)
     return fail(MEVP_ERR_ARG,
                 "run_subcycles_noalloc: a %dx%d mesh needs %zu scratch bytes, more than the "
-                "%zu-byte static scratch (at most 19*N_e + 9*N_n doubles; 128x128 fits)",
+                "%zu-byte static scratch (19*N_e + 9*N_n + 2*(nx+ny) doubles; 128x128 fits)",
                 nx, ny, L.total, kNoAllocScratchBytes);
   // parameters: same admissible ranges as mevp_set_params
   const double pv[] = {p->Pstar, p->C,       p->e,      p->DeltaMin, p->alpha,      p->beta,
@@ -599,17 +592,7 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
   int rc = noalloc_scratch(device, &scratch);
   if (rc) return rc;
 
-  const double ie2 = 1.0 / (p->e * p->e);
-  Rheo r{};
-  r.dmin2 = p->DeltaMin * p->DeltaMin;
-  r.k_sq = 1.0 + ie2;
-  r.k_mix = 2.0 * (1.0 - ie2);
-  r.k_sh = 4.0 * ie2;
-  r.c_a = 0.5 * (1.0 + ie2);
-  r.c_b = 0.5 * (1.0 - ie2);
-  r.c_s = ie2;
-  r.ainv = 1.0 / p->alpha;
-  r.fac = 1.0 - r.ainv;
+  const Rheo r = mevp::make_rheo(*p);
 
   char *b = (char *)scratch;
   DevState d{};
@@ -623,6 +606,7 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
   d.prec = MEVP_FP64;
   d.xline = xline;
   d.yline = yline;
+  d.lines = (double *)(b + L.lines);
   d.vel[0] = vel;
   d.vel[1] = (double *)(b + L.vel2);
   d.S = S;

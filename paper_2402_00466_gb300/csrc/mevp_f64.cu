@@ -20,6 +20,7 @@
 // paper's "on-the-fly map", Sec. 3.2), so no per-element matrices are read.
 // On a rectangle the inverse local mass and the Jacobian cancel, leaving the
 // compile-time reference tables of mevp_ref.cuh scaled by 1/hx, 1/hy.
+#include "mevp_elem.cuh"
 #include "mevp_internal.cuh"
 #include "mevp_ref.cuh"
 
@@ -39,104 +40,21 @@ __device__ __forceinline__ void gather9(const double *__restrict__ f, int nw, in
     for (int a = 0; a < 3; ++a) out[a + 3 * b] = __ldg(base + (size_t)b * nw + a);
 }
 
-// Strain: E_c = M^-1 int phi eps_c(v) on a rectangle hx x hy, through the
-// exact projected reference derivatives (eps12 = (du/dy + dv/dx)/2).
+// Strain coefficients E11, E12, E22 (for the diagnostic read-back):
+// E11 = du/dx, E22 = dv/dy, E12 = (du/dy + dv/dx)/2, projected onto DG.
 template <int NS>
 __device__ __forceinline__ void strain_dg(const double u[9], const double v[9], double ihx,
                                           double ihy, double E11[NS], double E12[NS],
                                           double E22[NS]) {
+  double Uxi[NS], Ueta[NS], Vxi[NS], Veta[NS];
+  ref_derivs<NS>(u, Uxi, Ueta);
+  ref_derivs<NS>(v, Vxi, Veta);
   const double h2x = 0.5 * ihx, h2y = 0.5 * ihy;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    double uxi = -0.0, ueta = -0.0, vxi = -0.0, veta = -0.0;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      const double cx = dxi(s, j), ce = deta(s, j);
-      if (cx != 0.0) {
-        uxi = fma(cx, u[j], uxi);
-        vxi = fma(cx, v[j], vxi);
-      }
-      if (ce != 0.0) {
-        ueta = fma(ce, u[j], ueta);
-        veta = fma(ce, v[j], veta);
-      }
-    }
-    E11[s] = ihx * uxi;
-    E22[s] = ihy * veta;
-    E12[s] = fma(h2y, ueta, h2x * vxi);
-  }
-}
-
-// Stress: Gauss-point evaluation, viscous-plastic law with ice strength P,
-// relaxed update S <- (1 - 1/alpha) S + M^-1 int phi s_vp / alpha.
-template <int NS>
-__device__ __forceinline__ void stress_update(double S11[NS], double S12[NS], double S22[NS],
-                                              const double E11[NS], const double E12[NS],
-                                              const double E22[NS], double P, const Rheo &r) {
-  constexpr int NGP = DgSpace<NS>::NGP;
-  constexpr int NG = NGP * NGP;
-  double a11[NS], a12[NS], a22[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) a11[s] = a12[s] = a22[s] = -0.0;
-  const double halfP = 0.5 * P;
-#pragma unroll
-  for (int g = 0; g < NG; ++g) {
-    double e11 = -0.0, e12 = -0.0, e22 = -0.0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const double ps = psi<NS>(s, g);
-      if (ps != 0.0) {
-        e11 = fma(ps, E11[s], e11);
-        e12 = fma(ps, E12[s], e12);
-        e22 = fma(ps, E22[s], e22);
-      }
-    }
-    const double d2 = r.dmin2 + r.k_sq * (e11 * e11 + e22 * e22) + r.k_mix * e11 * e22 +
-                      r.k_sh * e12 * e12;
-    const double PD = P / sqrt(d2);
-    const double s11 = r.ainv * (PD * (r.c_a * e11 + r.c_b * e22) - halfP);
-    const double s12 = r.ainv * (PD * (r.c_s * e12));
-    const double s22 = r.ainv * (PD * (r.c_a * e22 + r.c_b * e11) - halfP);
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const double q = proj<NS>(s, g);
-      if (q != 0.0) {
-        a11[s] = fma(q, s11, a11[s]);
-        a12[s] = fma(q, s12, a12[s]);
-        a22[s] = fma(q, s22, a22[s]);
-      }
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    S11[s] = fma(r.fac, S11[s], a11[s]);
-    S12[s] = fma(r.fac, S12[s], a12[s]);
-    S22[s] = fma(r.fac, S22[s], a22[s]);
-  }
-}
-
-// Element forces f_j = -int sigma : grad phi_j on a rectangle hx x hy.
-template <int NS>
-__device__ __forceinline__ void element_forces(const double S11[NS], const double S12[NS],
-                                               const double S22[NS], double hx, double hy,
-                                               double fx[9], double fy[9]) {
-#pragma unroll
-  for (int j = 0; j < 9; ++j) {
-    double x1 = -0.0, x2 = -0.0, y1 = -0.0, y2 = -0.0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const double gx = gxi(j, s), ge = geta(j, s);
-      if (gx != 0.0) {
-        x1 = fma(gx, S11[s], x1);
-        y1 = fma(gx, S12[s], y1);
-      }
-      if (ge != 0.0) {
-        x2 = fma(ge, S12[s], x2);
-        y2 = fma(ge, S22[s], y2);
-      }
-    }
-    fx[j] = -fma(hy, x1, hx * x2);
-    fy[j] = -fma(hy, y1, hx * y2);
+    E11[s] = ihx * Uxi[s];
+    E22[s] = ihy * Veta[s];
+    E12[s] = fma(h2y, Ueta[s], h2x * Vxi[s]);
   }
 }
 
@@ -145,14 +63,13 @@ __global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, 
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
   const int ky = K / d.nx, kx = K - ky * d.nx;
-  const double hx = d.xline[kx + 1] - d.xline[kx];
-  const double hy = d.yline[ky + 1] - d.yline[ky];
-  const double ihx = 1.0 / hx, ihy = 1.0 / hy;
+  const double hx = __ldg(d.lines + kx), ihx = __ldg(d.lines + d.nx + kx);
+  const double hy = __ldg(d.lines + 2 * d.nx + ky), ihy = __ldg(d.lines + 2 * d.nx + d.ny + ky);
   double u[9], v[9];
   gather9(d.vel[cur], d.nw, kx, ky, u);
   gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
-  double E11[NS], E12[NS], E22[NS];
-  strain_dg<NS>(u, v, ihx, ihy, E11, E12, E22);
+  double Pc[NS], Qc[NS], Gc[NS];
+  strain_invariants<NS>(u, v, ihx, ihy, r.ie, Pc, Qc, Gc);
   double S11[NS], S12[NS], S22[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -160,7 +77,8 @@ __global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, 
     S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
     S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
   }
-  stress_update<NS>(S11, S12, S22, E11, E12, E22, __ldg(d.Pe + K), r);
+  const double Ph = __ldg(d.Pe + K) * r.hainv;
+  relax_stress<NS>(S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     d.S[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
@@ -168,7 +86,7 @@ __global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, 
     d.S[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
   }
   double fx[9], fy[9];
-  element_forces<NS>(S11, S12, S22, hx, hy, fx, fy);
+  element_forces_t<NS>(S11, S12, S22, hx, hy, fx, fy);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     d.fbuf[(size_t)j * d.ne + K] = fx[j];
@@ -285,6 +203,21 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_f64(DevState d, int cur, in
 }
 
 // ---- outer-step preparation ----------------------------------------------
+// Element widths and their inverses per mesh column / row.
+__global__ void k_mesh_lines(DevState d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.nx) {
+    const double h = d.xline[i + 1] - d.xline[i];
+    d.lines[i] = h;
+    d.lines[d.nx + i] = 1.0 / h;
+  } else if (i < d.nx + d.ny) {
+    const int j = i - d.nx;
+    const double h = d.yline[j + 1] - d.yline[j];
+    d.lines[2 * d.nx + j] = h;
+    d.lines[2 * d.nx + d.ny + j] = 1.0 / h;
+  }
+}
+
 __global__ void k_strength(DevState d, double Pstar, double C) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
@@ -362,7 +295,7 @@ __global__ void k_force_elem(DevState d) {
     S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
   }
   double fx[9], fy[9];
-  element_forces<NS>(S11, S12, S22, hx, hy, fx, fy);
+  element_forces_t<NS>(S11, S12, S22, hx, hy, fx, fy);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     d.fbuf[(size_t)j * d.ne + K] = fx[j];
@@ -386,6 +319,7 @@ inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
 cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                            cudaStream_t st) {
+  k_mesh_lines<<<blocks(d.nx + d.ny, 256), 256, 0, st>>>(d);
   k_strength<<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
   k_node_constants<<<blocks(d.nn, 256), 256, 0, st>>>(d, cur, p, has_vo ? 1 : 0);
   return cudaGetLastError();

@@ -28,12 +28,33 @@ struct Rheo {
   double c_s;    // 1/e^2            (1/4)
   double ainv;   // 1/alpha
   double fac;    // 1 - 1/alpha
+  double ie;     // 1/e
+  double hainv;  // 1/(2 alpha)
 };
+
+// Derive the stress-update constants from the parameters.
+inline Rheo make_rheo(const mevp_params &p) {
+  Rheo r{};
+  const double ie2 = 1.0 / (p.e * p.e);
+  r.dmin2 = p.DeltaMin * p.DeltaMin;
+  r.k_sq = 1.0 + ie2;
+  r.k_mix = 2.0 * (1.0 - ie2);
+  r.k_sh = 4.0 * ie2;
+  r.c_a = 0.5 * (1.0 + ie2);
+  r.c_b = 0.5 * (1.0 - ie2);
+  r.c_s = ie2;
+  r.ainv = 1.0 / p.alpha;
+  r.fac = 1.0 - r.ainv;
+  r.ie = 1.0 / p.e;
+  r.hainv = 0.5 / p.alpha;
+  return r;
+}
 
 // Device view of a state (all pointers into the workspace).
 struct DevState {
   int nx, ny, ne, nw, nh, nn, ns, prec;
   const double *xline, *yline;
+  double *lines;       // [hx: nx][1/hx: nx][hy: ny][1/hy: ny], from the mesh lines
   double *vel[2];      // [2][nn] ping-pong
   double *S;           // FP64: [3][ns][ne]
   float *S32;          // mixed: [3][ns][ne]
