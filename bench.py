@@ -180,6 +180,118 @@ def run_reference(a):
     return 0
 
 
+# Algorithmic HBM bytes per element per launch of the mixed kernels (two
+# launches per subcycle): element kernel = stress R+W (FP32) + ice strength +
+# velocity pairs of ~4 nodes (16 B each) + element forces W (FP32);
+# node kernel = element forces R + ~4 nodes x (velocity R + W + 4 constants).
+MIXED_ELEM_BYTES = {3: 72 + 4 + 64 + 72, 6: 144 + 4 + 64 + 72}
+MIXED_NODE_BYTES = 72 + 4 * (16 + 16 + 16)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# per-kernel CUDA events on every 10th subcycle of the timed region (events
+# between every pair of launches would add ~2-4 us per subcycle)
+TIMING_STRIDE = 10
+
+
+def measure(mevp, torch, barrier, ws, case, precision, steps, warmup, flush, timing=True):
+    """Time `steps` outer steps (begin_step + n_sub subcycles) after `warmup`,
+    L2 flushed between steps.  Returns value, step times and kernel timing."""
+    nx, ny, ns, n_sub = case["nx"], case["ny"], case["n_s"], case["n_sub"]
+    ne = nx * ny
+    st = mevp.State(nx, ny, ns, vertex_xy=case["xy"], precision=precision,
+                    params=case["params"])
+    st.set_ice(case["H"], case["A"])
+    st.set_forcing(case["tau"])
+    st.set_velocity(case["vel0"])
+    st.set_stress(case["S0"])
+
+    def step():
+        st.begin_step()
+        st.run_subcycles(n_sub)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    if timing:
+        st.timing_enable(TIMING_STRIDE)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    t0 = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()  # L2 flush between timed steps, outside the step events
+        evs[k][0].record()
+        step()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    kt = st.timing_read() if timing else None
+    st.timing_enable(0)
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in evs)
+    return dict(state=st, total_ms=total_ms, kt=kt, wall=wall,
+                value=ws * ne * n_sub * steps / (total_ms / 1e3))
+
+
+def roofline_for(precision, case, kt, total_ms, steps):
+    ns, ne, n_sub = case["n_s"], case["nx"] * case["ny"], case["n_sub"]
+    el_ms, el_n = kt["element"]
+    nd_ms, nd_n = kt["node"]
+    el_s = el_ms / max(el_n, 1) / 1e3
+    nd_s = nd_ms / max(nd_n, 1) / 1e3
+    hbm_peak, hbm_kind = load_peaks()
+    sub_s = (total_ms / 1e3) / (n_sub * steps)
+    common = {"element_kernel_ms_mean": el_s * 1e3, "node_kernel_ms_mean": nd_s * 1e3,
+              "element_share_of_subcycle": el_ms / max(el_ms + nd_ms, 1e-12)}
+    if precision == "fp64":
+        ach = ELEM_FLOPS[ns] * ne / el_s / 1e12
+        bytes_sub = HBM_BYTES.get(("fp64", ns), 0) * ne
+        return dict({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": f"k_element_f64<{ns}>",
+                     "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
+                     "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
+                     "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak}, **common)
+    # mixed: HBM-bound; the dominant kernel is the one with the larger share
+    eb, nb = MIXED_ELEM_BYTES[ns] * ne, MIXED_NODE_BYTES * ne
+    if el_ms >= nd_ms:
+        name, ach = f"k_element_mix<{ns}>", eb / el_s / 1e9
+    else:
+        name, ach = "k_node_mix", nb / nd_s / 1e9
+    return dict({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                 "frac": ach / hbm_peak, "traffic": None, "kernel": name,
+                 "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                 "element_GBps": eb / el_s / 1e9, "node_GBps": nb / nd_s / 1e9,
+                 "subcycle_GBps": (eb + nb) / sub_s / 1e9,
+                 "subcycle_frac": (eb + nb) / sub_s / 1e9 / hbm_peak,
+                 "element_fp32_TFLOPs": ELEM_FLOPS[ns] * ne / el_s / 1e12,
+                 "fp32_peak_TFLOPs": FP32_PEAK_TFLOPS}, **common)
+
+
+def field_error(mevp, case, n_sub, alpha_beta):
+    """Mixed vs FP64 GPU path (the FP64 path matches the oracle to 1e-11) after
+    n_sub subcycles at a stable alpha = beta; relative L2 / max errors."""
+    p = dict(case["params"], alpha=alpha_beta, beta=alpha_beta)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        with mevp.State(case["nx"], case["ny"], case["n_s"], vertex_xy=case["xy"],
+                        precision=prec, params=p) as st:
+            st.set_ice(case["H"], case["A"])
+            st.set_forcing(case["tau"])
+            st.set_velocity(case["vel0"])
+            st.set_stress(case["S0"])
+            st.begin_step()
+            st.run_subcycles(n_sub)
+            out[prec] = (st.velocity(), st.stress())
+    res = {"n_sub": n_sub, "alpha_beta": alpha_beta, "reference": "FP64 GPU path"}
+    for i, f in enumerate(("velocity", "stress")):
+        x, r = out["mixed"][i], out["fp64"][i]
+        res[f + "_rel_l2"] = float(np.linalg.norm(x - r) / np.linalg.norm(r))
+        res[f + "_rel_max"] = float(np.abs(x - r).max() / np.abs(r).max())
+    return res
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -201,67 +313,20 @@ def run_ours(a):
     case = W.make_case(a.workload)
     nx, ny, ns, n_sub = case["nx"], case["ny"], case["n_s"], case["n_sub"]
     ne, nn, _ = W.sizes(nx, ny)
-    st = mevp.State(nx, ny, ns, vertex_xy=case["xy"], precision=a.precision,
-                    params=case["params"])
-    st.set_ice(case["H"], case["A"])
-    st.set_forcing(case["tau"])
-    st.set_velocity(case["vel0"])
-    st.set_stress(case["S0"])
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
 
-    def step():
-        st.begin_step()
-        st.run_subcycles(n_sub)
-
-    for _ in range(a.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
     clocks = Clocks(dev)
-    barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    st.timing_enable(True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(a.steps)]
-    t_wall0 = time.perf_counter()
-    for k in range(a.steps):
-        flush.zero_()  # L2 flush between timed steps, outside the step events
-        evs[k][0].record()
-        step()
-        evs[k][1].record()
-    torch.cuda.synchronize()
-    barrier()
-    t_wall = time.perf_counter() - t_wall0
-    kt = st.timing_read()
-    st.timing_enable(False)
+    m = measure(mevp, torch, barrier, ws, case, a.precision, a.steps, a.warmup, flush)
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in evs]
-    total_ms = sum(step_ms)
+    st = m["state"]
+    total_ms = m["total_ms"]
     if ws > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    units = ws * ne * n_sub * a.steps
-    value = units / (total_ms / 1e3)
-
-    # dominant kernel: the element kernel; achieved = algorithmic flops per launch / mean launch time
-    el_ms, el_n = kt["element"]
-    nd_ms, nd_n = kt["node"]
-    el_avg_s = el_ms / max(el_n, 1) / 1e3
-    flops_launch = ELEM_FLOPS[ns] * ne
-    achieved_tflops = flops_launch / el_avg_s / 1e12
-    hbm_peak, hbm_kind = load_peaks()
-    bytes_sub = HBM_BYTES.get((a.precision, ns), 0) * ne
-    sub_s = (total_ms / 1e3) / (n_sub * a.steps)
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": f"k_element_f64<{ns}>", "peak_kind": "derived (FP64 pipe, max clock)",
-                "kernel_ms_mean": el_avg_s * 1e3, "node_kernel_ms_mean": nd_ms / max(nd_n, 1),
-                "kernel_share_of_subcycle": el_ms / max(el_ms + nd_ms, 1e-12),
-                "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
-                "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak, "hbm_peak_GBps": hbm_peak,
-                "hbm_peak_kind": hbm_kind}
+    value = ws * ne * n_sub * a.steps / (total_ms / 1e3)
+    roofline = roofline_for(a.precision, case, m["kt"], m["total_ms"], a.steps)
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -295,18 +360,42 @@ def run_ours(a):
         d2h = 8 * (2 * nn + 3 * ns * ne)
         e2e = {"value": ws * ne * n_sub * e2e_steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+    st.close()
+
+    variants = None
+    if not a.no_variants and ws == 1:
+        variants = {}
+        other = "mixed" if a.precision == "fp64" else "fp64"
+        mv = measure(mevp, torch, barrier, 1, case, other, a.steps, a.warmup, flush)
+        mv["state"].close()
+        variants[other] = {"workload": a.workload, "value": mv["value"],
+                           "ms_per_step": mv["total_ms"] / a.steps,
+                           "roofline": roofline_for(other, case, mv["kt"], mv["total_ms"],
+                                                    a.steps)}
+        stable_ab = max(300.0, 4e6 / (case["L"] / nx))  # stable when alpha*h >~ 4e6 m
+        variants["mixed_field_error"] = field_error(mevp, case, n_sub, stable_ab)
+        if a.workload != "mesh1024_dg2":
+            big = W.make_case("mesh1024_dg2")
+            for prec in ("fp64", "mixed"):
+                mb = measure(mevp, torch, barrier, 1, big, prec, 2 if prec == "fp64" else 5, 3,
+                             flush)
+                mb["state"].close()
+                nsteps = 2 if prec == "fp64" else 5
+                variants[f"{prec}_mesh1024_dg2"] = {
+                    "workload": "mesh1024_dg2", "value": mb["value"],
+                    "ms_per_step": mb["total_ms"] / nsteps,
+                    "roofline": roofline_for(prec, big, mb["kt"], mb["total_ms"], nsteps)}
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(case)
 
-    st.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if a.precision == "fp64" else "f32+f64",
+            "dtype": "f64" if a.precision == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": a.workload, "nx": nx, "ny": ny, "n_stress": ns,
                        "n_sub": n_sub, "precision": a.precision,
@@ -314,8 +403,9 @@ def run_ours(a):
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": a.steps * (2 + 2 * n_sub),
-            "clocks": clk, "wall_s": t_wall,
+            # per step: begin_step (3 kernels; mixed adds 2 conversions) + 2 per subcycle
+            "gpu_launches": a.steps * ((5 if a.precision == "mixed" else 3) + 2 * n_sub),
+            "clocks": clk, "wall_s": m["wall"], "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -333,6 +423,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other precision and the 1024^2 measurements")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ours":
         ap.error("--warmup must be >= 3")

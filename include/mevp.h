@@ -125,12 +125,16 @@ MEVP_API int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int
 
 /* Create a state for n_stress in {3, 6} (DG1/DG2 stress; Gauss rule 2x2 or
  * 3x3 as in App. A), n_adv = 1 (DG0 H, A) and precision MEVP_FP64 or
- * MEVP_MIXED, bound to the current CUDA device and to cuda_stream
- * (a cudaStream_t; NULL = legacy default stream).  workspace: device memory
- * of at least mevp_state_workspace_bytes(), 256-byte aligned, owned by the
- * caller and kept alive until mevp_state_destroy; or NULL, in which case the
- * library allocates (cudaMalloc) and frees it.  The mesh must outlive the
- * state.  All fields start at zero; parameters must be set before running. */
+ * MEVP_MIXED, bound to the current CUDA device and to cuda_stream (a
+ * cudaStream_t; NULL = legacy default stream).  MEVP_MIXED computes strain,
+ * viscosities, stress and element forces in FP32 (the FP32 stress update of
+ * Sec. 4, extended to every element stage), keeps the velocity state as
+ * compensated FP32 pairs and sums nodal forces with compensation; inputs and
+ * outputs at this boundary stay FP64.  workspace: device memory of at least
+ * mevp_state_workspace_bytes(), 256-byte aligned, owned by the caller and
+ * kept alive until mevp_state_destroy; or NULL, in which case the library
+ * allocates (cudaMalloc) and frees it.  The mesh must outlive the state.
+ * All fields start at zero; parameters must be set before running. */
 MEVP_API int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
                       void *cuda_stream, void *workspace, size_t workspace_bytes,
                       mevp_state **out);
@@ -219,8 +223,9 @@ MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp
                                         const double *v_ocean, double *vel, double *S, int n,
                                         void *cuda_stream);
 
-/* Per-kernel timing with CUDA events, for benchmarks.  With on != 0 every
- * launch of mevp_run_subcycles is bracketed by events on the state's stream.
+/* Per-kernel timing with CUDA events, for benchmarks.  With on = k > 0 the
+ * launches of every k-th subcycle of mevp_run_subcycles are bracketed by
+ * events on the state's stream (k = 1: every subcycle; 0 switches off).
  * mevp_timing_read waits for the stream and returns, for kernel 0 (element
  * kernel) and kernel 1 (node kernel), the summed milliseconds and the number
  * of timed launches since the last read (or since timing was switched on),

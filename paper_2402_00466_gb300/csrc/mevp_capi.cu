@@ -34,7 +34,8 @@ struct mevp_state {
   bool prepared = false;
   bool has_vo = false;
   // event timing (benchmarks)
-  bool timing = false;
+  int timing = 0;                   // sampling stride (0 = off)
+  long long timed_calls = 0;        // subcycles launched since timing was enabled
   std::vector<cudaEvent_t> events;  // pool, 3 per timed subcycle
   size_t ev_used = 0;
 };
@@ -67,7 +68,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t xline, yline, lines, vel0, vel1, S, S32, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
-      total;
+      vel2a, vel2b, Pe32, nodec32, vo2, total;
 };
 
 Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
@@ -85,7 +86,7 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.lines = take(sizeof(double) * 2 * (m->nx + m->ny));
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
-  L.S = take(prec == MEVP_FP64 ? sizeof(double) * 3 * ns * ne : 0);
+  L.S = take(sizeof(double) * 3 * ns * ne);
   L.S32 = take(prec == MEVP_MIXED ? sizeof(float) * 3 * ns * ne : 0);
   L.H = take(sizeof(double) * na * ne);
   L.A = take(sizeof(double) * na * ne);
@@ -94,10 +95,16 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.Pe = take(sizeof(double) * ne);
   L.nodec = take(sizeof(double) * 6 * nn);
   L.mass = take(sizeof(double) * nn);
-  L.fbuf = take(prec == MEVP_FP64 ? sizeof(double) * 18 * ne : 0);
+  L.fbuf = take(sizeof(double) * 18 * ne);
   L.fbuf32 = take(prec == MEVP_MIXED ? sizeof(float) * 18 * ne : 0);
   const size_t dg = sizeof(double) * 3 * ns * ne, nd = sizeof(double) * 2 * nn;
   L.diag = take(dg > nd ? dg : nd);
+  const bool mx = prec == MEVP_MIXED;
+  L.vel2a = take(mx ? sizeof(float2) * 2 * nn : 0);
+  L.vel2b = take(mx ? sizeof(float2) * 2 * nn : 0);
+  L.Pe32 = take(mx ? sizeof(float) * ne : 0);
+  L.nodec32 = take(mx ? sizeof(float) * 4 * nn : 0);
+  L.vo2 = take(mx ? sizeof(float2) * nn : 0);
   L.total = off;
   return L;
 }
@@ -216,8 +223,6 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   size_t need = 0;
   int rc = mevp_state_workspace_bytes(mesh, n_stress, n_adv, precision, &need);
   if (rc) return rc;
-  if (precision == MEVP_MIXED)
-    return fail(MEVP_ERR_UNSUPPORTED, "state_create: mixed precision not built yet");
   if (workspace && workspace_bytes < need)
     return fail(MEVP_ERR_OOM, "state_create: workspace %zu bytes < %zu needed", workspace_bytes,
                 need);
@@ -276,6 +281,13 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.fbuf = (double *)(b + L.fbuf);
   d.fbuf32 = (float *)(b + L.fbuf32);
   d.diag = (double *)(b + L.diag);
+  if (precision == MEVP_MIXED) {
+    d.vel2[0] = (float2 *)(b + L.vel2a);
+    d.vel2[1] = (float2 *)(b + L.vel2b);
+    d.Pe32 = (float *)(b + L.Pe32);
+    d.nodec32 = (float *)(b + L.nodec32);
+    d.vo2 = (float2 *)(b + L.vo2);
+  }
   int r2 = MEVP_OK;
   e = cudaMemsetAsync(s->ws, 0, need, s->stream);
   if (e == cudaSuccess)
@@ -352,21 +364,30 @@ int mevp_set_forcing(mevp_state *s, const double *tau, const double *v_ocean, in
 int mevp_set_velocity(mevp_state *s, const double *uv, int on_device) {
   int rc = check_state(s);
   if (rc) return rc;
-  return copy_in(s, s->d.vel[s->cur], uv, 2 * (size_t)s->d.nn, on_device, "set_velocity");
+  rc = copy_in(s, s->d.vel[s->cur], uv, 2 * (size_t)s->d.nn, on_device, "set_velocity");
+  if (rc || s->prec != MEVP_MIXED) return rc;
+  cudaError_t e = mevp::launch_vel_split(s->d, s->cur, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_velocity split");
+  return MEVP_OK;
 }
 
 int mevp_set_stress(mevp_state *s, const double *S, int on_device) {
   int rc = check_state(s);
   if (rc) return rc;
-  if (s->prec != MEVP_FP64) return fail(MEVP_ERR_UNSUPPORTED, "set_stress: precision");
-  return copy_in(s, s->d.S, S, 3 * (size_t)s->ns * s->d.ne, on_device, "set_stress");
+  rc = copy_in(s, s->d.S, S, 3 * (size_t)s->ns * s->d.ne, on_device, "set_stress");
+  if (rc || s->prec != MEVP_MIXED) return rc;
+  cudaError_t e = mevp::launch_stress_to_f32(s->d, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_stress convert");
+  return MEVP_OK;
 }
 
 int mevp_begin_step(mevp_state *s) {
   int rc = check_state(s);
   if (rc) return rc;
   if (!s->have_params) return fail(MEVP_ERR_STATE, "begin_step: parameters not set");
-  cudaError_t e = mevp::launch_prepare(s->d, s->prm, s->has_vo, s->cur, s->stream);
+  cudaError_t e = s->prec == MEVP_MIXED
+                      ? mevp::launch_prepare_mixed(s->d, s->prm, s->has_vo, s->cur, s->stream)
+                      : mevp::launch_prepare(s->d, s->prm, s->has_vo, s->cur, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "begin_step launch");
   s->prepared = true;
   return MEVP_OK;
@@ -379,7 +400,7 @@ int mevp_run_subcycles(mevp_state *s, int n) {
   if (!s->prepared) return fail(MEVP_ERR_STATE, "run_subcycles: call mevp_begin_step first");
   for (int i = 0; i < n; ++i) {
     cudaEvent_t *ev = nullptr;
-    if (s->timing) {
+    if (s->timing && (s->timed_calls++ % s->timing) == 0) {
       while (s->events.size() < s->ev_used + 3) {
         cudaEvent_t e;
         MEVP_CUDA(cudaEventCreate(&e), "run_subcycles timing event");
@@ -388,7 +409,10 @@ int mevp_run_subcycles(mevp_state *s, int n) {
       ev = &s->events[s->ev_used];
       s->ev_used += 3;
     }
-    cudaError_t e = mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, s->cur, s->stream, ev);
+    cudaError_t e =
+        s->prec == MEVP_MIXED
+            ? mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, s->cur, s->stream, ev)
+            : mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, s->cur, s->stream, ev);
     if (e != cudaSuccess) return cuda_fail(e, "run_subcycles launch");
     s->cur ^= 1;
   }
@@ -398,7 +422,9 @@ int mevp_run_subcycles(mevp_state *s, int n) {
 int mevp_timing_enable(mevp_state *s, int on) {
   int rc = check_state(s);
   if (rc) return rc;
-  s->timing = on != 0;
+  if (on < 0) return fail(MEVP_ERR_ARG, "timing_enable: stride %d < 0", on);
+  s->timing = on;
+  s->timed_calls = 0;
   s->ev_used = 0;
   return MEVP_OK;
 }
@@ -432,22 +458,27 @@ int mevp_read_field(mevp_state *s, int field, double *dst, size_t count, int on_
   const double *src = nullptr;
   size_t n = 0;
   cudaError_t e = cudaSuccess;
+  const bool mx = s->prec == MEVP_MIXED;
   switch (field) {
-    case MEVP_U: src = d.vel[s->cur]; n = nn; break;
-    case MEVP_V: src = d.vel[s->cur] + nn; n = nn; break;
+    case MEVP_U: case MEVP_V:
+      if (mx) e = mevp::launch_vel_join(d, s->cur, s->stream);
+      src = d.vel[s->cur] + (field == MEVP_V ? nn : 0);
+      n = nn;
+      break;
     case MEVP_S11: case MEVP_S12: case MEVP_S22:
-      if (s->prec != MEVP_FP64) return fail(MEVP_ERR_UNSUPPORTED, "read_field: precision");
+      if (mx) e = mevp::launch_stress_to_f64(d, s->stream);
       src = d.S + (size_t)(field - MEVP_S11) * ns * ne;
       n = ns * ne;
       break;
     case MEVP_E11: case MEVP_E12: case MEVP_E22:
-      e = mevp::launch_strain_diag(d, s->cur, s->stream);
+      if (mx) e = mevp::launch_vel_join(d, s->cur, s->stream);
+      if (e == cudaSuccess) e = mevp::launch_strain_diag(d, s->cur, s->stream);
       src = d.diag + (size_t)(field - MEVP_E11) * ns * ne;
       n = ns * ne;
       break;
     case MEVP_FORCE_X: case MEVP_FORCE_Y:
-      if (s->prec != MEVP_FP64) return fail(MEVP_ERR_UNSUPPORTED, "read_field: precision");
-      e = mevp::launch_force_diag(d, s->stream);
+      if (mx) e = mevp::launch_stress_to_f64(d, s->stream);
+      if (e == cudaSuccess) e = mevp::launch_force_diag(d, s->stream);
       src = d.diag + (size_t)(field - MEVP_FORCE_X) * nn;
       n = nn;
       break;

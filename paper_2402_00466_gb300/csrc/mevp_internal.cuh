@@ -67,6 +67,11 @@ struct DevState {
   double *fbuf;        // FP64: [18][ne] per-element nodal forces (scratch)
   float *fbuf32;       // mixed: [18][ne]
   double *diag;        // [3][ns][ne] or [2][nn] diagnostic output
+  // mixed precision only (FP64 buffers above stage inputs and outputs)
+  float2 *vel2[2];     // [2][nn] (hi, lo) pairs, ping-pong
+  float *Pe32;         // [ne]
+  float *nodec32;      // [4][nn] m/dt, qx, qy, l Cw rho_w
+  float2 *vo2;         // [nn] ocean velocity
 };
 
 // Launchers (return cudaGetLastError of the launch).
@@ -77,6 +82,16 @@ cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo,
 cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
                                 cudaStream_t st, cudaEvent_t *ev);
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
+
+// mixed precision
+cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool has_vo, int cur,
+                                 cudaStream_t st);
+cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
+                                  bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev);
+cudaError_t launch_vel_split(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_vel_join(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_stress_to_f32(const DevState &d, cudaStream_t st);
+cudaError_t launch_stress_to_f64(const DevState &d, cudaStream_t st);
 cudaError_t launch_force_diag(const DevState &d, cudaStream_t st);
 
 }  // namespace mevp

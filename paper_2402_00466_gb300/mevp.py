@@ -227,8 +227,9 @@ def mevp_run_subcycles_noalloc(nx, ny, n_stress, params, xline, yline, H, A, tau
         ptr(tau), ptr(v_ocean), ptr(vel), ptr(S), int(n), ctypes.c_void_p(stream)))
 
 
-def mevp_timing_enable(state, on: bool):
-    _check(load().mevp_timing_enable(state, int(bool(on))))
+def mevp_timing_enable(state, stride: int):
+    """Event-time every `stride`-th subcycle (0 = off)."""
+    _check(load().mevp_timing_enable(state, int(stride)))
 
 
 def mevp_timing_read(state):
@@ -299,7 +300,7 @@ class State:
     def begin_step(self): mevp_begin_step(self.state)
     def run_subcycles(self, n): mevp_run_subcycles(self.state, n)
     def sync(self): mevp_sync(self.state)
-    def timing_enable(self, on=True): mevp_timing_enable(self.state, on)
+    def timing_enable(self, stride=1): mevp_timing_enable(self.state, stride)
     def timing_read(self): return mevp_timing_read(self.state)
 
     def field_shape(self, field):
