@@ -179,6 +179,17 @@ MEVP_API int mevp_read_field(mevp_state *state, int field, double *dst, size_t c
 /* Wait for all work on the state's stream; reports asynchronous errors. */
 MEVP_API int mevp_sync(mevp_state *state);
 
+/* Options of a state (mevp_set_option). */
+enum {
+  /* MEVP_MIXED only: 1 (default) = one fused launch per subcycle (element
+   * work for a tile plus a one-element halo, forces through shared memory,
+   * node update in the same CTA); 0 = two launches (element kernel writing
+   * per-element forces to global memory, node kernel gathering them).  Both
+   * give bitwise identical results. */
+  MEVP_OPT_FUSED = 1
+};
+MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
+
 /* Size of the static device scratch used by mevp_run_subcycles_noalloc. */
 #define MEVP_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -33,6 +33,7 @@ struct mevp_state {
   bool have_params = false;
   bool prepared = false;
   bool has_vo = false;
+  bool fused = true;  // mixed precision: one fused launch per subcycle
   // event timing (benchmarks)
   int timing = 0;                   // sampling stride (0 = off)
   long long timed_calls = 0;        // subcycles launched since timing was enabled
@@ -67,7 +68,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t xline, yline, lines, vel0, vel1, S, S32, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, lines, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, total;
 };
 
@@ -87,7 +88,8 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(sizeof(double) * 3 * ns * ne);
-  L.S32 = take(prec == MEVP_MIXED ? sizeof(float) * 3 * ns * ne : 0);
+  L.S32a = take(prec == MEVP_MIXED ? sizeof(float) * 3 * ns * ne : 0);
+  L.S32b = take(prec == MEVP_MIXED ? sizeof(float) * 3 * ns * ne : 0);
   L.H = take(sizeof(double) * na * ne);
   L.A = take(sizeof(double) * na * ne);
   L.tau = take(sizeof(double) * 2 * nn);
@@ -270,7 +272,8 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.vel[0] = (double *)(b + L.vel0);
   d.vel[1] = (double *)(b + L.vel1);
   d.S = (double *)(b + L.S);
-  d.S32 = (float *)(b + L.S32);
+  d.S32[0] = (float *)(b + L.S32a);
+  d.S32[1] = (float *)(b + L.S32b);
   d.H = (double *)(b + L.H);
   d.A = (double *)(b + L.A);
   d.tau = (double *)(b + L.tau);
@@ -376,7 +379,7 @@ int mevp_set_stress(mevp_state *s, const double *S, int on_device) {
   if (rc) return rc;
   rc = copy_in(s, s->d.S, S, 3 * (size_t)s->ns * s->d.ne, on_device, "set_stress");
   if (rc || s->prec != MEVP_MIXED) return rc;
-  cudaError_t e = mevp::launch_stress_to_f32(s->d, s->stream);
+  cudaError_t e = mevp::launch_stress_to_f32(s->d, s->cur, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_stress convert");
   return MEVP_OK;
 }
@@ -411,12 +414,26 @@ int mevp_run_subcycles(mevp_state *s, int n) {
     }
     cudaError_t e =
         s->prec == MEVP_MIXED
-            ? mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, s->cur, s->stream, ev)
+            ? mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, s->cur, s->stream, ev,
+                                          s->fused)
             : mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, s->cur, s->stream, ev);
     if (e != cudaSuccess) return cuda_fail(e, "run_subcycles launch");
     s->cur ^= 1;
   }
   return MEVP_OK;
+}
+
+int mevp_set_option(mevp_state *s, int option, int value) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  switch (option) {
+    case MEVP_OPT_FUSED:
+      if (value != 0 && value != 1) return fail(MEVP_ERR_ARG, "set_option: FUSED takes 0 or 1");
+      s->fused = value != 0;
+      return MEVP_OK;
+    default:
+      return fail(MEVP_ERR_ARG, "set_option: unknown option %d", option);
+  }
 }
 
 int mevp_timing_enable(mevp_state *s, int on) {
@@ -466,7 +483,7 @@ int mevp_read_field(mevp_state *s, int field, double *dst, size_t count, int on_
       n = nn;
       break;
     case MEVP_S11: case MEVP_S12: case MEVP_S22:
-      if (mx) e = mevp::launch_stress_to_f64(d, s->stream);
+      if (mx) e = mevp::launch_stress_to_f64(d, s->cur, s->stream);
       src = d.S + (size_t)(field - MEVP_S11) * ns * ne;
       n = ns * ne;
       break;
@@ -477,7 +494,7 @@ int mevp_read_field(mevp_state *s, int field, double *dst, size_t count, int on_
       n = ns * ne;
       break;
     case MEVP_FORCE_X: case MEVP_FORCE_Y:
-      if (mx) e = mevp::launch_stress_to_f64(d, s->stream);
+      if (mx) e = mevp::launch_stress_to_f64(d, s->cur, s->stream);
       if (e == cudaSuccess) e = mevp::launch_force_diag(d, s->stream);
       src = d.diag + (size_t)(field - MEVP_FORCE_X) * nn;
       n = nn;

@@ -57,7 +57,7 @@ struct DevState {
   double *lines;       // [hx: nx][1/hx: nx][hy: ny][1/hy: ny], from the mesh lines
   double *vel[2];      // [2][nn] ping-pong
   double *S;           // FP64: [3][ns][ne]
-  float *S32;          // mixed: [3][ns][ne]
+  float *S32[2];       // mixed: [3][ns][ne], ping-pong with the velocity
   double *H, *A;       // [ne]
   double *tau;         // [2][nn]
   double *vo;          // [2][nn]
@@ -87,11 +87,12 @@ cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                                  cudaStream_t st);
 cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
-                                  bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev);
+                                  bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
+                                  bool fused);
 cudaError_t launch_vel_split(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_vel_join(const DevState &d, int cur, cudaStream_t st);
-cudaError_t launch_stress_to_f32(const DevState &d, cudaStream_t st);
-cudaError_t launch_stress_to_f64(const DevState &d, cudaStream_t st);
+cudaError_t launch_stress_to_f32(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_stress_to_f64(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_diag(const DevState &d, cudaStream_t st);
 
 }  // namespace mevp

@@ -76,6 +76,7 @@ def load(build_if_stale: bool = True):
             "mevp_run_subcycles_noalloc": (i, [i, i, i, ctypes.POINTER(mevp_params), vp, vp, vp,
                                                vp, vp, vp, vp, vp, i, vp]),
             "mevp_timing_enable": (i, [vp, i]),
+            "mevp_set_option": (i, [vp, i, i]),
             "mevp_timing_read": (i, [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]),
             "mevp_last_error": (ctypes.c_char_p, []),
@@ -227,6 +228,13 @@ def mevp_run_subcycles_noalloc(nx, ny, n_stress, params, xline, yline, H, A, tau
         ptr(tau), ptr(v_ocean), ptr(vel), ptr(S), int(n), ctypes.c_void_p(stream)))
 
 
+MEVP_OPT_FUSED = 1
+
+
+def mevp_set_option(state, option: int, value: int):
+    _check(load().mevp_set_option(state, int(option), int(value)))
+
+
 def mevp_timing_enable(state, stride: int):
     """Event-time every `stride`-th subcycle (0 = off)."""
     _check(load().mevp_timing_enable(state, int(stride)))
@@ -301,6 +309,7 @@ class State:
     def run_subcycles(self, n): mevp_run_subcycles(self.state, n)
     def sync(self): mevp_sync(self.state)
     def timing_enable(self, stride=1): mevp_timing_enable(self.state, stride)
+    def set_option(self, option, value): mevp_set_option(self.state, option, value)
     def timing_read(self): return mevp_timing_read(self.state)
 
     def field_shape(self, field):

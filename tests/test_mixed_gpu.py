@@ -137,3 +137,25 @@ def test_mixed_roundtrip_and_determinism():
     a = run_gpu(case, 9, "mixed")
     b = run_gpu(case, 9, "mixed")
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (31, 15), (32, 16), (62, 30), (63, 31),
+                                   (100, 7), (7, 100)])
+def test_fused_equals_two_kernel_path_bitwise(n_s, shape):
+    """The fused subcycle (tile + one-element halo, forces in shared memory)
+    performs the same arithmetic as the element/node kernel pair."""
+    case = W.small_case(*shape, n_s, seed=300 + shape[0] + 7 * shape[1])
+    out = []
+    for fused in (1, 0):
+        with mevp.State(case["nx"], case["ny"], n_s, vertex_xy=case["xy"], precision="mixed",
+                        params=case["params"]) as st:
+            st.set_option(mevp.MEVP_OPT_FUSED, fused)
+            st.set_ice(case["H"], case["A"])
+            st.set_forcing(case["tau"])
+            st.set_velocity(case["vel0"])
+            st.set_stress(case["S0"])
+            st.begin_step()
+            st.run_subcycles(5)
+            out.append((st.velocity(), st.stress()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
