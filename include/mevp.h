@@ -167,7 +167,10 @@ MEVP_API int mevp_begin_step(mevp_state *state);
 /* n >= 0 mEVP subcycles (Sec. 2: the momentum equation and Eq. 3 subcycled
  * within one outer step) from the current velocity and stress, with v^n and
  * the forcing of the last mevp_begin_step.  Asynchronous on the state's
- * stream; two kernel launches per subcycle. */
+ * stream; FP64: two kernel launches per subcycle, MEVP_MIXED: one (see
+ * MEVP_OPT_FUSED); replayed as CUDA graphs (MEVP_OPT_GRAPHS).  The first
+ * call after a parameter change captures its graphs: do not call it while
+ * the state's stream is itself being captured. */
 MEVP_API int mevp_run_subcycles(mevp_state *state, int n);
 
 /* Copy a field (enum mevp_field) to dst, FP64, `count` = number of doubles
@@ -186,7 +189,13 @@ enum {
    * node update in the same CTA); 0 = two launches (element kernel writing
    * per-element forces to global memory, node kernel gathering them).  Both
    * give bitwise identical results. */
-  MEVP_OPT_FUSED = 1
+  MEVP_OPT_FUSED = 1,
+  /* 1 (default) = mevp_run_subcycles replays runs of 4 or more subcycles as
+   * CUDA graphs (chunks of up to 64, captured on the state's stream at first
+   * use and kept until the parameters, the ocean forcing or an option
+   * change); 0 = one launch at a time.  States on the legacy default stream
+   * (cuda_stream = NULL) always launch one at a time. */
+  MEVP_OPT_GRAPHS = 2
 };
 MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
 

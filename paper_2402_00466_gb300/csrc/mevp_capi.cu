@@ -34,6 +34,12 @@ struct mevp_state {
   bool prepared = false;
   bool has_vo = false;
   bool fused = true;  // mixed precision: one fused launch per subcycle
+  bool use_graphs = true;  // replay captured subcycle chunks (non-default streams)
+  struct Graph {
+    int parity, len;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;  // instantiated chunks, dropped when kernel arguments change
   // event timing (benchmarks)
   int timing = 0;                   // sampling stride (0 = off)
   long long timed_calls = 0;        // subcycles launched since timing was enabled
@@ -67,9 +73,14 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Subcycle runs of at least kMinGraphChunk are replayed as CUDA graphs of up
+// to kMaxGraphChunk subcycles.
+constexpr int kMinGraphChunk = 4;
+constexpr int kMaxGraphChunk = 64;
+
 struct Layout {
   size_t xline, yline, lines, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
-      vel2a, vel2b, Pe32, nodec32, vo2, total;
+      vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
 Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
@@ -102,11 +113,12 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   const size_t dg = sizeof(double) * 3 * ns * ne, nd = sizeof(double) * 2 * nn;
   L.diag = take(dg > nd ? dg : nd);
   const bool mx = prec == MEVP_MIXED;
-  L.vel2a = take(mx ? sizeof(float2) * 2 * nn : 0);
-  L.vel2b = take(mx ? sizeof(float2) * 2 * nn : 0);
+  L.vel2a = take(mx ? sizeof(float4) * nn : 0);
+  L.vel2b = take(mx ? sizeof(float4) * nn : 0);
   L.Pe32 = take(mx ? sizeof(float) * ne : 0);
-  L.nodec32 = take(mx ? sizeof(float) * 4 * nn : 0);
+  L.nodec32 = take(mx ? sizeof(float4) * nn : 0);
   L.vo2 = take(mx ? sizeof(float2) * nn : 0);
+  L.lines32 = take(mx ? sizeof(float2) * (m->nx + m->ny) : 0);
   L.total = off;
   return L;
 }
@@ -138,6 +150,46 @@ int copy_in(mevp_state *s, double *dst, const double *src, size_t n, int on_devi
                             s->stream),
             what);
   if (!on_device) MEVP_CUDA(cudaStreamSynchronize(s->stream), what);
+  return MEVP_OK;
+}
+
+void drop_graphs(mevp_state *s) {
+  for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
+cudaError_t launch_one(mevp_state *s, int cur, cudaEvent_t *ev) {
+  return s->prec == MEVP_MIXED
+             ? mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, cur, s->stream, ev,
+                                           s->fused)
+             : mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, cur, s->stream, ev);
+}
+
+// Instantiated graph of `len` subcycles starting from velocity buffer
+// `parity`, captured on the state's stream and cached.
+int chunk_graph(mevp_state *s, int parity, int len, cudaGraphExec_t *out) {
+  for (auto &g : s->graphs)
+    if (g.parity == parity && g.len == len) {
+      *out = g.exec;
+      return MEVP_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "run_subcycles: begin capture");
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < len && le == cudaSuccess; ++k) le = launch_one(s, parity ^ (k & 1), nullptr);
+  e = cudaStreamEndCapture(s->stream, &graph);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return cuda_fail(le != cudaSuccess ? le : e, "run_subcycles: capture");
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "run_subcycles: instantiate");
+  s->graphs.push_back({parity, len, exec});
+  *out = exec;
   return MEVP_OK;
 }
 
@@ -285,11 +337,18 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.fbuf32 = (float *)(b + L.fbuf32);
   d.diag = (double *)(b + L.diag);
   if (precision == MEVP_MIXED) {
-    d.vel2[0] = (float2 *)(b + L.vel2a);
-    d.vel2[1] = (float2 *)(b + L.vel2b);
+    e = mevp::setup_mixed_kernels();
+    if (e != cudaSuccess) {
+      if (s->owns_ws) cudaFree(s->ws);
+      delete s;
+      return cuda_fail(e, "state_create: kernel attributes");
+    }
+    d.vel4[0] = (float4 *)(b + L.vel2a);
+    d.vel4[1] = (float4 *)(b + L.vel2b);
     d.Pe32 = (float *)(b + L.Pe32);
-    d.nodec32 = (float *)(b + L.nodec32);
+    d.nodec4 = (float4 *)(b + L.nodec32);
     d.vo2 = (float2 *)(b + L.vo2);
+    d.lines32 = (float2 *)(b + L.lines32);
   }
   int r2 = MEVP_OK;
   e = cudaMemsetAsync(s->ws, 0, need, s->stream);
@@ -314,6 +373,7 @@ void mevp_state_destroy(mevp_state *s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
   for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+  for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
   if (s->owns_ws) cudaFree(s->ws);
   delete s;
 }
@@ -338,6 +398,7 @@ int mevp_set_params(mevp_state *s, const mevp_params *p) {
   s->prm = *p;
   s->rheo = mevp::make_rheo(*p);
   s->have_params = true;
+  drop_graphs(s);
   return MEVP_OK;
 }
 
@@ -356,9 +417,11 @@ int mevp_set_forcing(mevp_state *s, const double *tau, const double *v_ocean, in
   if ((rc = copy_in(s, s->d.tau, tau, n, on_device, "set_forcing tau"))) return rc;
   if (v_ocean) {
     if ((rc = copy_in(s, s->d.vo, v_ocean, n, on_device, "set_forcing v_ocean"))) return rc;
+    if (!s->has_vo) drop_graphs(s);
     s->has_vo = true;
   } else {
     MEVP_CUDA(cudaMemsetAsync(s->d.vo, 0, n * sizeof(double), s->stream), "set_forcing");
+    if (s->has_vo) drop_graphs(s);
     s->has_vo = false;
   }
   return MEVP_OK;
@@ -401,24 +464,42 @@ int mevp_run_subcycles(mevp_state *s, int n) {
   if (rc) return rc;
   if (n < 0) return fail(MEVP_ERR_ARG, "run_subcycles: n=%d < 0", n);
   if (!s->prepared) return fail(MEVP_ERR_STATE, "run_subcycles: call mevp_begin_step first");
-  for (int i = 0; i < n; ++i) {
-    cudaEvent_t *ev = nullptr;
-    if (s->timing && (s->timed_calls++ % s->timing) == 0) {
-      while (s->events.size() < s->ev_used + 3) {
-        cudaEvent_t e;
-        MEVP_CUDA(cudaEventCreate(&e), "run_subcycles timing event");
-        s->events.push_back(e);
+  // The legacy default stream cannot be captured: launch directly there.
+  const bool graphs = s->use_graphs && s->stream != nullptr;
+  int i = 0;
+  while (i < n) {
+    const bool timed = s->timing && (s->timed_calls % s->timing) == 0;
+    if (timed || !graphs || n - i < kMinGraphChunk) {
+      cudaEvent_t *ev = nullptr;
+      if (timed) {
+        while (s->events.size() < s->ev_used + 3) {
+          cudaEvent_t e;
+          MEVP_CUDA(cudaEventCreate(&e), "run_subcycles timing event");
+          s->events.push_back(e);
+        }
+        ev = &s->events[s->ev_used];
+        s->ev_used += 3;
       }
-      ev = &s->events[s->ev_used];
-      s->ev_used += 3;
+      cudaError_t e = launch_one(s, s->cur, ev);
+      if (e != cudaSuccess) return cuda_fail(e, "run_subcycles launch");
+      s->cur ^= 1;
+      if (s->timing) s->timed_calls++;
+      ++i;
+      continue;
     }
-    cudaError_t e =
-        s->prec == MEVP_MIXED
-            ? mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, s->cur, s->stream, ev,
-                                          s->fused)
-            : mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, s->cur, s->stream, ev);
-    if (e != cudaSuccess) return cuda_fail(e, "run_subcycles launch");
-    s->cur ^= 1;
+    // untimed run up to the next timed subcycle (or the end), in graph chunks
+    int len = n - i;
+    if (len > kMaxGraphChunk) len = kMaxGraphChunk;
+    if (s->timing) {
+      const long long to_next = s->timing - (s->timed_calls % s->timing);
+      if (len > to_next) len = (int)to_next;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if ((rc = chunk_graph(s, s->cur, len, &exec))) return rc;
+    MEVP_CUDA(cudaGraphLaunch(exec, s->stream), "run_subcycles graph launch");
+    s->cur ^= (len & 1);
+    if (s->timing) s->timed_calls += len;
+    i += len;
   }
   return MEVP_OK;
 }
@@ -430,6 +511,11 @@ int mevp_set_option(mevp_state *s, int option, int value) {
     case MEVP_OPT_FUSED:
       if (value != 0 && value != 1) return fail(MEVP_ERR_ARG, "set_option: FUSED takes 0 or 1");
       s->fused = value != 0;
+      drop_graphs(s);
+      return MEVP_OK;
+    case MEVP_OPT_GRAPHS:
+      if (value != 0 && value != 1) return fail(MEVP_ERR_ARG, "set_option: GRAPHS takes 0 or 1");
+      s->use_graphs = value != 0;
       return MEVP_OK;
     default:
       return fail(MEVP_ERR_ARG, "set_option: unknown option %d", option);

@@ -68,10 +68,11 @@ struct DevState {
   float *fbuf32;       // mixed: [18][ne]
   double *diag;        // [3][ns][ne] or [2][nn] diagnostic output
   // mixed precision only (FP64 buffers above stage inputs and outputs)
-  float2 *vel2[2];     // [2][nn] (hi, lo) pairs, ping-pong
+  float4 *vel4[2];     // [nn] (u_hi, u_lo, v_hi, v_lo) records, ping-pong
   float *Pe32;         // [ne]
-  float *nodec32;      // [4][nn] m/dt, qx, qy, l Cw rho_w
+  float4 *nodec4;      // [nn] (m/dt, qx, qy, l Cw rho_w) records
   float2 *vo2;         // [nn] ocean velocity
+  float2 *lines32;     // [nx + ny] (h, 1/h) per mesh column, then per row
 };
 
 // Launchers (return cudaGetLastError of the launch).
@@ -84,6 +85,7 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
 
 // mixed precision
+cudaError_t setup_mixed_kernels();  // once per device, before any capture
 cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                                  cudaStream_t st);
 cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,

@@ -5,7 +5,8 @@
 // that accumulates over subcycles keeps FP64-level accuracy without any FP64
 // instruction in the loop (GB300 issues FP64 at 1/58 of the FP32 rate):
 //
-//   * velocity is stored as compensated FP32 pairs (hi, lo), v = hi + lo;
+//   * velocity is stored as compensated FP32 pairs (hi, lo), v = hi + lo,
+//     one 16-byte record (u_hi, u_lo, v_hi, v_lo) per node;
 //   * the element kernel forms nodal velocity differences against the
 //     element-centre node from the pairs, (hi_j - hi_c) + (lo_j - lo_c), so
 //     rigid-body motion cancels before the FP32 strain (the cancellation the
@@ -18,6 +19,12 @@
 //
 // The stress state is FP32.  Boundary handling, the force gather order and
 // the per-element algorithm are the same as in the FP64 kernels.
+//
+// Default launch: one fused kernel per subcycle (k_subcycle_mix).  A CTA
+// computes the element stage for its tile plus a one-element halo,
+// exchanges forces through shared memory and updates the nodes it owns.  The
+// two-kernel variant (k_element_mix + k_node_mix) does the same arithmetic
+// through a global force buffer.
 #include "mevp_elem.cuh"
 #include "mevp_internal.cuh"
 #include "mevp_ref.cuh"
@@ -40,60 +47,74 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
   e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
+// Asynchronous global -> shared copies (16 bytes, L2 only).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 struct MixArgs {
   float ie, hainv, dmin2, fac;  // stress update
   float opb, fdt;               // 1 + beta, f dt (velocity update)
   int has_vo;
 };
 
-// Full element step of element (kx, ky) in FP32: strain from the velocity
-// pairs, relaxed stress update (S32[cur] -> out), element forces.
+// Element step in FP32 from the 9 nodal velocity records (u_hi, u_lo, v_hi,
+// v_lo) and the element's stress (in/out): strain from pair differences
+// against the centre node, relaxed stress update, element forces.
 template <int NS>
-__device__ __forceinline__ void element_mix(const DevState &d, const MixArgs &a, int kx, int ky,
-                                            int cur, bool write_S, float fx[9], float fy[9]) {
-  const size_t K = (size_t)ky * d.nx + kx;
-  const float hx = (float)__ldg(d.lines + kx), ihx = (float)__ldg(d.lines + d.nx + kx);
-  const float hy = (float)__ldg(d.lines + 2 * d.nx + ky);
-  const float ihy = (float)__ldg(d.lines + 2 * d.nx + d.ny + ky);
-  const float2 *__restrict__ vu = d.vel2[cur];
-  const float2 *__restrict__ vv = d.vel2[cur] + d.nn;
-  const size_t base = (size_t)(2 * ky) * d.nw + 2 * kx;
-  float2 pu[9], pv[9];
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      pu[c + 3 * b] = __ldg(vu + base + (size_t)b * d.nw + c);
-      pv[c + 3 * b] = __ldg(vv + base + (size_t)b * d.nw + c);
-    }
+__device__ __forceinline__ void element_core(const float4 pv[9], float S11[NS], float S12[NS],
+                                             float S22[NS], float P, float hx, float ihx,
+                                             float hy, float ihy, const MixArgs &a, float fx[9],
+                                             float fy[9]) {
   float du[9], dv[9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    du[j] = __fsub_rn(pu[j].x, pu[4].x) + __fsub_rn(pu[j].y, pu[4].y);
-    dv[j] = __fsub_rn(pv[j].x, pv[4].x) + __fsub_rn(pv[j].y, pv[4].y);
+    du[j] = __fsub_rn(pv[j].x, pv[4].x) + __fsub_rn(pv[j].y, pv[4].y);
+    dv[j] = __fsub_rn(pv[j].z, pv[4].z) + __fsub_rn(pv[j].w, pv[4].w);
   }
   float Pc[NS], Qc[NS], Gc[NS];
   strain_invariants<NS>(du, dv, ihx, ihy, a.ie, Pc, Qc, Gc);
+  relax_stress<NS>(S11, S12, S22, Pc, Qc, Gc, P * a.hainv, a.dmin2, a.fac, a.ie);
+  element_forces_t<NS>(S11, S12, S22, hx, hy, fx, fy);
+}
+
+template <int NS>
+__device__ __forceinline__ void load_stress(const DevState &d, int cur, size_t K, float S11[NS],
+                                            float S12[NS], float S22[NS]) {
   const float *__restrict__ Sin = d.S32[cur];
-  float S11[NS], S12[NS], S22[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     S11[s] = __ldg(Sin + (size_t)(0 * NS + s) * d.ne + K);
     S12[s] = __ldg(Sin + (size_t)(1 * NS + s) * d.ne + K);
     S22[s] = __ldg(Sin + (size_t)(2 * NS + s) * d.ne + K);
   }
-  const float Ph = __ldg(d.Pe32 + K) * a.hainv;
-  relax_stress<NS>(S11, S12, S22, Pc, Qc, Gc, Ph, a.dmin2, a.fac, a.ie);
-  if (write_S) {
-    float *__restrict__ Sout = d.S32[cur ^ 1];
+}
+
+template <int NS>
+__device__ __forceinline__ void store_stress(const DevState &d, int cur, size_t K,
+                                             const float S11[NS], const float S12[NS],
+                                             const float S22[NS]) {
+  float *__restrict__ Sout = d.S32[cur ^ 1];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      Sout[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
-      Sout[(size_t)(1 * NS + s) * d.ne + K] = S12[s];
-      Sout[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
-    }
+  for (int s = 0; s < NS; ++s) {
+    Sout[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
+    Sout[(size_t)(1 * NS + s) * d.ne + K] = S12[s];
+    Sout[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
   }
-  element_forces_t<NS>(S11, S12, S22, hx, hy, fx, fy);
+}
+
+__device__ __forceinline__ void line_geometry(const DevState &d, int kx, int ky, float &hx,
+                                              float &ihx, float &hy, float &ihy) {
+  const float2 gx = __ldg(d.lines32 + kx), gy = __ldg(d.lines32 + d.nx + ky);
+  hx = gx.x;
+  ihx = gx.y;
+  hy = gy.x;
+  ihy = gy.y;
 }
 
 template <int NS>
@@ -101,8 +122,20 @@ __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs 
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
   const int ky = K / d.nx, kx = K - ky * d.nx;
+  const float4 *__restrict__ vel = d.vel4[cur];
+  const size_t base = (size_t)(2 * ky) * d.nw + 2 * kx;
+  float4 pv[9];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pv[c + 3 * b] = __ldg(vel + base + (size_t)b * d.nw + c);
+  float S11[NS], S12[NS], S22[NS];
+  load_stress<NS>(d, cur, K, S11, S12, S22);
+  float hx, ihx, hy, ihy;
+  line_geometry(d, kx, ky, hx, ihx, hy, ihy);
   float fx[9], fy[9];
-  element_mix<NS>(d, a, kx, ky, cur, true, fx, fy);
+  element_core<NS>(pv, S11, S12, S22, __ldg(d.Pe32 + K), hx, ihx, hy, ihy, a, fx, fy);
+  store_stress<NS>(d, cur, K, S11, S12, S22);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     d.fbuf32[(size_t)j * d.ne + K] = fx[j];
@@ -112,15 +145,17 @@ __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs 
 
 // Compensated sum of up to four FP32 element contributions in the fixed
 // order SW, SE, NW, NE: returns hi + lo.
-__device__ __forceinline__ void csum(const float *t, int n, float &hi, float &lo) {
+__device__ __forceinline__ void csum(const float2 *t, int n, float2 &hi, float2 &lo) {
   hi = t[0];
-  lo = 0.0f;
+  lo = make_float2(0.f, 0.f);
 #pragma unroll
   for (int i = 1; i < 4; ++i) {
     if (i < n) {
       float e;
-      two_sum(hi, t[i], hi, e);
-      lo = __fadd_rn(lo, e);
+      two_sum(hi.x, t[i].x, hi.x, e);
+      lo.x = __fadd_rn(lo.x, e);
+      two_sum(hi.y, t[i].y, hi.y, e);
+      lo.y = __fadd_rn(lo.y, e);
     }
   }
 }
@@ -129,52 +164,40 @@ __device__ __forceinline__ void csum(const float *t, int n, float &hi, float &lo
 //   a = m(1+beta)/dt + c, b = m f, c = l Cw rho_w |v_o - v|,
 //   r' = (q - (m/dt) v) + F + c (v_o - v) + b (v_y, -v_x),  q = (m/dt) v^n + l tau,
 //   (a + i b) d = r',  v <- v + d (compensated).
-__device__ __forceinline__ void node_update_mix(const DevState &d, const MixArgs &ma, int cur,
-                                                size_t node, const float tx[4],
-                                                const float ty[4], int n) {
-  const size_t nn = d.nn;
-  const float2 *__restrict__ vp = d.vel2[cur];
-  float2 *__restrict__ vq = d.vel2[cur ^ 1];
-  float Fxh, Fxl, Fyh, Fyl;
-  csum(tx, n, Fxh, Fxl);
-  csum(ty, n, Fyh, Fyl);
-  const float2 ux = vp[node], uy = vp[nn + node];
-  const float mdt = __ldg(d.nodec32 + 0 * nn + node);
-  const float qx = __ldg(d.nodec32 + 1 * nn + node), qy = __ldg(d.nodec32 + 2 * nn + node);
-  const float cD = __ldg(d.nodec32 + 3 * nn + node);
-  float ox = 0.f, oy = 0.f;
-  if (ma.has_vo) {
-    const float2 o = __ldg(d.vo2 + node);
-    ox = o.x;
-    oy = o.y;
-  }
-  const float rx0 = (ox - ux.x) - ux.y, ry0 = (oy - uy.x) - uy.y;
+// v = (u_hi, u_lo, v_hi, v_lo), k = (m/dt, qx, qy, l Cw rho_w), t[n] = element
+// force contributions (f_x, f_y).
+__device__ __forceinline__ float4 node_update_mix(const MixArgs &ma, float4 v, float4 k,
+                                                  float2 o, const float2 *t, int n) {
+  float2 Fh, Fl;
+  csum(t, n, Fh, Fl);
+  const float mdt = k.x, qx = k.y, qy = k.z, cD = k.w;
+  const float rx0 = (o.x - v.x) - v.y, ry0 = (o.y - v.z) - v.w;
   const float c = cD * sqrtf(fmaf(rx0, rx0, ry0 * ry0));
   const float a = fmaf(mdt, ma.opb, c);
   const float b = mdt * ma.fdt;
-  float rx = (qx - fmaf(mdt, ux.x, mdt * ux.y)) + Fxh;
-  rx = fmaf(c, rx0, rx + Fxl);
-  rx = fmaf(b, uy.x, rx);
-  float ry = (qy - fmaf(mdt, uy.x, mdt * uy.y)) + Fyh;
-  ry = fmaf(c, ry0, ry + Fyl);
-  ry = fmaf(-b, ux.x, ry);
+  float rx = (qx - fmaf(mdt, v.x, mdt * v.y)) + Fh.x;
+  rx = fmaf(c, rx0, rx + Fl.x);
+  rx = fmaf(b, v.z, rx);
+  float ry = (qy - fmaf(mdt, v.z, mdt * v.w)) + Fh.y;
+  ry = fmaf(c, ry0, ry + Fl.y);
+  ry = fmaf(-b, v.x, ry);
   const float det = fmaf(a, a, b * b);
-  float2 nx, ny;
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
   if (det > 0.f) {
     const float inv = 1.0f / det;
     const float ddx = fmaf(a, rx, b * ry) * inv;
     const float ddy = fmaf(a, ry, -b * rx) * inv;
     float s, e;
-    two_sum(ux.x, ddx, s, e);
-    fast_two_sum(s, __fadd_rn(ux.y, e), nx.x, nx.y);
-    two_sum(uy.x, ddy, s, e);
-    fast_two_sum(s, __fadd_rn(uy.y, e), ny.x, ny.y);
-  } else {
-    nx = make_float2(0.f, 0.f);
-    ny = make_float2(0.f, 0.f);
+    two_sum(v.x, ddx, s, e);
+    fast_two_sum(s, __fadd_rn(v.y, e), out.x, out.y);
+    two_sum(v.z, ddy, s, e);
+    fast_two_sum(s, __fadd_rn(v.w, e), out.z, out.w);
   }
-  vq[node] = nx;
-  vq[nn + node] = ny;
+  return out;
+}
+
+__device__ __forceinline__ float2 ocean(const DevState &d, const MixArgs &ma, size_t node) {
+  return ma.has_vo ? __ldg(d.vo2 + node) : make_float2(0.f, 0.f);
 }
 
 __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma, int cur) {
@@ -182,8 +205,8 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma,
   const int sw = d.nx + 1;
   if (slot >= sw * (d.ny + 1)) return;
   const int ky = slot / sw, kx = slot - ky * sw;
-  float2 *__restrict__ vq = d.vel2[cur ^ 1];
-  const size_t nn = d.nn;
+  const float4 *__restrict__ vp = d.vel4[cur];
+  float4 *__restrict__ vq = d.vel4[cur ^ 1];
   const size_t ne = d.ne;
   const float *__restrict__ fb = d.fbuf32;
 #pragma unroll
@@ -194,130 +217,160 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma,
       if (ix >= d.nw || iy >= d.nh) continue;
       const size_t node = (size_t)iy * d.nw + ix;
       if (ix == 0 || iy == 0 || ix == d.nw - 1 || iy == d.nh - 1) {
-        vq[node] = make_float2(0.f, 0.f);
-        vq[nn + node] = make_float2(0.f, 0.f);
+        vq[node] = make_float4(0.f, 0.f, 0.f, 0.f);
         continue;
       }
-      float tx[4] = {0.f, 0.f, 0.f, 0.f}, ty[4] = {0.f, 0.f, 0.f, 0.f};
+      float2 t[4];
       int n;
+      auto F = [&](int j, size_t K) { return make_float2(__ldg(fb + j * ne + K), __ldg(fb + (9 + j) * ne + K)); };
       if (dx == 0 && dy == 0) {
         const size_t Ksw = (size_t)(ky - 1) * d.nx + kx - 1, Kse = Ksw + 1;
         const size_t Knw = (size_t)ky * d.nx + kx - 1, Kne = Knw + 1;
-        tx[0] = __ldg(fb + 8 * ne + Ksw); tx[1] = __ldg(fb + 6 * ne + Kse);
-        tx[2] = __ldg(fb + 2 * ne + Knw); tx[3] = __ldg(fb + 0 * ne + Kne);
-        ty[0] = __ldg(fb + 17 * ne + Ksw); ty[1] = __ldg(fb + 15 * ne + Kse);
-        ty[2] = __ldg(fb + 11 * ne + Knw); ty[3] = __ldg(fb + 9 * ne + Kne);
+        t[0] = F(8, Ksw); t[1] = F(6, Kse); t[2] = F(2, Knw); t[3] = F(0, Kne);
         n = 4;
       } else if (dx == 1 && dy == 0) {
-        const size_t Ks = (size_t)(ky - 1) * d.nx + kx, Kn = (size_t)ky * d.nx + kx;
-        tx[0] = __ldg(fb + 7 * ne + Ks); tx[1] = __ldg(fb + 1 * ne + Kn);
-        ty[0] = __ldg(fb + 16 * ne + Ks); ty[1] = __ldg(fb + 10 * ne + Kn);
+        t[0] = F(7, (size_t)(ky - 1) * d.nx + kx); t[1] = F(1, (size_t)ky * d.nx + kx);
         n = 2;
       } else if (dx == 0 && dy == 1) {
-        const size_t Kw = (size_t)ky * d.nx + kx - 1, Ke = Kw + 1;
-        tx[0] = __ldg(fb + 5 * ne + Kw); tx[1] = __ldg(fb + 3 * ne + Ke);
-        ty[0] = __ldg(fb + 14 * ne + Kw); ty[1] = __ldg(fb + 12 * ne + Ke);
+        const size_t Kw = (size_t)ky * d.nx + kx - 1;
+        t[0] = F(5, Kw); t[1] = F(3, Kw + 1);
         n = 2;
       } else {
-        const size_t K = (size_t)ky * d.nx + kx;
-        tx[0] = __ldg(fb + 4 * ne + K);
-        ty[0] = __ldg(fb + 13 * ne + K);
+        t[0] = F(4, (size_t)ky * d.nx + kx);
         n = 1;
       }
-      node_update_mix(d, ma, cur, node, tx, ty, n);
+      vq[node] = node_update_mix(ma, vp[node], __ldg(d.nodec4 + node), ocean(d, ma, node), t, n);
     }
   }
 }
 
-// One fused subcycle.  A CTA takes a FTX x FTY block of elements: the
-// (FTX-1) x (FTY-1) elements it owns plus one halo column to the west and one
-// halo row to the south, recomputed from S^{p-1} and v^{p-1} so that every
-// node the CTA owns -- ix in [2 x0, 2 x0 + 2(FTX-1)), iy likewise, plus the
-// last boundary row/column of the domain -- sees all of its element forces
-// without any exchange.  Forces go through shared memory; the stress is
-// ping-ponged (halo readers need S^{p-1}).  Arithmetic is identical to the
-// two-kernel path, element for element and node for node.
+// ---- fused subcycle ---------------------------------------------------------
+// A CTA takes a FTX x FTY block of elements: the (FTX-1) x (FTY-1) elements it
+// owns plus one halo column to the west and one halo row to the south,
+// recomputed from S^{p-1} and v^{p-1} so that every node the CTA owns -- ix in
+// [2 x0, 2 x0 + 2(FTX-1)), iy likewise, plus the last boundary row/column of
+// the domain -- sees all of its element forces without an exchange.  The
+// stress is ping-ponged (halo readers need S^{p-1}).
 constexpr int FTX = 32, FTY = 16;
+constexpr int TNW = 2 * (FTX - 1), TNH = 2 * (FTY - 1);  // owned-node window
+constexpr size_t kFusedSmem = sizeof(float4) * 2 * TNW * TNH + sizeof(float2) * 9 * FTX * FTY;
 
+// The element phase loads straight from global memory, so each warp proceeds
+// as soon as its own loads arrive (staging the whole tile into shared memory
+// first, behind a barrier, measured slower: 106 vs 91 us per subcycle at
+// 1024^2).  The owned nodes' velocity and constant records, needed only by
+// the node phase, are copied into shared memory asynchronously from the start.
 template <int NS>
 __global__ void __launch_bounds__(FTX *FTY) k_subcycle_mix(DevState d, MixArgs ma, int cur) {
-  __shared__ float fs[18][FTY][FTX];
-  const int lx = threadIdx.x, ly = threadIdx.y;
+  extern __shared__ float4 smem[];
+  float4 *sv = smem;              // [TNH][TNW] velocity records of the owned nodes
+  float4 *sk = sv + TNW * TNH;    // [TNH][TNW] constant records of the owned nodes
+  float2(*fs)[FTY][FTX] = (float2(*)[FTY][FTX])(sk + TNW * TNH);  // [9][FTY][FTX] forces
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * FTX + lx;
   const int x0 = blockIdx.x * (FTX - 1), y0 = blockIdx.y * (FTY - 1);
+  const int ixs = 2 * x0, iys = 2 * y0;
+  const float4 *__restrict__ vel = d.vel4[cur];
+  // The node phase's inputs do not depend on the element phase: start their
+  // copies now, so that they arrive while the elements are computed.
+  for (int i = tid; i < TNW * TNH; i += FTX * FTY) {
+    const int r = i / TNW, c = i - r * TNW;
+    const int gx = ixs + c, gy = iys + r;
+    if (gx < d.nw && gy < d.nh) {
+      const size_t node = (size_t)gy * d.nw + gx;
+      cp_async16(sv + i, vel + node);
+      cp_async16(sk + i, d.nodec4 + node);
+    }
+  }
+  cp_async_commit();
   const int kx = x0 - 1 + lx, ky = y0 - 1 + ly;
   const bool active = kx >= 0 && ky >= 0 && kx < d.nx && ky < d.ny;
-  float fx[9], fy[9];
+  float2 f[9];
   if (active) {
-    element_mix<NS>(d, ma, kx, ky, cur, lx >= 1 && ly >= 1, fx, fy);
+    const size_t K = (size_t)ky * d.nx + kx;
+    float S11[NS], S12[NS], S22[NS];
+    load_stress<NS>(d, cur, K, S11, S12, S22);
+    const float P = __ldg(d.Pe32 + K);
+    const size_t base = (size_t)(2 * ky) * d.nw + 2 * kx;
+    float4 pv[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pv[c + 3 * b] = __ldg(vel + base + (size_t)b * d.nw + c);
+    float hx, ihx, hy, ihy;
+    line_geometry(d, kx, ky, hx, ihx, hy, ihy);
+    float fx[9], fy[9];
+    element_core<NS>(pv, S11, S12, S22, P, hx, ihx, hy, ihy, ma, fx, fy);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) f[j] = make_float2(fx[j], fy[j]);
+    if (lx >= 1 && ly >= 1) store_stress<NS>(d, cur, K, S11, S12, S22);
   } else {
 #pragma unroll
-    for (int j = 0; j < 9; ++j) fx[j] = fy[j] = 0.f;
+    for (int j = 0; j < 9; ++j) f[j] = make_float2(0.f, 0.f);
   }
 #pragma unroll
-  for (int j = 0; j < 9; ++j) {
-    fs[j][ly][lx] = fx[j];
-    fs[9 + j][ly][lx] = fy[j];
-  }
+  for (int j = 0; j < 9; ++j) fs[j][ly][lx] = f[j];
+  cp_async_wait_all();
   __syncthreads();
-  const int ixs = 2 * x0, iys = 2 * y0;
-  const int ixe = (x0 + FTX - 1 >= d.nx) ? d.nw : ixs + 2 * (FTX - 1);
-  const int iye = (y0 + FTY - 1 >= d.ny) ? d.nh : iys + 2 * (FTY - 1);
-  const int wx = ixe - ixs, wy = iye - iys;
-  float2 *__restrict__ vq = d.vel2[cur ^ 1];
-  const size_t nn = d.nn;
-  for (int t = ly * FTX + lx; t < wx * wy; t += FTX * FTY) {
-    const int ty_ = t / wx;
-    const int ix = ixs + (t - ty_ * wx), iy = iys + ty_;
+  const int ixe = (x0 + FTX - 1 >= d.nx) ? d.nw : ixs + TNW;
+  const int iye = (y0 + FTY - 1 >= d.ny) ? d.nh : iys + TNH;
+  float4 *__restrict__ vq = d.vel4[cur ^ 1];
+  // interior window first (constant width: cheap index arithmetic) ...
+  for (int t = tid; t < TNW * TNH; t += FTX * FTY) {
+    const int r = t / TNW;
+    const int ix = ixs + (t - r * TNW), iy = iys + r;
+    if (ix >= ixe || iy >= iye) continue;
     const size_t node = (size_t)iy * d.nw + ix;
     if (ix == 0 || iy == 0 || ix == d.nw - 1 || iy == d.nh - 1) {
-      vq[node] = make_float2(0.f, 0.f);
-      vq[nn + node] = make_float2(0.f, 0.f);
+      vq[node] = make_float4(0.f, 0.f, 0.f, 0.f);
       continue;
     }
     // local tile coordinates of the element whose lower-left node is (ix, iy)
     const int ex = (ix >> 1) - x0 + 1, ey = (iy >> 1) - y0 + 1;
-    float tx[4] = {0.f, 0.f, 0.f, 0.f}, tyv[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 tf[4];
     int n;
     const bool odd_x = ix & 1, odd_y = iy & 1;
     if (!odd_x && !odd_y) {  // vertex: SW, SE, NW, NE
-      tx[0] = fs[8][ey - 1][ex - 1]; tx[1] = fs[6][ey - 1][ex];
-      tx[2] = fs[2][ey][ex - 1];     tx[3] = fs[0][ey][ex];
-      tyv[0] = fs[17][ey - 1][ex - 1]; tyv[1] = fs[15][ey - 1][ex];
-      tyv[2] = fs[11][ey][ex - 1];     tyv[3] = fs[9][ey][ex];
+      tf[0] = fs[8][ey - 1][ex - 1]; tf[1] = fs[6][ey - 1][ex];
+      tf[2] = fs[2][ey][ex - 1];     tf[3] = fs[0][ey][ex];
       n = 4;
     } else if (odd_x && !odd_y) {  // horizontal edge: S, N
-      tx[0] = fs[7][ey - 1][ex]; tx[1] = fs[1][ey][ex];
-      tyv[0] = fs[16][ey - 1][ex]; tyv[1] = fs[10][ey][ex];
+      tf[0] = fs[7][ey - 1][ex]; tf[1] = fs[1][ey][ex];
       n = 2;
     } else if (!odd_x && odd_y) {  // vertical edge: W, E
-      tx[0] = fs[5][ey][ex - 1]; tx[1] = fs[3][ey][ex];
-      tyv[0] = fs[14][ey][ex - 1]; tyv[1] = fs[12][ey][ex];
+      tf[0] = fs[5][ey][ex - 1]; tf[1] = fs[3][ey][ex];
       n = 2;
     } else {  // centre
-      tx[0] = fs[4][ey][ex];
-      tyv[0] = fs[13][ey][ex];
+      tf[0] = fs[4][ey][ex];
       n = 1;
     }
-    node_update_mix(d, ma, cur, node, tx, tyv, n);
+    vq[node] = node_update_mix(ma, sv[t], sk[t], ocean(d, ma, node), tf, n);
   }
+  // ... then the domain's last boundary column / row, owned by the last tiles
+  if (ixe == d.nw)
+    for (int iy = iys + tid; iy < iye; iy += FTX * FTY)
+      vq[(size_t)iy * d.nw + d.nw - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (iye == d.nh)
+    for (int ix = ixs + tid; ix < ixe; ix += FTX * FTY)
+      vq[(size_t)(d.nh - 1) * d.nw + ix] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ---- conversions between the FP64 staging buffers and the FP32 state ----
 // v (FP64) -> (hi, lo) with hi = fl32(v), lo = fl32(v - hi).
 __global__ void k_vel_split(DevState d, int cur) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * (size_t)d.nn) return;
-  const double v = d.vel[cur][i];
-  const float hi = __double2float_rn(v);
-  const float lo = __double2float_rn(v - (double)hi);
-  d.vel2[cur][i] = make_float2(hi, lo);
+  if (i >= (size_t)d.nn) return;
+  const double u = d.vel[cur][i], v = d.vel[cur][(size_t)d.nn + i];
+  const float uh = __double2float_rn(u), vh = __double2float_rn(v);
+  d.vel4[cur][i] = make_float4(uh, __double2float_rn(u - (double)uh), vh,
+                               __double2float_rn(v - (double)vh));
 }
 
 __global__ void k_vel_join(DevState d, int cur) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * (size_t)d.nn) return;
-  const float2 p = d.vel2[cur][i];
+  if (i >= (size_t)d.nn) return;
+  const float4 p = d.vel4[cur][i];
   d.vel[cur][i] = (double)p.x + (double)p.y;
+  d.vel[cur][(size_t)d.nn + i] = (double)p.z + (double)p.w;
 }
 
 __global__ void k_stress_to_f32(DevState d, int cur) {
@@ -339,27 +392,42 @@ __global__ void k_consts_to_f32(DevState d, double dt, int has_vo) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nn = d.nn;
   if (i < nn) {
-    d.nodec32[0 * nn + i] = __double2float_rn(d.mass[i] / dt);
-    d.nodec32[1 * nn + i] = __double2float_rn(d.nodec[3 * nn + i]);
-    d.nodec32[2 * nn + i] = __double2float_rn(d.nodec[4 * nn + i]);
-    d.nodec32[3 * nn + i] = __double2float_rn(d.nodec[5 * nn + i]);
+    d.nodec4[i] = make_float4(__double2float_rn(d.mass[i] / dt),
+                              __double2float_rn(d.nodec[3 * nn + i]),
+                              __double2float_rn(d.nodec[4 * nn + i]),
+                              __double2float_rn(d.nodec[5 * nn + i]));
     if (has_vo)
       d.vo2[i] = make_float2(__double2float_rn(d.vo[i]), __double2float_rn(d.vo[nn + i]));
   }
   if (i < (size_t)d.ne) d.Pe32[i] = __double2float_rn(d.Pe[i]);
+  if (i < (size_t)d.nx)
+    d.lines32[i] = make_float2(__double2float_rn(d.lines[i]), __double2float_rn(d.lines[d.nx + i]));
+  if (i < (size_t)d.ny)
+    d.lines32[d.nx + i] = make_float2(__double2float_rn(d.lines[2 * d.nx + i]),
+                                      __double2float_rn(d.lines[2 * d.nx + d.ny + i]));
 }
 
 inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
 }  // namespace
 
+cudaError_t setup_mixed_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_subcycle_mix<3>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kFusedSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_subcycle_mix<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFusedSmem);
+  return e;
+}
+
 cudaError_t launch_vel_split(const DevState &d, int cur, cudaStream_t st) {
-  k_vel_split<<<blocks(2LL * d.nn, 256), 256, 0, st>>>(d, cur);
+  k_vel_split<<<blocks(d.nn, 256), 256, 0, st>>>(d, cur);
   return cudaGetLastError();
 }
 
 cudaError_t launch_vel_join(const DevState &d, int cur, cudaStream_t st) {
-  k_vel_join<<<blocks(2LL * d.nn, 256), 256, 0, st>>>(d, cur);
+  k_vel_join<<<blocks(d.nn, 256), 256, 0, st>>>(d, cur);
   return cudaGetLastError();
 }
 
@@ -375,10 +443,12 @@ cudaError_t launch_stress_to_f64(const DevState &d, int cur, cudaStream_t st) {
 
 cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                                  cudaStream_t st) {
-  k_vel_join<<<blocks(2LL * d.nn, 256), 256, 0, st>>>(d, cur);
+  k_vel_join<<<blocks(d.nn, 256), 256, 0, st>>>(d, cur);
   cudaError_t e = launch_prepare(d, p, has_vo, cur, st);
   if (e != cudaSuccess) return e;
-  const long long n = d.nn > d.ne ? d.nn : d.ne;
+  long long n = d.nn > d.ne ? d.nn : d.ne;
+  if (n < d.nx) n = d.nx;
+  if (n < d.ny) n = d.ny;
   k_consts_to_f32<<<blocks(n, 256), 256, 0, st>>>(d, p.dt, has_vo ? 1 : 0);
   return cudaGetLastError();
 }
@@ -399,9 +469,9 @@ cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_p
     const dim3 grid((d.nx + FTX - 2) / (FTX - 1), (d.ny + FTY - 2) / (FTY - 1));
     const dim3 block(FTX, FTY);
     if (d.ns == 3)
-      k_subcycle_mix<3><<<grid, block, 0, st>>>(d, a, cur);
+      k_subcycle_mix<3><<<grid, block, kFusedSmem, st>>>(d, a, cur);
     else
-      k_subcycle_mix<6><<<grid, block, 0, st>>>(d, a, cur);
+      k_subcycle_mix<6><<<grid, block, kFusedSmem, st>>>(d, a, cur);
     if (ev) cudaEventRecord(ev[1], st);
     if (ev) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
