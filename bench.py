@@ -308,9 +308,107 @@ def run_ours(a):
         return _run_ours(a, torch, dist, ws, rank)
 
 
+def run_ensemble(a, torch, dist, ws, rank):
+    """Ensemble workload: all members advanced together (one persistent
+    launch per subcycle in the mixed precision), tile shape autotuned."""
+    from paper_2402_00466_gb300 import mevp
+
+    dev = torch.cuda.current_device()
+    members = W.make_ensemble(a.workload)
+    n_sub = members[0]["n_sub"]
+    units_step = sum(c["nx"] * c["ny"] for c in members) * n_sub
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    states = []
+    for c in members:
+        st = mevp.State(c["nx"], c["ny"], c["n_s"], vertex_xy=c["xy"], precision=a.precision,
+                        params=c["params"])
+        st.set_ice(c["H"], c["A"])
+        st.set_forcing(c["tau"])
+        st.set_velocity(c["vel0"])
+        st.set_stress(c["S0"])
+        states.append(st)
+    ens = mevp.Ensemble(states)
+    ens.begin_step()
+    shape = ens.autotune(10)
+    shapes = mevp.mevp_ensemble_shapes(a.precision)
+
+    def timed(step, steps, warmup):
+        for _ in range(warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record()
+            step()
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        return sum(s_.elapsed_time(e_) for s_, e_ in evs)
+
+    def ens_step():
+        ens.begin_step()
+        ens.run_subcycles(n_sub)
+
+    def seq_step():  # the same members one state at a time
+        for st in states:
+            st.begin_step()
+            st.run_subcycles(n_sub)
+
+    clocks = Clocks(dev)
+    clocks.start()
+    total_ms = timed(ens_step, a.steps, a.warmup)
+    clk = clocks.stop()
+    seq_ms = timed(seq_step, 1, 1)
+    value = ws * units_step * a.steps / (total_ms / 1e3)
+    sub_s = total_ms / 1e3 / (a.steps * n_sub)
+    hbm_peak, hbm_kind = load_peaks()
+    roofline = None
+    if a.precision == "mixed":
+        byts = sum(c["nx"] * c["ny"] * MIXED_SURVEY_BYTES[c["n_s"]] for c in members)
+        ach = byts / sub_s / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": None,
+                    "kernel": "k_ens_mix<%d,%d>" % shapes[shape],
+                    "bytes_per_element": "SURVEY 8(d): 424 (DG2) / 352 (DG1)",
+                    "peak_kind": hbm_kind}
+    else:
+        flops = sum(c["nx"] * c["ny"] * ELEM_FLOPS[c["n_s"]] for c in members)
+        ach = flops / sub_s / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "k_ens_f64_elem<%d> + k_ens_f64_node" % shapes[shape][0],
+                    "note": "whole subcycle (element + node launch) timed"}
+    for st in states:
+        st.close()
+    ens.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": a.workload, "members": len(members),
+                   "elements": sum(c["nx"] * c["ny"] for c in members),
+                   "dg2_members": sum(c["n_s"] == 6 for c in members), "n_sub": n_sub,
+                   "precision": a.precision, "shape": shapes[shape],
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "roofline": roofline, "sequential_ms_per_step": seq_ms,
+        "speedup_vs_sequential": seq_ms / (total_ms / a.steps),
+        "gpu_launches": a.steps * (len(members) * (5 if a.precision == "mixed" else 3) +
+                                   n_sub * (1 if a.precision == "mixed" else 2)),
+        "clocks": clk, "cpu_baseline": None, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def _run_ours(a, torch, dist, ws, rank):
     from paper_2402_00466_gb300 import mevp
 
+    if a.workload in W.ENSEMBLES:
+        return run_ensemble(a, torch, dist, ws, rank)
     dev = torch.cuda.current_device()
 
     def barrier():
@@ -426,7 +524,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="mesh256_dg2", choices=sorted(W.CONFIGS))
+    ap.add_argument("--workload", default="mesh256_dg2",
+                    choices=sorted(W.CONFIGS) + sorted(W.ENSEMBLES))
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -199,6 +199,44 @@ enum {
 };
 MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
 
+/* ---- Ensembles ------------------------------------------------------------
+ * Many independent domains advanced together, for ensembles of uneven
+ * domains (sizes, DG1/DG2, parameters may differ per member).  The members
+ * are existing states that share one precision, one device and one stream;
+ * the ensemble borrows them (they must outlive it) and they remain usable on
+ * their own.  Per subcycle, MEVP_MIXED issues one persistent launch over the
+ * (member, tile) work list of all members; MEVP_FP64 issues a persistent
+ * element launch and a persistent node launch.  Results are bitwise those of
+ * stepping each member alone.  The ensemble allocates small device tables
+ * (cudaMalloc) for its member descriptors and work lists. */
+typedef struct mevp_ensemble mevp_ensemble; /* opaque, library-owned */
+
+MEVP_API int mevp_ensemble_create(mevp_state *const *members, int n, mevp_ensemble **out);
+MEVP_API void mevp_ensemble_destroy(mevp_ensemble *ensemble);
+
+/* mevp_begin_step on every member. */
+MEVP_API int mevp_ensemble_begin_step(mevp_ensemble *ensemble);
+
+/* n subcycles of every member (runs of 4 or more replayed as CUDA graphs on
+ * a non-default stream, as for a single state).  Asynchronous. */
+MEVP_API int mevp_ensemble_run_subcycles(mevp_ensemble *ensemble, int n);
+
+/* Work decomposition candidates: MEVP_MIXED tile shapes (elements, x by y),
+ * MEVP_FP64 element block sizes (threads, 1).  dims receives up to max
+ * (x, y) pairs; count the number of candidates. */
+MEVP_API int mevp_ensemble_shapes(int precision, int *dims, int max, int *count);
+MEVP_API int mevp_ensemble_set_shape(mevp_ensemble *ensemble, int shape);
+
+/* Time trial_subcycles (after 2 warm-up subcycles) with every candidate
+ * shape on the ensemble itself, keep the fastest and return its index in
+ * *best (may be NULL).  The members' velocity and stress are copied to a
+ * temporary device buffer (cudaMalloc) first and restored afterwards, so the
+ * trials leave no trace in the results.  Synchronises the stream. */
+MEVP_API int mevp_ensemble_autotune(mevp_ensemble *ensemble, int trial_subcycles, int *best);
+
+/* 1 (default): replay runs of subcycles as CUDA graphs; 0: direct launches. */
+MEVP_API int mevp_ensemble_set_graphs(mevp_ensemble *ensemble, int on);
+
 /* Size of the static device scratch used by mevp_run_subcycles_noalloc. */
 #define MEVP_NOALLOC_SCRATCH_BYTES (8u << 20)
 

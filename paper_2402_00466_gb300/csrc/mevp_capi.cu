@@ -18,34 +18,6 @@
 using mevp::DevState;
 using mevp::Rheo;
 
-struct mevp_state {
-  const mevp_mesh *mesh = nullptr;
-  int ns = 0, na = 0, prec = 0;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  void *ws = nullptr;
-  size_t ws_bytes = 0;
-  bool owns_ws = false;
-  DevState d{};
-  int cur = 0;
-  mevp_params prm{};
-  Rheo rheo{};
-  bool have_params = false;
-  bool prepared = false;
-  bool has_vo = false;
-  bool fused = true;  // mixed precision: one fused launch per subcycle
-  bool use_graphs = true;  // replay captured subcycle chunks (non-default streams)
-  struct Graph {
-    int parity, len;
-    cudaGraphExec_t exec;
-  };
-  std::vector<Graph> graphs;  // instantiated chunks, dropped when kernel arguments change
-  // event timing (benchmarks)
-  int timing = 0;                   // sampling stride (0 = off)
-  long long timed_calls = 0;        // subcycles launched since timing was enabled
-  std::vector<cudaEvent_t> events;  // pool, 3 per timed subcycle
-  size_t ev_used = 0;
-};
 
 namespace {
 
@@ -64,6 +36,15 @@ int fail(int code, const char *fmt, ...) {
 int cuda_fail(cudaError_t e, const char *what) {
   return fail(MEVP_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+}  // namespace
+
+namespace mevp {
+int api_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+int api_cuda_fail(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+}  // namespace mevp
+
+namespace {
 
 #define MEVP_CUDA(call, what)                    \
   do {                                           \
@@ -129,7 +110,9 @@ bool finite_all(const double *p, size_t n) {
   return true;
 }
 
-int check_state(const mevp_state *s) {
+}  // namespace
+
+int mevp::api_check_state(const mevp_state *s) {
   if (!s) return fail(MEVP_ERR_ARG, "state is NULL");
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -138,6 +121,10 @@ int check_state(const mevp_state *s) {
     return fail(MEVP_ERR_STATE, "current device %d is not the state's device %d", dev, s->device);
   return MEVP_OK;
 }
+
+namespace {
+
+int check_state(const mevp_state *s) { return mevp::api_check_state(s); }
 
 // Copy n doubles into device buffer dst on the state's stream.
 int copy_in(mevp_state *s, double *dst, const double *src, size_t n, int on_device,

@@ -58,10 +58,10 @@ __device__ __forceinline__ void strain_dg(const double u[9], const double v[9], 
   }
 }
 
+// One element of the FP64 subcycle (strain, stress update in place, element
+// forces into the force buffer).
 template <int NS>
-__global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, int cur) {
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K >= d.ne) return;
+__device__ __forceinline__ void elem_f64(const DevState &d, const Rheo &r, int cur, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
   const double hx = __ldg(d.lines + kx), ihx = __ldg(d.lines + d.nx + kx);
   const double hy = __ldg(d.lines + 2 * d.nx + ky), ihy = __ldg(d.lines + 2 * d.nx + d.ny + ky);
@@ -92,6 +92,12 @@ __global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, 
     d.fbuf[(size_t)j * d.ne + K] = fx[j];
     d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
   }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, int cur) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K < d.ne) elem_f64<NS>(d, r, cur, K);
 }
 
 // Sum of the element forces at node (ix, iy) over the elements that contain
@@ -125,16 +131,10 @@ __device__ __forceinline__ void gather_force(const double *__restrict__ fb, int 
   }
 }
 
-// Velocity update at an interior node (Eq. 2 with the mEVP beta relaxation;
-// drag coefficient lagged, drag and Coriolis implicit):
-//   a = m(1+beta)/dt + c,  b = m f,  c = l Cw rho_w |v_o - v^{p-1}|
-//   r = m beta/dt v^{p-1} + (m/dt v^n + l tau) + F + c v_o
-//   (a + i b) v^p = r   (complex notation)
-__global__ void __launch_bounds__(kNodeBlock) k_node_f64(DevState d, int cur, int has_vo) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  const int sw = d.nx + 1;
-  if (slot >= sw * (d.ny + 1)) return;
-  const int ky = slot / sw, kx = slot - ky * sw;
+// The up-to-four CG2 nodes (2kx + dx, 2ky + dy), dx, dy in {0,1}, of node
+// slot (kx, ky): force gather and velocity update.
+__device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int has_vo, int kx,
+                                              int ky) {
   const double *__restrict__ vp = d.vel[cur];
   double *__restrict__ vq = d.vel[cur ^ 1];
   const size_t nn = d.nn;
@@ -199,6 +199,50 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_f64(DevState d, int cur, in
       vq[node] = ux;
       vq[nn + node] = uy;
     }
+  }
+}
+
+// Velocity update at an interior node (Eq. 2 with the mEVP beta relaxation;
+// drag coefficient lagged, drag and Coriolis implicit):
+//   a = m(1+beta)/dt + c,  b = m f,  c = l Cw rho_w |v_o - v^{p-1}|
+//   r = m beta/dt v^{p-1} + (m/dt v^n + l tau) + F + c v_o
+//   (a + i b) v^p = r   (complex notation)
+__global__ void __launch_bounds__(kNodeBlock) k_node_f64(DevState d, int cur, int has_vo) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sw = d.nx + 1;
+  if (slot >= sw * (d.ny + 1)) return;
+  const int ky = slot / sw, kx = slot - ky * sw;
+  node_slot_f64(d, cur, has_vo, kx, ky);
+}
+
+// Ensemble kernels: persistent, grid-stride over (member, block) work items.
+template <int B>
+__global__ void __launch_bounds__(B) k_ens_f64_elem(const EnsMember *__restrict__ mem,
+                                                    const EnsWork *__restrict__ work, int nwork,
+                                                    int flip) {
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const EnsWork it = work[w];
+    const EnsMember &m = mem[it.member];
+    const int K = it.tx * B + threadIdx.x;
+    if (K >= m.d.ne) continue;
+    if (m.d.ns == 3)
+      elem_f64<3>(m.d, m.r, m.base_cur ^ flip, K);
+    else
+      elem_f64<6>(m.d, m.r, m.base_cur ^ flip, K);
+  }
+}
+
+__global__ void __launch_bounds__(kNodeBlock) k_ens_f64_node(const EnsMember *__restrict__ mem,
+                                                             const EnsWork *__restrict__ work,
+                                                             int nwork, int flip) {
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const EnsWork it = work[w];
+    const EnsMember &m = mem[it.member];
+    const int slot = it.tx * kNodeBlock + threadIdx.x;
+    const int sw = m.d.nx + 1;
+    if (slot >= sw * (m.d.ny + 1)) continue;
+    const int ky = slot / sw, kx = slot - ky * sw;
+    node_slot_f64(m.d, m.base_cur ^ flip, m.has_vo, kx, ky);
   }
 }
 
@@ -337,6 +381,43 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
   k_node_f64<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, cur, has_vo ? 1 : 0);
   if (ev) cudaEventRecord(ev[2], st);
   return cudaGetLastError();
+}
+
+// FP64 ensemble element block sizes the autotuner chooses from.
+const int kF64Blocks[kF64BlockCount] = {64, 128, 256};
+
+cudaError_t launch_ensemble_f64(const EnsMember *mem, const EnsWork *ework, int nework,
+                                const EnsWork *nwork_list, int nnwork, int block, int grid_e,
+                                int grid_n, int flip, cudaStream_t st) {
+  switch (block) {
+    case 0:
+      k_ens_f64_elem<64><<<grid_e, 64, 0, st>>>(mem, ework, nework, flip);
+      break;
+    case 1:
+      k_ens_f64_elem<128><<<grid_e, 128, 0, st>>>(mem, ework, nework, flip);
+      break;
+    default:
+      k_ens_f64_elem<256><<<grid_e, 256, 0, st>>>(mem, ework, nework, flip);
+      break;
+  }
+  k_ens_f64_node<<<grid_n, kNodeBlock, 0, st>>>(mem, nwork_list, nnwork, flip);
+  return cudaGetLastError();
+}
+
+int f64_block_ctas_per_sm(int block) {
+  int n = 0;
+  switch (block) {
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<64>, 64, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<128>, 128, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<256>, 256, 0); break;
+  }
+  return n > 0 ? n : 1;
+}
+
+int f64_node_ctas_per_sm() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_node, kNodeBlock, 0);
+  return n > 0 ? n : 1;
 }
 
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st) {

@@ -75,6 +75,26 @@ struct DevState {
   float2 *lines32;     // [nx + ny] (h, 1/h) per mesh column, then per row
 };
 
+// Scalar constants of the mixed-precision kernels (FP32).
+struct MixArgs {
+  float ie, hainv, dmin2, fac;  // stress update
+  float opb, fdt;               // 1 + beta, f dt (velocity update)
+  int has_vo;
+};
+
+// Ensemble member as the persistent kernels see it.
+struct EnsMember {
+  DevState d;
+  MixArgs ma;    // mixed precision
+  Rheo r;        // FP64
+  int has_vo;
+  int base_cur;  // velocity/stress buffer at flip = 0
+};
+struct EnsWork {
+  int member;
+  int tx, ty;  // tile (mixed) or block index (FP64, in tx)
+};
+
 // Launchers (return cudaGetLastError of the launch).
 cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                            cudaStream_t st);
@@ -84,7 +104,25 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
                                 cudaStream_t st, cudaEvent_t *ev);
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
 
+// FP64 ensemble: persistent element kernel (block size chosen from
+// kF64Blocks) + persistent node kernel (256 threads), over their work lists
+constexpr int kF64BlockCount = 3;
+extern const int kF64Blocks[kF64BlockCount];
+constexpr int kNodeSlotBlock = 256;
+cudaError_t launch_ensemble_f64(const EnsMember *mem, const EnsWork *ework, int nework,
+                                const EnsWork *nwork_list, int nnwork, int block, int grid_e,
+                                int grid_n, int flip, cudaStream_t st);
+int f64_block_ctas_per_sm(int block);
+int f64_node_ctas_per_sm();
+
 // mixed precision
+constexpr int kMixTileCount = 3;
+extern const int kMixTiles[kMixTileCount][2];
+MixArgs make_mixargs(const Rheo &r, const mevp_params &p, bool has_vo);
+int mixed_tile_count(int tile, int nx, int ny, int *tiles_x, int *tiles_y);
+int mixed_tile_ctas_per_sm(int tile);
+cudaError_t launch_ensemble_mixed(const EnsMember *mem, const EnsWork *work, int nwork, int tile,
+                                  int grid, int flip, cudaStream_t st);
 cudaError_t setup_mixed_kernels();  // once per device, before any capture
 cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                                  cudaStream_t st);
@@ -97,4 +135,43 @@ cudaError_t launch_stress_to_f32(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_stress_to_f64(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_diag(const DevState &d, cudaStream_t st);
 
+// Error reporting shared by the C-ABI translation units (sets the thread-local
+// message returned by mevp_last_error and returns the code).
+int api_fail(int code, const char *msg);
+int api_cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace mevp
+
+// Host-side state behind the opaque mevp_state handle.
+struct mevp_state {
+  const mevp_mesh *mesh = nullptr;
+  int ns = 0, na = 0, prec = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = false;
+  mevp::DevState d{};
+  int cur = 0;
+  mevp_params prm{};
+  mevp::Rheo rheo{};
+  bool have_params = false;
+  bool prepared = false;
+  bool has_vo = false;
+  bool fused = true;  // mixed precision: one fused launch per subcycle
+  bool use_graphs = true;  // replay captured subcycle chunks (non-default streams)
+  struct Graph {
+    int parity, len;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;  // instantiated chunks, dropped when kernel arguments change
+  // event timing (benchmarks)
+  int timing = 0;                   // sampling stride (0 = off)
+  long long timed_calls = 0;        // subcycles launched since timing was enabled
+  std::vector<cudaEvent_t> events;  // pool, 3 per timed subcycle
+  size_t ev_used = 0;
+};
+
+namespace mevp {
+int api_check_state(const mevp_state *s);
 }  // namespace mevp

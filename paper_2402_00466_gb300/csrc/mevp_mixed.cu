@@ -57,11 +57,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-struct MixArgs {
-  float ie, hainv, dmin2, fac;  // stress update
-  float opb, fdt;               // 1 + beta, f dt (velocity update)
-  int has_vo;
-};
+
 
 // Element step in FP32 from the 9 nodal velocity records (u_hi, u_lo, v_hi,
 // v_lo) and the element's stress (in/out): strain from pair differences
@@ -245,34 +241,37 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma,
 }
 
 // ---- fused subcycle ---------------------------------------------------------
-// A CTA takes a FTX x FTY block of elements: the (FTX-1) x (FTY-1) elements it
+// A CTA takes a TX x TY block of elements: the (TX-1) x (TY-1) elements it
 // owns plus one halo column to the west and one halo row to the south,
 // recomputed from S^{p-1} and v^{p-1} so that every node the CTA owns -- ix in
-// [2 x0, 2 x0 + 2(FTX-1)), iy likewise, plus the last boundary row/column of
+// [2 x0, 2 x0 + 2(TX-1)), iy likewise, plus the last boundary row/column of
 // the domain -- sees all of its element forces without an exchange.  The
 // stress is ping-ponged (halo readers need S^{p-1}).
-constexpr int FTX = 32, FTY = 16;
-constexpr int TNW = 2 * (FTX - 1), TNH = 2 * (FTY - 1);  // owned-node window
-constexpr size_t kFusedSmem = sizeof(float4) * 2 * TNW * TNH + sizeof(float2) * 9 * FTX * FTY;
-
-// The element phase loads straight from global memory, so each warp proceeds
+//
+// The element stage loads straight from global memory, so each warp proceeds
 // as soon as its own loads arrive (staging the whole tile into shared memory
 // first, behind a barrier, measured slower: 106 vs 91 us per subcycle at
 // 1024^2).  The owned nodes' velocity and constant records, needed only by
-// the node phase, are copied into shared memory asynchronously from the start.
-template <int NS>
-__global__ void __launch_bounds__(FTX *FTY) k_subcycle_mix(DevState d, MixArgs ma, int cur) {
-  extern __shared__ float4 smem[];
+// the node stage, are copied into shared memory asynchronously from the start.
+template <int TX, int TY> struct Tile {
+  static constexpr int NW = 2 * (TX - 1), NH = 2 * (TY - 1);  // owned-node window
+  static constexpr size_t smem = sizeof(float4) * 2 * NW * NH + sizeof(float2) * 9 * TX * TY;
+};
+
+template <int NS, int TX, int TY>
+__device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, int cur, int bx,
+                                         int by, float4 *smem) {
+  constexpr int TNW = Tile<TX, TY>::NW, TNH = Tile<TX, TY>::NH;
   float4 *sv = smem;              // [TNH][TNW] velocity records of the owned nodes
   float4 *sk = sv + TNW * TNH;    // [TNH][TNW] constant records of the owned nodes
-  float2(*fs)[FTY][FTX] = (float2(*)[FTY][FTX])(sk + TNW * TNH);  // [9][FTY][FTX] forces
-  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * FTX + lx;
-  const int x0 = blockIdx.x * (FTX - 1), y0 = blockIdx.y * (FTY - 1);
+  float2(*fs)[TY][TX] = (float2(*)[TY][TX])(sk + TNW * TNH);  // [9][TY][TX] forces
+  const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
+  const int x0 = bx * (TX - 1), y0 = by * (TY - 1);
   const int ixs = 2 * x0, iys = 2 * y0;
   const float4 *__restrict__ vel = d.vel4[cur];
-  // The node phase's inputs do not depend on the element phase: start their
+  // The node stage's inputs do not depend on the element stage: start their
   // copies now, so that they arrive while the elements are computed.
-  for (int i = tid; i < TNW * TNH; i += FTX * FTY) {
+  for (int i = tid; i < TNW * TNH; i += TX * TY) {
     const int r = i / TNW, c = i - r * TNW;
     const int gx = ixs + c, gy = iys + r;
     if (gx < d.nw && gy < d.nh) {
@@ -311,11 +310,11 @@ __global__ void __launch_bounds__(FTX *FTY) k_subcycle_mix(DevState d, MixArgs m
   for (int j = 0; j < 9; ++j) fs[j][ly][lx] = f[j];
   cp_async_wait_all();
   __syncthreads();
-  const int ixe = (x0 + FTX - 1 >= d.nx) ? d.nw : ixs + TNW;
-  const int iye = (y0 + FTY - 1 >= d.ny) ? d.nh : iys + TNH;
+  const int ixe = (x0 + TX - 1 >= d.nx) ? d.nw : ixs + TNW;
+  const int iye = (y0 + TY - 1 >= d.ny) ? d.nh : iys + TNH;
   float4 *__restrict__ vq = d.vel4[cur ^ 1];
   // interior window first (constant width: cheap index arithmetic) ...
-  for (int t = tid; t < TNW * TNH; t += FTX * FTY) {
+  for (int t = tid; t < TNW * TNH; t += TX * TY) {
     const int r = t / TNW;
     const int ix = ixs + (t - r * TNW), iy = iys + r;
     if (ix >= ixe || iy >= iye) continue;
@@ -347,11 +346,40 @@ __global__ void __launch_bounds__(FTX *FTY) k_subcycle_mix(DevState d, MixArgs m
   }
   // ... then the domain's last boundary column / row, owned by the last tiles
   if (ixe == d.nw)
-    for (int iy = iys + tid; iy < iye; iy += FTX * FTY)
+    for (int iy = iys + tid; iy < iye; iy += TX * TY)
       vq[(size_t)iy * d.nw + d.nw - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (iye == d.nh)
-    for (int ix = ixs + tid; ix < ixe; ix += FTX * FTY)
+    for (int ix = ixs + tid; ix < ixe; ix += TX * TY)
       vq[(size_t)(d.nh - 1) * d.nw + ix] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+constexpr int FTX = 32, FTY = 16;  // single-domain tile
+constexpr size_t kFusedSmem = Tile<FTX, FTY>::smem;
+
+template <int NS>
+__global__ void __launch_bounds__(FTX *FTY) k_subcycle_mix(DevState d, MixArgs ma, int cur) {
+  extern __shared__ float4 smem[];
+  mix_tile<NS, FTX, FTY>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+}
+
+// Ensemble: one persistent launch per subcycle over the (member, tile) work
+// list of all members (largest work first).  Member m runs on velocity /
+// stress buffer base_cur(m) ^ flip.
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY)) k_ens_mix(const EnsMember *__restrict__ mem,
+                                                    const EnsWork *__restrict__ work, int nwork,
+                                                    int flip) {
+  extern __shared__ float4 smem[];
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const EnsWork it = work[w];
+    const EnsMember &m = mem[it.member];
+    const int cur = m.base_cur ^ flip;
+    if (m.d.ns == 3)
+      mix_tile<3, TX, TY>(m.d, m.ma, cur, it.tx, it.ty, smem);
+    else
+      mix_tile<6, TX, TY>(m.d, m.ma, cur, it.tx, it.ty, smem);
+    __syncthreads();  // the next tile reuses the shared memory
+  }
 }
 
 // ---- conversions between the FP64 staging buffers and the FP32 state ----
@@ -418,7 +446,59 @@ cudaError_t setup_mixed_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_subcycle_mix<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kFusedSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ens_mix<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<32, 8>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ens_mix<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<32, 16>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ens_mix<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<64, 8>::smem);
   return e;
+}
+
+// Mixed ensemble tile shapes (TX, TY) the autotuner chooses from.
+const int kMixTiles[kMixTileCount][2] = {{32, 8}, {32, 16}, {64, 8}};
+
+int mixed_tile_count(int tile, int nx, int ny, int *tiles_x, int *tiles_y) {
+  const int tx = kMixTiles[tile][0], ty = kMixTiles[tile][1];
+  *tiles_x = (nx + tx - 2) / (tx - 1);
+  *tiles_y = (ny + ty - 2) / (ty - 1);
+  return *tiles_x * *tiles_y;
+}
+
+cudaError_t launch_ensemble_mixed(const EnsMember *mem, const EnsWork *work, int nwork, int tile,
+                                  int grid, int flip, cudaStream_t st) {
+  switch (tile) {
+    case 0:
+      k_ens_mix<32, 8><<<grid, dim3(32, 8), Tile<32, 8>::smem, st>>>(mem, work, nwork, flip);
+      break;
+    case 1:
+      k_ens_mix<32, 16><<<grid, dim3(32, 16), Tile<32, 16>::smem, st>>>(mem, work, nwork, flip);
+      break;
+    default:
+      k_ens_mix<64, 8><<<grid, dim3(64, 8), Tile<64, 8>::smem, st>>>(mem, work, nwork, flip);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+int mixed_tile_ctas_per_sm(int tile) {
+  int n = 0;
+  switch (tile) {
+    case 0:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<32, 8>, 256, Tile<32, 8>::smem);
+      break;
+    case 1:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<32, 16>, 512,
+                                                    Tile<32, 16>::smem);
+      break;
+    default:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<64, 8>, 512, Tile<64, 8>::smem);
+      break;
+  }
+  return n > 0 ? n : 1;
 }
 
 cudaError_t launch_vel_split(const DevState &d, int cur, cudaStream_t st) {
@@ -453,9 +533,7 @@ cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool h
   return cudaGetLastError();
 }
 
-cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
-                                  bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
-                                  bool fused) {
+MixArgs make_mixargs(const Rheo &r, const mevp_params &p, bool has_vo) {
   MixArgs a;
   a.ie = (float)r.ie;
   a.hainv = (float)r.hainv;
@@ -464,6 +542,13 @@ cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_p
   a.opb = (float)(1.0 + p.beta);
   a.fdt = (float)(p.coriolis_f * p.dt);
   a.has_vo = has_vo ? 1 : 0;
+  return a;
+}
+
+cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
+                                  bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
+                                  bool fused) {
+  const MixArgs a = make_mixargs(r, p, has_vo);
   if (ev) cudaEventRecord(ev[0], st);
   if (fused) {
     const dim3 grid((d.nx + FTX - 2) / (FTX - 1), (d.ny + FTY - 2) / (FTY - 1));

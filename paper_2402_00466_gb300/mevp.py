@@ -79,6 +79,14 @@ def load(build_if_stale: bool = True):
             "mevp_set_option": (i, [vp, i, i]),
             "mevp_timing_read": (i, [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]),
+            "mevp_ensemble_create": (i, [ctypes.POINTER(vp), i, pvp]),
+            "mevp_ensemble_destroy": (None, [vp]),
+            "mevp_ensemble_begin_step": (i, [vp]),
+            "mevp_ensemble_run_subcycles": (i, [vp, i]),
+            "mevp_ensemble_shapes": (i, [i, ctypes.POINTER(i), i, ctypes.POINTER(i)]),
+            "mevp_ensemble_set_shape": (i, [vp, i]),
+            "mevp_ensemble_autotune": (i, [vp, i, ctypes.POINTER(i)]),
+            "mevp_ensemble_set_graphs": (i, [vp, i]),
             "mevp_last_error": (ctypes.c_char_p, []),
             "mevp_version": (ctypes.c_char_p, []),
         }
@@ -341,3 +349,78 @@ class State:
 
     def force(self):
         return np.stack([self.read("FORCE_X"), self.read("FORCE_Y")])
+
+
+def mevp_ensemble_create(states):
+    """An ensemble over mevp State objects or raw state handles."""
+    handles = [st.state if isinstance(st, State) else st for st in states]
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if hasattr(h, "value") else h
+                                             for h in handles])
+    out = ctypes.c_void_p()
+    _check(load().mevp_ensemble_create(arr, len(handles), ctypes.byref(out)))
+    return out
+
+
+def mevp_ensemble_destroy(ens):
+    load().mevp_ensemble_destroy(ens)
+
+
+def mevp_ensemble_begin_step(ens):
+    _check(load().mevp_ensemble_begin_step(ens))
+
+
+def mevp_ensemble_run_subcycles(ens, n):
+    _check(load().mevp_ensemble_run_subcycles(ens, int(n)))
+
+
+def mevp_ensemble_shapes(precision):
+    prec = {"fp64": MEVP_FP64, "mixed": MEVP_MIXED}.get(precision, precision)
+    dims = (ctypes.c_int * 32)()
+    cnt = ctypes.c_int()
+    _check(load().mevp_ensemble_shapes(prec, dims, 16, ctypes.byref(cnt)))
+    return [(dims[2 * i], dims[2 * i + 1]) for i in range(cnt.value)]
+
+
+def mevp_ensemble_set_shape(ens, shape):
+    _check(load().mevp_ensemble_set_shape(ens, int(shape)))
+
+
+def mevp_ensemble_autotune(ens, trial_subcycles=20):
+    best = ctypes.c_int()
+    _check(load().mevp_ensemble_autotune(ens, int(trial_subcycles), ctypes.byref(best)))
+    return best.value
+
+
+def mevp_ensemble_set_graphs(ens, on):
+    _check(load().mevp_ensemble_set_graphs(ens, int(bool(on))))
+
+
+class Ensemble:
+    """Several State objects advanced together (see include/mevp.h)."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        self.handle = mevp_ensemble_create(self.states)
+
+    def begin_step(self): mevp_ensemble_begin_step(self.handle)
+    def run_subcycles(self, n): mevp_ensemble_run_subcycles(self.handle, n)
+    def set_shape(self, shape): mevp_ensemble_set_shape(self.handle, shape)
+    def set_graphs(self, on): mevp_ensemble_set_graphs(self.handle, on)
+    def autotune(self, trial_subcycles=20): return mevp_ensemble_autotune(self.handle, trial_subcycles)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            mevp_ensemble_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -42,6 +42,14 @@ CONFIGS = {
                         wind_seed=14),
 }
 
+# Ensemble of independent square domains on the 512 km square: sides drawn
+# log-uniformly in [64, 512] elements, DG1 or DG2 stress at random, Gaussian-
+# random ice and a cyclone of its own per member, 200 subcycles per step.
+ENSEMBLES = {
+    "ensemble64": dict(n_members=64, side_lo=64, side_hi=512, n_sub=200, seed=6),
+    "ensemble8": dict(n_members=8, side_lo=16, side_hi=64, n_sub=20, seed=9),
+}
+
 
 def sizes(nx: int, ny: int):
     """(elements, CG2 nodes, vertices)."""
@@ -178,3 +186,24 @@ def small_case(nx: int, ny: int, n_s: int, seed: int, L: float = DOMAIN_M, movin
     return dict(name=f"small{nx}x{ny}_dg{n_s}", nx=nx, ny=ny, n_s=n_s, n_a=1, n_sub=10, L=L,
                 xy=uniform_vertices(nx, ny, L, L), H=H, A=A, tau=tau, vel0=vel0, S0=S0,
                 params=dict(DEFAULT_PARAMS if params is None else params))
+
+
+def make_ensemble(name: str, L: float = DOMAIN_M, params: dict | None = None):
+    """List of member cases (dicts as make_case returns) of a named ensemble."""
+    cfg = ENSEMBLES[name]
+    rng = np.random.Generator(np.random.PCG64(cfg["seed"]))
+    lo, hi = math.log(cfg["side_lo"]), math.log(cfg["side_hi"])
+    members = []
+    for m in range(cfg["n_members"]):
+        side = int(round(math.exp(rng.uniform(lo, hi))))
+        n_s = 6 if rng.random() < 0.5 else 3
+        s1, s2, sw = (int(x) for x in rng.integers(1, 2 ** 31 - 1, 3))
+        ne, nn, _ = sizes(side, side)
+        H, A = ice_grf(side, side, (s1, s2), L)
+        tau = cyclone_wind_stress(node_coords_uniform(side, side, L, L), cyclone_params(sw, L))
+        members.append(dict(name=f"{name}[{m}]", nx=side, ny=side, n_s=n_s, n_a=1,
+                            n_sub=cfg["n_sub"], L=L, xy=uniform_vertices(side, side, L, L),
+                            H=H, A=A, tau=tau, vel0=np.zeros((2, nn)),
+                            S0=np.zeros((3, n_s, ne)),
+                            params=dict(DEFAULT_PARAMS if params is None else params)))
+    return members

@@ -1,0 +1,121 @@
+"""Ensembles of uneven domains advanced together (one persistent launch per
+subcycle in the mixed precision, element + node launches in FP64): bitwise the
+results of stepping each member alone, for every work decomposition, with and
+without CUDA graph replay; the autotuner leaves no trace in the results."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2402_00466_gb300 import mevp  # noqa: E402
+from paper_2402_00466_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MEMBERS = [(40, 33, 6, 1), (17, 9, 3, 2), (64, 20, 6, 3), (5, 70, 3, 4), (1, 1, 6, 5)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mevp.load()
+
+
+def make_members(precision):
+    states, cases = [], []
+    for nx, ny, ns, seed in MEMBERS:
+        case = W.small_case(nx, ny, ns, seed=500 + seed)
+        p = dict(case["params"], alpha=300.0 + 50 * seed, coriolis_f=1.46e-4 * (1 - 0.3 * seed))
+        st = mevp.State(nx, ny, ns, vertex_xy=case["xy"], precision=precision, params=p)
+        st.set_ice(case["H"], case["A"])
+        st.set_forcing(case["tau"], case["vel0"] * 0.1 if seed == 3 else None)
+        st.set_velocity(case["vel0"])
+        st.set_stress(case["S0"])
+        states.append(st)
+        cases.append(case)
+    return states, cases
+
+
+def results(states):
+    return [(st.velocity(), st.stress()) for st in states]
+
+
+def step_alone(precision, counts):
+    states, _ = make_members(precision)
+    for st in states:
+        st.begin_step()
+        for n in counts:
+            st.run_subcycles(n)
+    out = results(states)
+    for st in states:
+        st.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_ensemble_bitwise_equals_members_alone(precision):
+    counts = (3, 70, 1)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ref = step_alone(precision, counts)
+        shapes = mevp.mevp_ensemble_shapes(precision)
+        assert len(shapes) >= 2
+        for shape in range(len(shapes)):
+            for graphs in (1, 0):
+                states, _ = make_members(precision)
+                with mevp.Ensemble(states) as ens:
+                    ens.set_shape(shape)
+                    ens.set_graphs(graphs)
+                    ens.begin_step()
+                    for n in counts:
+                        ens.run_subcycles(n)
+                    got = results(states)
+                for st in states:
+                    st.close()
+                for m, ((va, Sa), (vb, Sb)) in enumerate(zip(got, ref)):
+                    assert np.array_equal(va, vb), (shape, graphs, m, "velocity")
+                    assert np.array_equal(Sa, Sb), (shape, graphs, m, "stress")
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_autotune_leaves_no_trace(precision):
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ref = step_alone(precision, (9,))
+        states, _ = make_members(precision)
+        with mevp.Ensemble(states) as ens:
+            ens.begin_step()
+            best = ens.autotune(4)
+            assert 0 <= best < len(mevp.mevp_ensemble_shapes(precision))
+            ens.run_subcycles(9)
+            got = results(states)
+        for st in states:
+            st.close()
+    for (va, Sa), (vb, Sb) in zip(got, ref):
+        assert np.array_equal(va, vb) and np.array_equal(Sa, Sb)
+
+
+def test_members_stay_usable_and_mixing_is_rejected():
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        a, _ = make_members("mixed")
+        b, _ = make_members("fp64")
+        with pytest.raises(mevp.MevpError) as e:
+            mevp.Ensemble([a[0], b[0]])
+        assert e.value.code == -1
+        with pytest.raises(mevp.MevpError):
+            mevp.Ensemble([a[0], a[0]])
+        # a member stepped on its own between ensemble runs stays consistent
+        ref = step_alone("mixed", (5, 3, 4))
+        with mevp.Ensemble(a) as ens:
+            ens.begin_step()
+            ens.run_subcycles(5)
+            for st in a:
+                st.run_subcycles(3)
+            ens.run_subcycles(4)
+            got = results(a)
+        for (va, Sa), (vb, Sb) in zip(got, ref):
+            assert np.array_equal(va, vb) and np.array_equal(Sa, Sb)
+        for st in a + b:
+            st.close()
