@@ -146,6 +146,12 @@ MEVP_API int mevp_set_params(mevp_state *state, const mevp_params *params);
 /* H and A, [n_adv][N_e] FP64 each.  Takes effect at the next mevp_begin_step. */
 MEVP_API int mevp_set_ice(mevp_state *state, const double *H, const double *A, int on_device);
 
+/* Per-element ice strength parameter P* [N_e] (N/m^2, replacing
+ * params.Pstar element by element; NULL returns to params.Pstar).  Enters the
+ * ice strength P = P* max(0,H) exp(-C (1 - clamp(A,0,1))) of Listing 1 at
+ * the next mevp_begin_step. */
+MEVP_API int mevp_set_strength_field(mevp_state *state, const double *Pstar, int on_device);
+
 /* Nodal wind stress tau [2][N_n] (N/m^2) and ocean velocity [2][N_n] (m/s)
  * or NULL for an ocean at rest.  Takes effect at the next mevp_begin_step. */
 MEVP_API int mevp_set_forcing(mevp_state *state, const double *tau, const double *v_ocean,
@@ -280,6 +286,25 @@ MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp
                                         const double *H, const double *A, const double *tau,
                                         const double *v_ocean, double *vel, double *S, int n,
                                         void *cuda_stream);
+
+/* Gradient of the kinetic energy J = 1/2 sum_j m_j |v_j|^2 (m_j the lumped
+ * nodal mass) after n >= 1 subcycles from the current state, with respect to
+ * the per-element P* field (mevp_set_strength_field; params.Pstar where none
+ * is set) and the nodal wind stress tau, for an FP64 state after
+ * mevp_begin_step.  A hand-written reverse mode of the subcycle (Table 1's
+ * four stages: strain, the stress update of Listing 1, divergence, velocity):
+ * the forward sweep keeps checkpoints (v, S) every checkpoint_every
+ * subcycles, and each segment's velocities are recomputed before it is
+ * reversed.  The drag's kink |v_o - v| = 0 takes derivative 0.  Outputs (any
+ * may be NULL): *J; dJ_dPstar [N_e]; dJ_dtau [2][N_n]; host memory with
+ * on_device = 0 (the call then waits), device memory with on_device = 1.
+ * Afterwards the state holds the result of the n subcycles, as after
+ * mevp_run_subcycles(n).  Allocates its working memory (cudaMalloc):
+ * about (n/checkpoint_every) (2 N_n + 3 n_stress N_e) + (checkpoint_every
+ * + 8) 2 N_n + 40 N_e doubles.  MEVP_ERR_UNSUPPORTED for MEVP_MIXED. */
+MEVP_API int mevp_adjoint_kinetic_energy(mevp_state *state, int n, int checkpoint_every,
+                                         double *J, double *dJ_dPstar, double *dJ_dtau,
+                                         int on_device);
 
 /* Per-kernel timing with CUDA events, for benchmarks.  With on = k > 0 the
  * launches of every k-th subcycle of mevp_run_subcycles are bracketed by

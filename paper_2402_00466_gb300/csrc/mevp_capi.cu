@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, lines, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, lines, pstar, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -77,6 +77,7 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.xline = take(sizeof(double) * (m->nx + 1));
   L.yline = take(sizeof(double) * (m->ny + 1));
   L.lines = take(sizeof(double) * 2 * (m->nx + m->ny));
+  L.pstar = take(sizeof(double) * ne);
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(sizeof(double) * 3 * ns * ne);
@@ -308,6 +309,8 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.xline = (const double *)(b + L.xline);
   d.yline = (const double *)(b + L.yline);
   d.lines = (double *)(b + L.lines);
+  s->pstar_buf = (double *)(b + L.pstar);
+  d.pstar = nullptr;
   d.vel[0] = (double *)(b + L.vel0);
   d.vel[1] = (double *)(b + L.vel1);
   d.S = (double *)(b + L.S);
@@ -411,6 +414,23 @@ int mevp_set_forcing(mevp_state *s, const double *tau, const double *v_ocean, in
     if (s->has_vo) drop_graphs(s);
     s->has_vo = false;
   }
+  return MEVP_OK;
+}
+
+int mevp_set_strength_field(mevp_state *s, const double *Pstar, int on_device) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (!Pstar) {
+    s->d.pstar = nullptr;
+    s->has_pstar = false;
+    drop_graphs(s);
+    return MEVP_OK;
+  }
+  if ((rc = copy_in(s, s->pstar_buf, Pstar, (size_t)s->d.ne, on_device, "set_strength_field")))
+    return rc;
+  s->d.pstar = s->pstar_buf;
+  s->has_pstar = true;
+  drop_graphs(s);
   return MEVP_OK;
 }
 

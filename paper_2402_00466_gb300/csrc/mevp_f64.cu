@@ -267,7 +267,7 @@ __global__ void k_strength(DevState d, double Pstar, double C) {
   if (K >= d.ne) return;
   const double h = fmax(0.0, d.H[K]);
   const double a = fmin(1.0, fmax(0.0, d.A[K]));
-  d.Pe[K] = Pstar * h * exp(-C * (1.0 - a));
+  d.Pe[K] = (d.pstar ? d.pstar[K] : Pstar) * h * exp(-C * (1.0 - a));
 }
 
 // Lumped mass m_j = rho_ice sum_K max(0,H_K) hx hy w_a w_b and area

@@ -62,6 +62,7 @@ struct DevState {
   double *tau;         // [2][nn]
   double *vo;          // [2][nn]
   double *Pe;          // [ne] ice strength per element
+  const double *pstar; // [ne] per-element P* field, or NULL (params.Pstar everywhere)
   double *nodec;       // [6][nn] cA, cB, cK, qx, qy, cD
   double *mass;        // [nn]
   double *fbuf;        // FP64: [18][ne] per-element nodal forces (scratch)
@@ -158,6 +159,8 @@ struct mevp_state {
   bool have_params = false;
   bool prepared = false;
   bool has_vo = false;
+  bool has_pstar = false;  // per-element P* field set (mevp_set_strength_field)
+  double *pstar_buf = nullptr;
   bool fused = true;  // mixed precision: one fused launch per subcycle
   bool use_graphs = true;  // replay captured subcycle chunks (non-default streams)
   struct Graph {

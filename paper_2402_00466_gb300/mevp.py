@@ -79,6 +79,8 @@ def load(build_if_stale: bool = True):
             "mevp_set_option": (i, [vp, i, i]),
             "mevp_timing_read": (i, [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]),
+            "mevp_set_strength_field": (i, [vp, vp, i]),
+            "mevp_adjoint_kinetic_energy": (i, [vp, i, i, vp, vp, vp, i]),
             "mevp_ensemble_create": (i, [ctypes.POINTER(vp), i, pvp]),
             "mevp_ensemble_destroy": (None, [vp]),
             "mevp_ensemble_begin_step": (i, [vp]),
@@ -186,6 +188,19 @@ def mevp_set_velocity(state, uv):
 def mevp_set_stress(state, S):
     p, dev, k = _ptr(S)
     _check(load().mevp_set_stress(state, p, dev))
+
+
+def mevp_set_strength_field(state, Pstar):
+    """Per-element P* field [N_e] (numpy or torch float64), or None for params.Pstar."""
+    p, dev, k = _ptr(Pstar)
+    _check(load().mevp_set_strength_field(state, p, dev))
+
+
+def mevp_adjoint_kinetic_energy(state, n, checkpoint_every, J, dJ_dPstar, dJ_dtau, on_device):
+    """Thin call: pointers (or None) for J, dJ/dP* [N_e], dJ/dtau [2][N_n]."""
+    vp = lambda x: None if x is None else ctypes.c_void_p(x)  # noqa: E731
+    _check(load().mevp_adjoint_kinetic_energy(state, int(n), int(checkpoint_every), vp(J),
+                                              vp(dJ_dPstar), vp(dJ_dtau), int(on_device)))
 
 
 def mevp_begin_step(state):
@@ -317,6 +332,27 @@ class State:
     def begin_step(self): mevp_begin_step(self.state)
     def run_subcycles(self, n): mevp_run_subcycles(self.state, n)
     def sync(self): mevp_sync(self.state)
+    def set_strength_field(self, Pstar): mevp_set_strength_field(self.state, Pstar)
+
+    def adjoint_kinetic_energy(self, n, checkpoint_every=10, device=False):
+        """(J, dJ/dP*, dJ/dtau) of the kinetic energy after n subcycles from the
+        current state (FP64 states, after begin_step); numpy, or CUDA tensors
+        with device=True."""
+        if device:
+            import torch
+            J = torch.empty((), dtype=torch.float64, device="cuda")
+            gP = torch.empty(self.ne, dtype=torch.float64, device="cuda")
+            gT = torch.empty((2, self.nn), dtype=torch.float64, device="cuda")
+            mevp_adjoint_kinetic_energy(self.state, n, checkpoint_every, J.data_ptr(),
+                                        gP.data_ptr(), gT.data_ptr(), 1)
+            return J, gP, gT
+        J = np.zeros(1)
+        gP = np.zeros(self.ne)
+        gT = np.zeros((2, self.nn))
+        mevp_adjoint_kinetic_energy(self.state, n, checkpoint_every, J.ctypes.data,
+                                    gP.ctypes.data, gT.ctypes.data, 0)
+        return float(J[0]), gP, gT
+
     def timing_enable(self, stride=1): mevp_timing_enable(self.state, stride)
     def set_option(self, option, value): mevp_set_option(self.state, option, value)
     def timing_read(self): return mevp_timing_read(self.state)
@@ -424,3 +460,30 @@ class Ensemble:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def kinetic_energy(state, pstar, tau, n, checkpoint_every=10):
+    """Differentiable J(P*, tau): the kinetic energy 1/2 sum_j m_j |v_j|^2 after
+    n subcycles of an FP64 State from its current velocity and stress, as a
+    function of the per-element P* field `pstar` [N_e] and the nodal wind
+    stress `tau` [2, N_n] (CUDA float64 tensors).  backward() returns the
+    gradients of the library's hand-written adjoint.  The call leaves the
+    state after the n subcycles, like State.run_subcycles."""
+    import torch
+
+    class _KineticEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, p, t):
+            state.set_strength_field(p.detach().contiguous())
+            state.set_forcing(t.detach().contiguous())
+            state.begin_step()
+            J, gP, gT = state.adjoint_kinetic_energy(n, checkpoint_every, device=True)
+            ctx.save_for_backward(gP, gT)
+            return J
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gP, gT = ctx.saved_tensors
+            return gJ * gP, gJ * gT
+
+    return _KineticEnergy.apply(pstar, tau)
