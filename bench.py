@@ -113,6 +113,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Max of a per-rank float over all ranks (timings: the slowest rank
+    defines the whole job's time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -427,10 +441,8 @@ def _run_ours(a, torch, dist, ws, rank):
     st = m["state"]
     total_ms = m["total_ms"]
     if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * ne * n_sub * a.steps / (total_ms / 1e3)
+        total_ms = reduce_max(total_ms, dist, "cuda")
+    value = whole_job_throughput(ne * n_sub * a.steps, ws, total_ms / 1e3)
     roofline = roofline_for(a.precision, case, m["kt"], m["total_ms"], a.steps)
 
     # end to end through the public API with pinned host buffers
@@ -458,9 +470,7 @@ def _run_ours(a, torch, dist, ws, rank):
         barrier()
         dt = time.perf_counter() - t0
         if ws > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+            dt = reduce_max(dt, dist, "cuda")
         h2d = 8 * (2 * ne + 2 * nn + 2 * nn + 3 * ns * ne)
         d2h = 8 * (2 * nn + 3 * ns * ne)
         e2e = {"value": ws * ne * n_sub * e2e_steps / dt, "unit": UNIT,

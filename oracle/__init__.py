@@ -61,7 +61,10 @@ def build(openmp: bool = False, force: bool = False) -> str:
 def _lib(openmp: bool = False):
     with _lock:
         if openmp not in _handles:
-            lib = ctypes.CDLL(build(openmp))
+            # MEVP_ORACLE_LIB: load another build of this source (the mutation
+            # tests plant a mistake in a copy and check that the pins fail)
+            override = os.environ.get("MEVP_ORACLE_LIB")
+            lib = ctypes.CDLL(override if override else build(openmp))
             dp = ctypes.POINTER(ctypes.c_double)
             pp = ctypes.POINTER(Params)
             i = ctypes.c_int

@@ -1,0 +1,62 @@
+"""Mutation tests of the oracle's pins: each plausible mistake below is
+planted in a copy of the oracle's C source (on the CPU), compiled, and the pin
+suite (test_oracle_pins.py) must fail against it.  A surviving mutant would
+mean a part of the oracle no pin fixes."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, original text, mutated text): one plausible mistake each
+MUTANTS = [
+    ("shear strain without 1/2", "e12[g] = 0.5 * (uy + vx);", "e12[g] = (uy + vx);"),
+    ("divergence sign", "loc[(size_t)K * 18 + j] = -fx;", "loc[(size_t)K * 18 + j] = fx;"),
+    ("Jacobian transposed", "E->dx[g][j] = (J11 * M->q2x[g][j] - J10 * M->q2e[g][j]) / det;",
+     "E->dx[g][j] = (J11 * M->q2x[g][j] - J01 * M->q2e[g][j]) / det;"),
+    ("Gauss weights halved", "ws[i] = 2.0 / ((1.0 - x * x) * dpn * dpn);",
+     "ws[i] = 1.0 / ((1.0 - x * x) * dpn * dpn);"),
+    ("Delta cross term", "k_mix * e11 * e22", "k_mix * e11 * e11"),
+    ("s22 uses e22 twice", "s22[g] = alphaInv * (PD * (c_a * e22 + c_b * e11) - 0.5 * P);",
+     "s22[g] = alphaInv * (PD * (c_a * e22 + c_b * e22) - 0.5 * P);"),
+    ("no relaxation of S11", "*q11 = fac * *q11 + a;", "*q11 = *q11 + a;"),
+    ("ice strength exponent", "exp(-p->C * (1.0 - a))", "exp(-p->C * a)"),
+    ("h not clamped", "double h = fmax(0.0, hg);\n      double a = fmin", "double h = hg;\n      double a = fmin"),
+    ("Coriolis sign", "vout[j] = (a * rx + b * ry) / det;", "vout[j] = (a * rx - b * ry) / det;"),
+    ("drag without rho_w", "double c = l[j] * p->Cw * p->rho_water *", "double c = l[j] * p->Cw *"),
+    ("mass without rho_ice", "m[G.node[j]] += p->rho_ice * G.wdet[g] * h * M->q2[g][j];",
+     "m[G.node[j]] += G.wdet[g] * h * M->q2[g][j];"),
+    ("local node index transposed", "E->node[a + 3 * b] = (2 * ky + b) * nw + 2 * kx + a;",
+     "E->node[a + 3 * b] = (2 * ky + a) * nw + 2 * kx + b;"),
+    ("no beta relaxation", "mdt * (p->beta * vprev[j] + vn[j])", "mdt * (vprev[j] + vn[j])"),
+    ("DG basis constant", "all[3] = xh * xh - 1.0 / 12.0;", "all[3] = xh * xh - 1.0 / 6.0;"),
+    ("Q2 node moved", "q2_nodes[3] = {0.0, 0.5, 1.0};", "q2_nodes[3] = {0.0, 0.4, 1.0};"),
+    ("inverse mass skipped", "acc += mass[s * n_s + t] * E->wdet[g] * M->psi_s[t][g];",
+     "acc += (s == t) * E->wdet[g] * M->psi_s[t][g];"),
+    ("north boundary not Dirichlet", "ix == nw - 1 || iy == nh - 1)", "ix == nw - 1)"),
+    ("velocity uses v^n for drag", "double dvx = ox - vprev[j], dvy = oy - vprev[nn + j];",
+     "double dvx = ox - vn[j], dvy = oy - vn[nn + j];"),
+    ("stress 12 coefficient", "s12[g] = alphaInv * (PD * c_s * e12);",
+     "s12[g] = alphaInv * (PD * c_a * e12);"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught_by_the_pins(name, old, new, tmp_path):
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique/found: {name}"
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "mutant.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                    "-D_POSIX_C_SOURCE=199309L", "-o", str(so), str(mut), "-lm"], check=True)
+    env = dict(os.environ, MEVP_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests",
+                                                                     "test_oracle_pins.py"),
+                        "-x", "-q", "-p", "no:cacheprovider"], env=env, cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant survived the pins: {name}\n{r.stdout[-2000:]}"
