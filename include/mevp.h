@@ -201,7 +201,11 @@ enum {
    * use and kept until the parameters, the ocean forcing or an option
    * change); 0 = one launch at a time.  States on the legacy default stream
    * (cuda_stream = NULL) always launch one at a time. */
-  MEVP_OPT_GRAPHS = 2
+  MEVP_OPT_GRAPHS = 2,
+  /* k > 0: after every k subcycles a watchdog kernel scans the velocity for
+   * NaN/Inf and raises a device flag, which the next mevp_sync reports as
+   * MEVP_ERR_NAN (and clears); 0 (default) = off. */
+  MEVP_OPT_NAN_CHECK = 3
 };
 MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
 

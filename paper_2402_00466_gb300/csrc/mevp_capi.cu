@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, lines, pstar, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, lines, pstar, flags, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -78,6 +78,7 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.yline = take(sizeof(double) * (m->ny + 1));
   L.lines = take(sizeof(double) * 2 * (m->nx + m->ny));
   L.pstar = take(sizeof(double) * ne);
+  L.flags = take(sizeof(int) * 4);
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(sizeof(double) * 3 * ns * ne);
@@ -310,6 +311,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.yline = (const double *)(b + L.yline);
   d.lines = (double *)(b + L.lines);
   s->pstar_buf = (double *)(b + L.pstar);
+  d.flags = (int *)(b + L.flags);
   d.pstar = nullptr;
   d.vel[0] = (double *)(b + L.vel0);
   d.vel[1] = (double *)(b + L.vel1);
@@ -475,8 +477,14 @@ int mevp_run_subcycles(mevp_state *s, int n) {
   const bool graphs = s->use_graphs && s->stream != nullptr;
   int i = 0;
   while (i < n) {
+    if (s->nan_every > 0 && s->since_check >= s->nan_every) {
+      cudaError_t e = mevp::launch_nan_check(s->d, s->cur, s->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "run_subcycles watchdog");
+      s->since_check = 0;
+    }
     const bool timed = s->timing && (s->timed_calls % s->timing) == 0;
-    if (timed || !graphs || n - i < kMinGraphChunk) {
+    const int to_check = s->nan_every > 0 ? (int)(s->nan_every - s->since_check) : n;
+    if (timed || !graphs || n - i < kMinGraphChunk || to_check < kMinGraphChunk) {
       cudaEvent_t *ev = nullptr;
       if (timed) {
         while (s->events.size() < s->ev_used + 3) {
@@ -491,12 +499,15 @@ int mevp_run_subcycles(mevp_state *s, int n) {
       if (e != cudaSuccess) return cuda_fail(e, "run_subcycles launch");
       s->cur ^= 1;
       if (s->timing) s->timed_calls++;
+      s->since_check++;
       ++i;
       continue;
     }
-    // untimed run up to the next timed subcycle (or the end), in graph chunks
+    // untimed run up to the next timed subcycle or watchdog scan (or the
+    // end), in graph chunks
     int len = n - i;
     if (len > kMaxGraphChunk) len = kMaxGraphChunk;
+    if (len > to_check) len = to_check;
     if (s->timing) {
       const long long to_next = s->timing - (s->timed_calls % s->timing);
       if (len > to_next) len = (int)to_next;
@@ -506,7 +517,13 @@ int mevp_run_subcycles(mevp_state *s, int n) {
     MEVP_CUDA(cudaGraphLaunch(exec, s->stream), "run_subcycles graph launch");
     s->cur ^= (len & 1);
     if (s->timing) s->timed_calls += len;
+    s->since_check += len;
     i += len;
+  }
+  if (s->nan_every > 0 && s->since_check >= s->nan_every) {
+    cudaError_t e = mevp::launch_nan_check(s->d, s->cur, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "run_subcycles watchdog");
+    s->since_check = 0;
   }
   return MEVP_OK;
 }
@@ -519,6 +536,11 @@ int mevp_set_option(mevp_state *s, int option, int value) {
       if (value != 0 && value != 1) return fail(MEVP_ERR_ARG, "set_option: FUSED takes 0 or 1");
       s->fused = value != 0;
       drop_graphs(s);
+      return MEVP_OK;
+    case MEVP_OPT_NAN_CHECK:
+      if (value < 0) return fail(MEVP_ERR_ARG, "set_option: NAN_CHECK takes k >= 0");
+      s->nan_every = value;
+      s->since_check = 0;
       return MEVP_OK;
     case MEVP_OPT_GRAPHS:
       if (value != 0 && value != 1) return fail(MEVP_ERR_ARG, "set_option: GRAPHS takes 0 or 1");
@@ -612,6 +634,14 @@ int mevp_sync(mevp_state *s) {
   if (rc) return rc;
   MEVP_CUDA(cudaStreamSynchronize(s->stream), "sync");
   MEVP_CUDA(cudaGetLastError(), "sync");
+  if (s->nan_every > 0) {
+    int flag = 0;
+    MEVP_CUDA(cudaMemcpy(&flag, s->d.flags, sizeof(int), cudaMemcpyDeviceToHost), "sync");
+    if (flag) {
+      MEVP_CUDA(cudaMemset(s->d.flags, 0, sizeof(int)), "sync");
+      return fail(MEVP_ERR_NAN, "sync: the watchdog found a non-finite velocity");
+    }
+  }
   return MEVP_OK;
 }
 

@@ -357,9 +357,32 @@ __global__ void k_force_gather(DevState d) {
   d.diag[(size_t)d.nn + node] = Fy;
 }
 
+// Watchdog: any non-finite velocity component raises flags[0] (every writer
+// stores the same value, so no atomics are needed).
+__global__ void k_nan_check(DevState d, int cur) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)d.nn; i += stride) {
+    bool bad;
+    if (d.prec == MEVP_MIXED) {
+      const float4 v = d.vel4[cur][i];
+      bad = !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+    } else {
+      bad = !(isfinite(d.vel[cur][i]) && isfinite(d.vel[cur][(size_t)d.nn + i]));
+    }
+    if (bad) d.flags[0] = 1;
+  }
+}
+
 inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
 }  // namespace
+
+cudaError_t launch_nan_check(const DevState &d, int cur, cudaStream_t st) {
+  int b = blocks(d.nn, 256);
+  if (b > 152 * 8) b = 152 * 8;
+  k_nan_check<<<b, 256, 0, st>>>(d, cur);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                            cudaStream_t st) {

@@ -68,6 +68,7 @@ struct DevState {
   double *fbuf;        // FP64: [18][ne] per-element nodal forces (scratch)
   float *fbuf32;       // mixed: [18][ne]
   double *diag;        // [3][ns][ne] or [2][nn] diagnostic output
+  int *flags;          // [4] device status words: [0] non-finite velocity seen
   // mixed precision only (FP64 buffers above stage inputs and outputs)
   float4 *vel4[2];     // [nn] (u_hi, u_lo, v_hi, v_lo) records, ping-pong
   float *Pe32;         // [ne]
@@ -135,6 +136,8 @@ cudaError_t launch_vel_join(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_stress_to_f32(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_stress_to_f64(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_diag(const DevState &d, cudaStream_t st);
+// sets flags[0] when the current velocity holds a non-finite value
+cudaError_t launch_nan_check(const DevState &d, int cur, cudaStream_t st);
 
 // Error reporting shared by the C-ABI translation units (sets the thread-local
 // message returned by mevp_last_error and returns the code).
@@ -162,6 +165,8 @@ struct mevp_state {
   bool has_pstar = false;  // per-element P* field set (mevp_set_strength_field)
   double *pstar_buf = nullptr;
   bool fused = true;  // mixed precision: one fused launch per subcycle
+  int nan_every = 0;         // watchdog interval in subcycles (0 = off)
+  long long since_check = 0; // subcycles since the last watchdog scan
   bool use_graphs = true;  // replay captured subcycle chunks (non-default streams)
   struct Graph {
     int parity, len;

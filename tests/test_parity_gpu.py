@@ -312,3 +312,33 @@ def test_graph_replay_equals_direct_launches(precision, timing):
     if precision == "fp64":
         assert_close(out[0][0], vo, "velocity")
         assert_close(out[0][1], So, "stress")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nan_watchdog_reports_device_side_corruption(precision):
+    """A NaN entering through a device-resident input (device inputs are not
+    checked on the host) is found by the watchdog and reported by sync; with
+    the watchdog off the same run syncs without error."""
+    case = W.small_case(11, 9, 6, seed=61)
+    bad = torch.from_numpy(case["S0"].copy()).cuda()
+    bad[0, 0, 17] = float("nan")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for every, expect in ((5, -5), (0, 0)):
+            with make_state(case, precision=precision) as st:
+                st.set_option(mevp.MEVP_OPT_NAN_CHECK, every)
+                st.set_stress(bad)
+                st.begin_step()
+                st.run_subcycles(23)
+                if expect:
+                    with pytest.raises(mevp.MevpError) as e:
+                        st.sync()
+                    assert e.value.code == expect
+                    st.sync()  # the flag was cleared
+                else:
+                    st.sync()
+        with make_state(case, precision=precision) as st:  # clean input: no report
+            st.set_option(mevp.MEVP_OPT_NAN_CHECK, 1)
+            st.begin_step()
+            st.run_subcycles(40)
+            st.sync()
