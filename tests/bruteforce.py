@@ -17,8 +17,8 @@ import numpy as np
 from numpy.polynomial import legendre as Lg
 from numpy.polynomial import polynomial as Pl
 
-DEG = {3: 1, 6: 2}
-NGP = {3: 2, 6: 3}
+DEG = {3: 1, 6: 2, 8: 2}
+NGP = {3: 2, 6: 3, 8: 3}
 
 
 def gauss01(n):
@@ -52,22 +52,28 @@ def q2(xi, eta):
 
 
 def dg_bf(n_s, xi, eta):
-    """Brute-force DG basis: shifted Legendre products of total degree <= k."""
-    k = {1: 0, 3: 1, 6: 2}[n_s]
+    """Brute-force DG basis: shifted Legendre products of total degree <= k;
+    the 8-dof space is Q2 without the biquadratic product (degree <= 2 in
+    each variable, total degree <= 3)."""
+    if n_s == 8:
+        pairs = [(i, j) for i in range(3) for j in range(3) if i + j <= 3]
+    else:
+        k = {1: 0, 3: 1, 6: 2}[n_s]
+        pairs = [(i, j) for i in range(k + 1) for j in range(k + 1 - i)]
     cols = []
-    for i in range(k + 1):
-        for j in range(k + 1 - i):
-            ei = np.zeros(i + 1); ei[i] = 1.0
-            ej = np.zeros(j + 1); ej[j] = 1.0
-            cols.append(Lg.legval(2 * xi - 1, ei) * Lg.legval(2 * eta - 1, ej))
+    for i, j in pairs:
+        ei = np.zeros(i + 1); ei[i] = 1.0
+        ej = np.zeros(j + 1); ej[j] = 1.0
+        cols.append(Lg.legval(2 * xi - 1, ei) * Lg.legval(2 * eta - 1, ej))
     return np.stack(cols, -1)
 
 
 def dg_documented(n_s, xi, eta):
     """The library's documented coefficient convention (xh = xi-1/2, eh = eta-1/2):
-    {1, xh, eh, xh^2-1/12, xh eh, eh^2-1/12}[:n_s]."""
+    {1, xh, eh, xh^2-1/12, xh eh, eh^2-1/12, (xh^2-1/12) eh, xh (eh^2-1/12)}[:n_s]."""
     xh, eh = xi - 0.5, eta - 0.5
-    allb = [np.ones_like(xh), xh, eh, xh * xh - 1 / 12, xh * eh, eh * eh - 1 / 12]
+    allb = [np.ones_like(xh), xh, eh, xh * xh - 1 / 12, xh * eh, eh * eh - 1 / 12,
+            (xh * xh - 1 / 12) * eh, xh * (eh * eh - 1 / 12)]
     return np.stack(allb[:n_s], -1)
 
 

@@ -80,7 +80,7 @@ def test_dg_basis_orthogonal_closed_form_mass():
     assert np.allclose(M, expect, atol=1e-15)
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 def test_dg_basis_spans_total_degree(n_s):
     rng = np.random.default_rng(0)
     pts = rng.uniform(0, 1, (30, 2))
@@ -111,7 +111,7 @@ def test_q2_lagrange_partition_and_gradients():
         assert abs(de @ pv - (2 * xi ** 2 * eta + 3 * xi)) < 1e-13
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 @pytest.mark.parametrize("affine", [True, False])
 def test_projection_matrix_is_left_inverse(n_s, affine):
     """iMJwPSI applied to the Gauss values of a DG function returns its coefficients."""
@@ -147,7 +147,7 @@ def _node_xy(nx, ny, xy):
     return out
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 @pytest.mark.parametrize("affine", [True, False])
 def test_strain_linear_field_exact(n_s, affine):
     nx, ny, L = 4, 3, 8e3
@@ -183,7 +183,7 @@ def _one_element_stress(n_s, E0, H, A, S0, params):
     return oracle.stress(1, 1, xy, n_s, 1, params, E, np.array([[H]]), np.array([[A]]), S)
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 def test_stress_single_point_matches_printed_constants(n_s):
     d, s, st = GOLD["delta"], GOLD["stress"], GOLD["strength"]
     p = dict(P0, Pstar=st["Pstar"], C=st["C"], e=2.0)
@@ -233,7 +233,7 @@ def test_stress_clamps():
     assert np.array_equal(lo, zero)
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 def test_stress_relaxation_closed_form(n_s):
     """E = 0, uniform H, A: S11_0^p = S22_0^p = -(P/2)(1 - (1-1/alpha)^p), S12 = 0."""
     p = dict(P0)
@@ -252,7 +252,7 @@ def test_stress_relaxation_closed_form(n_s):
 # --------------------------------------------------------------------------
 # Divergence (stage 3)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 def test_divergence_constant_stress(n_s):
     """Constant sigma: interior nodes feel nothing; boundary nodes feel -sigma.n
     times the 1-D Q2 edge weights (h/6, 4h/6, h/6); the total is zero."""
@@ -281,7 +281,7 @@ def test_divergence_constant_stress(n_s):
     assert np.allclose(F.sum(axis=1), 0, atol=1e-9 * scale)
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 @pytest.mark.parametrize("affine", [True, False])
 def test_divergence_matches_bruteforce(n_s, affine):
     nx, ny, L = 3, 2, 6e3
@@ -384,7 +384,7 @@ def test_converged_subcycle_is_implicit_euler():
     assert abs(centre[0] - v.real) < 1e-12 and abs(centre[1] - v.imag) < 1e-12
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 @pytest.mark.parametrize("affine", [True, False])
 def test_whole_subcycle_matches_bruteforce(n_s, affine):
     nx, ny = 2, 2
