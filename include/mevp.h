@@ -7,8 +7,9 @@
  * GPU.  One subcycle is the four stages of the paper's Table 1 -- strain,
  * stress, divergence, velocity -- fused into two kernel launches.  The
  * discretisation is the one of Sec. 2.1: CG2 (Q2) velocity on a structured
- * quadrilateral mesh, tensor-valued DG stress (DG1 = 3 or DG2 = 6 dofs per
- * component), DG0 ice height H and concentration A.  The stress update per
+ * quadrilateral mesh, tensor-valued DG stress (DG1 = 3, DG2 = 6 or the 8-dof
+ * space of App. A per component), DG0 ice height H and concentration A.  The
+ * stress update per
  * element is the one printed in Listing 1 / App. A (generalised to any
  * ellipse ratio e), with the inverse element map computed on the fly from the
  * mesh vertices (Sec. 3.2, "on-the-fly map").
@@ -40,7 +41,8 @@
  *   vertex coordinates: [N_v][2] (x, y) pairs
  * DG coefficients refer to the orthogonal basis on the reference square,
  * with xh = xi - 1/2, eh = eta - 1/2:
- *   {1, xh, eh, xh^2 - 1/12, xh*eh, eh^2 - 1/12}   (first 3 for DG1)
+ *   {1, xh, eh, xh^2 - 1/12, xh*eh, eh^2 - 1/12, (xh^2 - 1/12)*eh,
+ *    xh*(eh^2 - 1/12)}   (first 3 for DG1, first 6 for DG2)
  * Values at points, forces and velocities do not depend on this choice.
  */
 #ifndef MEVP_GB300_C_ABI_H
@@ -110,11 +112,16 @@ enum mevp_field {
 };
 
 /* Create a structured nx x ny quadrilateral mesh (Sec. 2.1).  vertex_xy is
- * [N_v][2] host memory, or NULL for a uniform mesh of [0,Lx] x [0,Ly]
- * (Lx, Ly ignored when vertex_xy is given).  This build handles rectilinear
- * meshes (vertex x depends only on jx, y only on jy, strictly increasing);
- * other vertex sets return MEVP_ERR_UNSUPPORTED.  No device memory is
- * allocated.  nx, ny >= 1 and (2nx+1)(2ny+1) < 2^31. */
+ * [N_v][2] host memory (copied), or NULL for a uniform mesh of [0,Lx] x [0,Ly]
+ * (Lx, Ly ignored when vertex_xy is given).  A rectilinear vertex set
+ * (x depends only on jx, y only on jy) must be strictly increasing in both
+ * directions and runs on the rectilinear kernels.  Any other vertex set is a
+ * general mesh: each element is the bilinear (Q1) image of the reference
+ * square, evaluated on the fly per Gauss point (Sec. 3.2), and must be a
+ * convex quadrilateral with counter-clockwise vertices (Jacobian determinant
+ * positive at its four corners, hence everywhere), else MEVP_ERR_ARG.
+ * General meshes run in FP64 only.  No device memory is allocated.
+ * nx, ny >= 1 and (2nx+1)(2ny+1) < 2^31. */
 MEVP_API int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_xy,
                      mevp_mesh **out);
 MEVP_API void mevp_mesh_destroy(mevp_mesh *mesh);
@@ -123,9 +130,10 @@ MEVP_API void mevp_mesh_destroy(mevp_mesh *mesh);
 MEVP_API int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
                                size_t *bytes);
 
-/* Create a state for n_stress in {3, 6} (DG1/DG2 stress; Gauss rule 2x2 or
- * 3x3 as in App. A), n_adv = 1 (DG0 H, A) and precision MEVP_FP64 or
- * MEVP_MIXED, bound to the current CUDA device and to cuda_stream (a
+/* Create a state for n_stress in {3, 6, 8} (DG1, DG2 and the 8-dof stress of
+ * App. A; Gauss rule 2x2, 3x3, 3x3), n_adv = 1 (DG0 H, A) and precision
+ * MEVP_FP64 or MEVP_MIXED (rectilinear meshes; general meshes take
+ * MEVP_FP64, else MEVP_ERR_UNSUPPORTED), bound to the current CUDA device and to cuda_stream (a
  * cudaStream_t; NULL = legacy default stream).  MEVP_MIXED computes strain,
  * viscosities, stress and element forces in FP32 (the FP32 stress update of
  * Sec. 4, extended to every element stage), keeps the velocity state as
@@ -218,7 +226,8 @@ MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
  * (member, tile) work list of all members; MEVP_FP64 issues a persistent
  * element launch and a persistent node launch.  Results are bitwise those of
  * stepping each member alone.  The ensemble allocates small device tables
- * (cudaMalloc) for its member descriptors and work lists. */
+ * (cudaMalloc) for its member descriptors and work lists.  Members must have
+ * rectilinear meshes and 3 or 6 stress dofs (else MEVP_ERR_UNSUPPORTED). */
 typedef struct mevp_ensemble mevp_ensemble; /* opaque, library-owned */
 
 MEVP_API int mevp_ensemble_create(mevp_state *const *members, int n, mevp_ensemble **out);
@@ -305,7 +314,8 @@ MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp
  * Afterwards the state holds the result of the n subcycles, as after
  * mevp_run_subcycles(n).  Allocates its working memory (cudaMalloc):
  * about (n/checkpoint_every) (2 N_n + 3 n_stress N_e) + (checkpoint_every
- * + 8) 2 N_n + 40 N_e doubles.  MEVP_ERR_UNSUPPORTED for MEVP_MIXED. */
+ * + 8) 2 N_n + 40 N_e doubles.  MEVP_ERR_UNSUPPORTED for MEVP_MIXED, for 8
+ * stress dofs and for general meshes. */
 MEVP_API int mevp_adjoint_kinetic_energy(mevp_state *state, int n, int checkpoint_every,
                                          double *J, double *dJ_dPstar, double *dJ_dtau,
                                          int on_device);

@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, lines, pstar, flags, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, xy, lines, pstar, flags, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -76,6 +76,7 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   };
   L.xline = take(sizeof(double) * (m->nx + 1));
   L.yline = take(sizeof(double) * (m->ny + 1));
+  L.xy = take(m->general ? m->xy.size() * sizeof(double) : 0);
   L.lines = take(sizeof(double) * 2 * (m->nx + m->ny));
   L.pstar = take(sizeof(double) * ne);
   L.flags = take(sizeof(int) * 4);
@@ -221,14 +222,34 @@ int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_
           delete m;
           return fail(MEVP_ERR_ARG, "mesh_create: non-finite vertex %d", j * vw + i);
         }
-        if (x != m->xline[i] || y != m->yline[j]) {
-          delete m;
-          return fail(MEVP_ERR_UNSUPPORTED,
-                      "mesh_create: vertex (%d,%d) breaks the rectilinear layout; this build "
-                      "handles rectilinear meshes only",
-                      i, j);
-        }
+        if (x != m->xline[i] || y != m->yline[j]) m->general = true;
       }
+    if (m->general) {
+      // Every element must be a convex, counter-clockwise quadrilateral: the
+      // Jacobian determinant of the bilinear map is affine in the reference
+      // coordinates, so it is positive everywhere iff it is at the corners,
+      // where it is the cross product of the two edges meeting there.
+      m->xy.assign(vertex_xy, vertex_xy + 2 * (size_t)vw * (ny + 1));
+      const double *v = m->xy.data();
+      for (int ky = 0; ky < ny; ++ky)
+        for (int kx = 0; kx < nx; ++kx) {
+          const double *p00 = v + 2 * ((size_t)ky * vw + kx), *p10 = p00 + 2;
+          const double *p01 = v + 2 * ((size_t)(ky + 1) * vw + kx), *p11 = p01 + 2;
+          auto cross = [](const double *o, const double *a, const double *b) {
+            return (a[0] - o[0]) * (b[1] - o[1]) - (a[1] - o[1]) * (b[0] - o[0]);
+          };
+          if (!(cross(p00, p10, p01) > 0 && cross(p10, p11, p00) > 0 &&
+                cross(p11, p01, p10) > 0 && cross(p01, p00, p11) > 0)) {
+            delete m;
+            return fail(MEVP_ERR_ARG,
+                        "mesh_create: element (%d,%d) is not a convex counter-clockwise "
+                        "quadrilateral",
+                        kx, ky);
+          }
+        }
+      *out = m;
+      return MEVP_OK;
+    }
   }
   for (int i = 0; i < nx; ++i)
     if (!(m->xline[i + 1] > m->xline[i])) {
@@ -249,11 +270,14 @@ void mevp_mesh_destroy(mevp_mesh *mesh) { delete mesh; }
 int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
                                size_t *bytes) {
   if (!mesh || !bytes) return fail(MEVP_ERR_ARG, "workspace_bytes: NULL argument");
-  if (n_stress != 3 && n_stress != 6)
-    return fail(MEVP_ERR_ARG, "n_stress=%d: DG stress needs 3 or 6 dofs", n_stress);
+  if (n_stress != 3 && n_stress != 6 && n_stress != 8)
+    return fail(MEVP_ERR_ARG, "n_stress=%d: DG stress needs 3, 6 or 8 dofs", n_stress);
   if (n_adv != 1) return fail(MEVP_ERR_UNSUPPORTED, "n_adv=%d: this build handles DG0 (1)", n_adv);
   if (precision != MEVP_FP64 && precision != MEVP_MIXED)
     return fail(MEVP_ERR_ARG, "precision=%d unknown", precision);
+  if (mesh->general && precision != MEVP_FP64)
+    return fail(MEVP_ERR_UNSUPPORTED,
+                "precision=%d: general (non-rectilinear) meshes run in FP64 only", precision);
   *bytes = make_layout(mesh, n_stress, n_adv, precision).total;
   return MEVP_OK;
 }
@@ -309,6 +333,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.prec = precision;
   d.xline = (const double *)(b + L.xline);
   d.yline = (const double *)(b + L.yline);
+  d.xy = mesh->general ? (const double2 *)(b + L.xy) : nullptr;
   d.lines = (double *)(b + L.lines);
   s->pstar_buf = (double *)(b + L.pstar);
   d.flags = (int *)(b + L.flags);
@@ -349,6 +374,9 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
                         cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((void *)d.yline, mesh->yline.data(), sizeof(double) * (d.ny + 1),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && mesh->general)
+    e = cudaMemcpyAsync((void *)d.xy, mesh->xy.data(), sizeof(double) * mesh->xy.size(),
                         cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) r2 = cuda_fail(e, "state_create: initialise workspace");

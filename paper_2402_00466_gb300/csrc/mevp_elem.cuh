@@ -33,9 +33,11 @@ template <int NS> __host__ __device__ constexpr int sidx(int kx, int ky) {
   return (kx == 0 && ky == 0) ? 0
        : (kx == 1 && ky == 0) ? 1
        : (kx == 0 && ky == 1) ? 2
-       : (NS == 6 && kx == 2 && ky == 0) ? 3
-       : (NS == 6 && kx == 1 && ky == 1) ? 4
-       : (NS == 6 && kx == 0 && ky == 2) ? 5
+       : (NS >= 6 && kx == 2 && ky == 0) ? 3
+       : (NS >= 6 && kx == 1 && ky == 1) ? 4
+       : (NS >= 6 && kx == 0 && ky == 2) ? 5
+       : (NS == 8 && kx == 2 && ky == 1) ? 6
+       : (NS == 8 && kx == 1 && ky == 2) ? 7
                                          : -1;
 }
 

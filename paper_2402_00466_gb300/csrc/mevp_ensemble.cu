@@ -258,6 +258,13 @@ int mevp_ensemble_create(mevp_state *const *members, int n, mevp_ensemble **out)
     for (int j = 0; j < i; ++j)
       if (members[j] == members[i])
         return efail(MEVP_ERR_ARG, "ensemble_create: member %d repeats member %d", i, j);
+    if (members[i]->d.xy)
+      return efail(MEVP_ERR_UNSUPPORTED,
+                   "ensemble_create: member %d has a general mesh; ensembles take rectilinear "
+                   "meshes", i);
+    if (members[i]->ns == 8)
+      return efail(MEVP_ERR_UNSUPPORTED,
+                   "ensemble_create: member %d has 8 stress dofs; ensembles take 3 or 6", i);
     if (members[i]->prec != members[0]->prec)
       return efail(MEVP_ERR_ARG, "ensemble_create: members must share one precision");
     if (members[i]->stream != members[0]->stream)

@@ -21,6 +21,7 @@
 // On a rectangle the inverse local mass and the Jacobian cancel, leaving the
 // compile-time reference tables of mevp_ref.cuh scaled by 1/hx, 1/hy.
 #include "mevp_elem.cuh"
+#include "mevp_geom.cuh"
 #include "mevp_internal.cuh"
 #include "mevp_ref.cuh"
 
@@ -30,15 +31,6 @@ namespace {
 
 constexpr int kElemBlock = 128;
 constexpr int kNodeBlock = 256;
-
-__device__ __forceinline__ void gather9(const double *__restrict__ f, int nw, int kx, int ky,
-                                        double out[9]) {
-  const double *base = f + (size_t)(2 * ky) * nw + 2 * kx;
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) out[a + 3 * b] = __ldg(base + (size_t)b * nw + a);
-}
 
 // Strain coefficients E11, E12, E22 (for the diagnostic read-back):
 // E11 = du/dx, E22 = dv/dy, E12 = (du/dy + dv/dx)/2, projected onto DG.
@@ -270,8 +262,10 @@ __global__ void k_strength(DevState d, double Pstar, double C) {
   d.Pe[K] = (d.pstar ? d.pstar[K] : Pstar) * h * exp(-C * (1.0 - a));
 }
 
-// Lumped mass m_j = rho_ice sum_K max(0,H_K) hx hy w_a w_b and area
-// l_j = sum_K hx hy w_a w_b (w = 1/6, 2/3, 1/6), then the node constants.
+// Lumped mass m_j = rho_ice sum_K max(0,H_K) int_K phi_j and area
+// l_j = sum_K int_K phi_j (hx hy w_a w_b on a rectangle, w = 1/6, 2/3, 1/6;
+// the exact integral against the affine det J on a general element), then the
+// node constants.
 __global__ void k_node_constants(DevState d, int cur, mevp_params p, int has_vo) {
   const int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= d.nn) return;
@@ -283,8 +277,13 @@ __global__ void k_node_constants(DevState d, int cur, mevp_params p, int has_vo)
     if (ky < 0 || ky >= d.ny) continue;
     for (int kx = kx1; kx <= kx2; ++kx) {
       if (kx < 0 || kx >= d.nx) continue;
-      const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
-      const double w = area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
+      double w;
+      if (d.xy) {
+        w = node_area_general(quad_map(d.xy, d.nx, kx, ky), ix - 2 * kx, iy - 2 * ky);
+      } else {
+        const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
+        w = area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
+      }
       l += w;
       mh += fmax(0.0, d.H[ky * d.nx + kx]) * w;
     }
@@ -386,7 +385,7 @@ cudaError_t launch_nan_check(const DevState &d, int cur, cudaStream_t st) {
 
 cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                            cudaStream_t st) {
-  k_mesh_lines<<<blocks(d.nx + d.ny, 256), 256, 0, st>>>(d);
+  if (!d.xy) k_mesh_lines<<<blocks(d.nx + d.ny, 256), 256, 0, st>>>(d);
   k_strength<<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
   k_node_constants<<<blocks(d.nn, 256), 256, 0, st>>>(d, cur, p, has_vo ? 1 : 0);
   return cudaGetLastError();
@@ -395,10 +394,14 @@ cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo,
 cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
                                 cudaStream_t st, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[0], st);
-  if (d.ns == 3)
+  if (d.xy)
+    launch_element_general(d, r, cur, st);
+  else if (d.ns == 3)
     k_element_f64<3><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
-  else
+  else if (d.ns == 6)
     k_element_f64<6><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
+  else
+    k_element_f64<8><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
   k_node_f64<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, cur, has_vo ? 1 : 0);
@@ -444,18 +447,25 @@ int f64_node_ctas_per_sm() {
 }
 
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st) {
+  if (d.xy) return launch_strain_diag_general(d, cur, st);
   if (d.ns == 3)
     k_strain_diag<3><<<blocks(d.ne, 128), 128, 0, st>>>(d, cur);
-  else
+  else if (d.ns == 6)
     k_strain_diag<6><<<blocks(d.ne, 128), 128, 0, st>>>(d, cur);
+  else
+    k_strain_diag<8><<<blocks(d.ne, 128), 128, 0, st>>>(d, cur);
   return cudaGetLastError();
 }
 
 cudaError_t launch_force_diag(const DevState &d, cudaStream_t st) {
-  if (d.ns == 3)
+  if (d.xy)
+    launch_force_elem_general(d, st);
+  else if (d.ns == 3)
     k_force_elem<3><<<blocks(d.ne, 128), 128, 0, st>>>(d);
-  else
+  else if (d.ns == 6)
     k_force_elem<6><<<blocks(d.ne, 128), 128, 0, st>>>(d);
+  else
+    k_force_elem<8><<<blocks(d.ne, 128), 128, 0, st>>>(d);
   k_force_gather<<<blocks(d.nn, 256), 256, 0, st>>>(d);
   return cudaGetLastError();
 }

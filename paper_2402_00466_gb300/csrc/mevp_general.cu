@@ -1,0 +1,151 @@
+// mevp_general.cu -- FP64 element kernels of the mEVP subcycle on general
+// (non-affine) quadrilateral meshes.
+//
+// k_element_gen does what k_element_f64 does on a rectilinear mesh (strain,
+// stress update of Listing 1 / App. A, element forces of the weak
+// divergence), with the bilinear element map evaluated on the fly from the
+// four vertices (Sec. 3.2) and the local DG mass matrix factored per element
+// (mevp_geom.cuh).  The node kernel (force gather in the fixed SW, SE, NW, NE
+// order and the velocity update) is shared with the rectilinear path.
+#include "mevp_geom.cuh"
+#include "mevp_internal.cuh"
+
+namespace mevp {
+
+namespace {
+
+constexpr int kGenBlock = 128;
+
+template <int NS>
+__device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int cur, int K) {
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const QuadMap m = quad_map(d.xy, d.nx, kx, ky);
+  MassFactor<NS> F;
+  mass_factor<NS>(m, F);
+  double Pc[NS], Qc[NS], Gc[NS];
+  {
+    double u[9], v[9];
+    gather9(d.vel[cur], d.nw, kx, ky, u);
+    gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+    double E11[NS], E22[NS], Esh[NS];
+    strain_general<NS>(m, F, u, v, E11, E22, Esh);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Pc[s] = E11[s] + E22[s];
+      Qc[s] = r.ie * (E11[s] - E22[s]);
+      Gc[s] = r.ie * Esh[s];
+    }
+  }
+  double S11[NS], S12[NS], S22[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
+    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
+    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+  }
+  const double Ph = __ldg(d.Pe + K) * r.hainv;
+  relax_general<NS>(m, F, S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    d.S[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
+    d.S[(size_t)(1 * NS + s) * d.ne + K] = S12[s];
+    d.S[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
+  }
+  double fx[9], fy[9];
+  forces_general<NS>(m, S11, S12, S22, fx, fy);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    d.fbuf[(size_t)j * d.ne + K] = fx[j];
+    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kGenBlock) k_element_gen(DevState d, Rheo r, int cur) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K < d.ne) elem_gen<NS>(d, r, cur, K);
+}
+
+// Strain coefficients E11, E12, E22 of the current velocity (read-back).
+template <int NS>
+__global__ void k_strain_diag_gen(DevState d, int cur) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const QuadMap m = quad_map(d.xy, d.nx, kx, ky);
+  MassFactor<NS> F;
+  mass_factor<NS>(m, F);
+  double u[9], v[9];
+  gather9(d.vel[cur], d.nw, kx, ky, u);
+  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+  double E11[NS], E22[NS], Esh[NS];
+  strain_general<NS>(m, F, u, v, E11, E22, Esh);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    d.diag[(size_t)(0 * NS + s) * d.ne + K] = E11[s];
+    d.diag[(size_t)(1 * NS + s) * d.ne + K] = 0.5 * Esh[s];
+    d.diag[(size_t)(2 * NS + s) * d.ne + K] = E22[s];
+  }
+}
+
+// Element forces of the current stress into the force buffer (read-back).
+template <int NS>
+__global__ void k_force_elem_gen(DevState d) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const QuadMap m = quad_map(d.xy, d.nx, kx, ky);
+  double S11[NS], S12[NS], S22[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
+    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
+    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+  }
+  double fx[9], fy[9];
+  forces_general<NS>(m, S11, S12, S22, fx, fy);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    d.fbuf[(size_t)j * d.ne + K] = fx[j];
+    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+  }
+}
+
+inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
+  const int g = blocks(d.ne, kGenBlock);
+  if (d.ns == 3)
+    k_element_gen<3><<<g, kGenBlock, 0, st>>>(d, r, cur);
+  else if (d.ns == 6)
+    k_element_gen<6><<<g, kGenBlock, 0, st>>>(d, r, cur);
+  else
+    k_element_gen<8><<<g, kGenBlock, 0, st>>>(d, r, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_strain_diag_general(const DevState &d, int cur, cudaStream_t st) {
+  const int g = blocks(d.ne, 128);
+  if (d.ns == 3)
+    k_strain_diag_gen<3><<<g, 128, 0, st>>>(d, cur);
+  else if (d.ns == 6)
+    k_strain_diag_gen<6><<<g, 128, 0, st>>>(d, cur);
+  else
+    k_strain_diag_gen<8><<<g, 128, 0, st>>>(d, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_elem_general(const DevState &d, cudaStream_t st) {
+  const int g = blocks(d.ne, 128);
+  if (d.ns == 3)
+    k_force_elem_gen<3><<<g, 128, 0, st>>>(d);
+  else if (d.ns == 6)
+    k_force_elem_gen<6><<<g, 128, 0, st>>>(d);
+  else
+    k_force_elem_gen<8><<<g, 128, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace mevp

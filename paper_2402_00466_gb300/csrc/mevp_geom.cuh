@@ -1,0 +1,365 @@
+// mevp_geom.cuh -- per-element arithmetic of the FP64 subcycle on general
+// (non-affine) quadrilateral meshes.
+//
+// Every element is the image of the reference square under the bilinear (Q1)
+// map of its four vertices, evaluated on the fly at the Gauss points (the
+// paper's "on-the-fly map", Sec. 3.2; the map from 4 vertices with 2 values
+// each).  In centred coordinates xh = xi - 1/2, eh = eta - 1/2 the map is
+//   x(xh, eh) = x_c + A xh + B eh + c xh eh,
+//   A = (bottom + top edge)/2, B = (left + right edge)/2,
+//   c = top edge - bottom edge,
+// so the Jacobian columns are dx/dxi = A + c eh and dx/deta = B + c xh, and
+// det J = d0 + d1 xh + d2 eh is affine in the reference coordinates.
+//
+// With that:
+//   * strain: the L2 projection E = M^-1 int psi eps(v) detJ.  detJ cancels
+//     against the inverse Jacobian inside the integrand, e.g.
+//     detJ du/dx = J11 du/dxi - J10 du/deta, so no division is needed;
+//   * stress: S <- (1-1/alpha) S + M^-1 int psi detJ s_vp / alpha (Listing 1
+//     with the element's own iMJwPSI, factored rather than stored);
+//   * divergence: f_j = -int sigma : grad phi_j detJ, where detJ again
+//     cancels: f_x = -sum_g w_g [(s11 J11 - s12 J01) dphi/dxi
+//                              + (s12 J00 - s11 J10) dphi/deta];
+//   * the local DG mass matrix M = d0 diag(mass) + d1 MX + d2 MY uses the
+//     exact moment tables of mevp_ref.cuh (the Gauss rule of App. A
+//     integrates these products exactly) and is factored as L D L^T per
+//     element.
+// Every sum over Gauss points is sum-factorised along the two directions.
+#pragma once
+
+#include "mevp_elem.cuh"
+#include "mevp_internal.cuh"
+#include "mevp_ref.cuh"
+
+namespace mevp {
+
+// The 9 values of a CG2 nodal field on element (kx, ky), local node a + 3b.
+__device__ __forceinline__ void gather9(const double *__restrict__ f, int nw, int kx, int ky,
+                                        double out[9]) {
+  const double *base = f + (size_t)(2 * ky) * nw + 2 * kx;
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a + 3 * b] = __ldg(base + (size_t)b * nw + a);
+}
+
+// Centred bilinear map of one element.
+struct QuadMap {
+  double Ax, Ay, Bx, By, cx, cy;
+  // det J = d0 + d1 xh + d2 eh
+  __device__ __forceinline__ double d0() const { return fma(Ax, By, -(Bx * Ay)); }
+  __device__ __forceinline__ double d1() const { return fma(Ax, cy, -(cx * Ay)); }
+  __device__ __forceinline__ double d2() const { return fma(cx, By, -(Bx * cy)); }
+};
+
+__device__ __forceinline__ QuadMap quad_map(const double2 *__restrict__ xy, int nx, int kx,
+                                            int ky) {
+  const size_t vw = (size_t)nx + 1;
+  const double2 p00 = xy[(size_t)ky * vw + kx], p10 = xy[(size_t)ky * vw + kx + 1];
+  const double2 p01 = xy[(size_t)(ky + 1) * vw + kx], p11 = xy[(size_t)(ky + 1) * vw + kx + 1];
+  const double bx = p10.x - p00.x, by = p10.y - p00.y;  // bottom edge
+  const double tx = p11.x - p01.x, ty = p11.y - p01.y;  // top edge
+  const double lx = p01.x - p00.x, ly = p01.y - p00.y;  // left edge
+  const double rx = p11.x - p10.x, ry = p11.y - p10.y;  // right edge
+  QuadMap m;
+  m.Ax = 0.5 * (bx + tx);
+  m.Ay = 0.5 * (by + ty);
+  m.Bx = 0.5 * (lx + rx);
+  m.By = 0.5 * (ly + ry);
+  m.cx = tx - bx;
+  m.cy = ty - by;
+  return m;
+}
+
+// Jacobian entries at 2-D Gauss point (gx, gy) of an NGP rule.
+template <int N>
+__device__ __forceinline__ void jac_at(const QuadMap &m, int gx, int gy, double &j00,
+                                       double &j01, double &j10, double &j11) {
+  const double xh = Gauss<N>::xh(gx), eh = Gauss<N>::xh(gy);
+  j00 = eh == 0.0 ? m.Ax : fma(m.cx, eh, m.Ax);
+  j10 = eh == 0.0 ? m.Ay : fma(m.cy, eh, m.Ay);
+  j01 = xh == 0.0 ? m.Bx : fma(m.cx, xh, m.Bx);
+  j11 = xh == 0.0 ? m.By : fma(m.cy, xh, m.By);
+}
+
+// Reference gradients (d/dxi, d/deta) of a Q2 field at the N x N Gauss
+// points, sum-factorised: row sums along xi, then columns along eta.
+template <int N>
+__device__ __forceinline__ void ref_grad_gauss(const double w[9], double gxi[N * N],
+                                               double geta[N * N]) {
+  double rd[3][N], r0[3][N];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) {
+      double a1 = -0.0, a0 = -0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double cd = dlq<N>(a, gx), c0 = lq<N>(a, gx);
+        if (cd != 0.0) a1 = cmul_acc(cd, w[a + 3 * b], a1);
+        if (c0 != 0.0) a0 = cmul_acc(c0, w[a + 3 * b], a0);
+      }
+      rd[b][gx] = a1;
+      r0[b][gx] = a0;
+    }
+#pragma unroll
+  for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) {
+      double s1 = -0.0, s2 = -0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double c0 = lq<N>(b, gy), cd = dlq<N>(b, gy);
+        if (c0 != 0.0) s1 = cmul_acc(c0, rd[b][gx], s1);
+        if (cd != 0.0) s2 = cmul_acc(cd, r0[b][gx], s2);
+      }
+      gxi[gx + N * gy] = s1;
+      geta[gx + N * gy] = s2;
+    }
+}
+
+// Moments R_s = sum_g w_g psi_s(g) D_g of Gauss-point values D (no mass
+// scaling), sum-factorised.
+template <int NS>
+__device__ __forceinline__ void gauss_moments(const double D[DgSpace<NS>::NGP * DgSpace<NS>::NGP],
+                                              double R[NS]) {
+  constexpr int N = DgSpace<NS>::NGP;
+  double t[3][N];
+#pragma unroll
+  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+    for (int gy = 0; gy < N; ++gy) {
+      double acc = -0.0;
+      if (sidx<NS>(kx, 0) >= 0) {
+#pragma unroll
+        for (int gx = 0; gx < N; ++gx) {
+          const double c = Gauss<N>::w(gx) * pg<N>(kx, gx);
+          if (c != 0.0) acc = cmul_acc(c, D[gx + N * gy], acc);
+        }
+      }
+      t[kx][gy] = acc;
+    }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double acc = -0.0;
+#pragma unroll
+    for (int gy = 0; gy < N; ++gy) {
+      const double c = Gauss<N>::w(gy) * pg<N>(dgy(s), gy);
+      if (c != 0.0) acc = cmul_acc(c, t[dgx(s)][gy], acc);
+    }
+    R[s] = acc;
+  }
+}
+
+// L D L^T factor of the local DG mass matrix of a bilinear element: the
+// strict lower triangle of L, row by row (L(i,k) at i(i-1)/2 + k; the unit
+// diagonal is implicit), and 1/D.
+template <int NS> struct MassFactor {
+  double L[NS * (NS - 1) / 2];
+  double Dinv[NS];
+  __device__ __forceinline__ double &at(int i, int k) { return L[i * (i - 1) / 2 + k]; }
+  __device__ __forceinline__ double at(int i, int k) const { return L[i * (i - 1) / 2 + k]; }
+};
+
+template <int NS>
+__device__ __forceinline__ void mass_factor(const QuadMap &m, MassFactor<NS> &F) {
+  const double d0 = m.d0(), d1 = m.d1(), d2 = m.d2();
+  double D[NS];
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    double dj = d0 * dgmass(j);
+#pragma unroll
+    for (int k = 0; k < j; ++k) dj = fma(-F.at(j, k) * D[k], F.at(j, k), dj);
+    D[j] = dj;
+    F.Dinv[j] = 1.0 / dj;
+#pragma unroll
+    for (int i = j + 1; i < NS; ++i) {
+      double a = 0.0;
+      if (mx(i, j) != 0.0) a = d1 * mx(i, j);
+      if (my(i, j) != 0.0) a = fma(d2, my(i, j), a);
+#pragma unroll
+      for (int k = 0; k < j; ++k) a = fma(-F.at(i, k) * D[k], F.at(j, k), a);
+      F.at(i, j) = a * F.Dinv[j];
+    }
+  }
+}
+
+// x <- M^-1 x with the factor above.
+template <int NS>
+__device__ __forceinline__ void mass_solve(const MassFactor<NS> &F, double x[NS]) {
+#pragma unroll
+  for (int i = 1; i < NS; ++i)
+#pragma unroll
+    for (int k = 0; k < i; ++k) x[i] = fma(-F.at(i, k), x[k], x[i]);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) x[i] *= F.Dinv[i];
+#pragma unroll
+  for (int ii = 0; ii < NS - 1; ++ii) {
+    const int i = NS - 2 - ii;
+#pragma unroll
+    for (int k = i + 1; k < NS; ++k) x[i] = fma(-F.at(k, i), x[k], x[i]);
+  }
+}
+
+// Strain of the nodal velocities u, v as DG coefficients:
+// E11 = M^-1 int psi du/dx, E22 = M^-1 int psi dv/dy,
+// Esh = M^-1 int psi (du/dy + dv/dx)  (= 2 E12).
+template <int NS>
+__device__ __forceinline__ void strain_general(const QuadMap &m, const MassFactor<NS> &F,
+                                               const double u[9], const double v[9],
+                                               double E11[NS], double E22[NS], double Esh[NS]) {
+  constexpr int N = DgSpace<NS>::NGP, NG = N * N;
+  double D11[NG], D22[NG], Dsh[NG];
+  {
+    double uxi[NG], ueta[NG], vxi[NG], veta[NG];
+    ref_grad_gauss<N>(u, uxi, ueta);
+    ref_grad_gauss<N>(v, vxi, veta);
+#pragma unroll
+    for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+      for (int gx = 0; gx < N; ++gx) {
+        const int g = gx + N * gy;
+        double j00, j01, j10, j11;
+        jac_at<N>(m, gx, gy, j00, j01, j10, j11);
+        D11[g] = fma(j11, uxi[g], -(j10 * ueta[g]));  // detJ du/dx
+        D22[g] = fma(j00, veta[g], -(j01 * vxi[g]));  // detJ dv/dy
+        const double duy = fma(j00, ueta[g], -(j01 * uxi[g]));
+        const double dvx = fma(j11, vxi[g], -(j10 * veta[g]));
+        Dsh[g] = duy + dvx;
+      }
+  }
+  gauss_moments<NS>(D11, E11);
+  gauss_moments<NS>(D22, E22);
+  gauss_moments<NS>(Dsh, Esh);
+  mass_solve<NS>(F, E11);
+  mass_solve<NS>(F, E22);
+  mass_solve<NS>(F, Esh);
+}
+
+// Relaxed stress update on a general element from the strain coefficients:
+// S <- fac S + M^-1 int psi detJ (X (p +- Q/e), X G/e) - Ph e_0, with
+// X = Ph / sqrt(Delta^2), Ph = P/(2 alpha) (invariant form of Listing 1).
+template <int NS>
+__device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor<NS> &F,
+                                              double S11[NS], double S12[NS], double S22[NS],
+                                              const double Pc[NS], const double Qc[NS],
+                                              const double Gc[NS], double Ph, double dmin2,
+                                              double fac, double ie) {
+  constexpr int N = DgSpace<NS>::NGP, NG = N * N;
+  double RP[NS], RQ[NS], RG[NS];
+  {
+    double pgv[NG], qgv[NG], ggv[NG];
+    gauss_eval<NS>(Pc, pgv);
+    gauss_eval<NS>(Qc, qgv);
+    gauss_eval<NS>(Gc, ggv);
+#pragma unroll
+    for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+      for (int gx = 0; gx < N; ++gx) {
+        const int g = gx + N * gy;
+        double j00, j01, j10, j11;
+        jac_at<N>(m, gx, gy, j00, j01, j10, j11);
+        const double det = fma(j00, j11, -(j01 * j10));
+        const double d2 = fma(ggv[g], ggv[g], fma(qgv[g], qgv[g], fma(pgv[g], pgv[g], dmin2)));
+        const double Xd = Ph * rsqrt(d2) * det;
+        pgv[g] *= Xd;
+        qgv[g] *= Xd;
+        ggv[g] *= Xd;
+      }
+    gauss_moments<NS>(pgv, RP);
+    gauss_moments<NS>(qgv, RQ);
+    gauss_moments<NS>(ggv, RG);
+  }
+  mass_solve<NS>(F, RP);
+  mass_solve<NS>(F, RQ);
+  mass_solve<NS>(F, RG);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const double base = (s == 0) ? RP[s] - Ph : RP[s];
+    const double q = ie * RQ[s];
+    S11[s] = fma(fac, S11[s], base + q);
+    S22[s] = fma(fac, S22[s], base - q);
+    S12[s] = fma(fac, S12[s], ie * RG[s]);
+  }
+}
+
+// Element forces f_j = -int sigma : grad phi_j of a DG stress on a general
+// element (fx[j], fy[j] for the 9 local Q2 nodes, j = a + 3b).
+template <int NS>
+__device__ __forceinline__ void forces_general(const QuadMap &m, const double S11[NS],
+                                               const double S12[NS], const double S22[NS],
+                                               double fx[9], double fy[9]) {
+  constexpr int N = DgSpace<NS>::NGP, NG = N * N;
+  double ax[NG], bx[NG], ay[NG], by[NG];
+  {
+    double s11[NG], s12[NG], s22[NG];
+    gauss_eval<NS>(S11, s11);
+    gauss_eval<NS>(S12, s12);
+    gauss_eval<NS>(S22, s22);
+#pragma unroll
+    for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+      for (int gx = 0; gx < N; ++gx) {
+        const int g = gx + N * gy;
+        double j00, j01, j10, j11;
+        jac_at<N>(m, gx, gy, j00, j01, j10, j11);
+        const double w = Gauss<N>::w(gx) * Gauss<N>::w(gy);
+        ax[g] = w * fma(s11[g], j11, -(s12[g] * j01));
+        bx[g] = w * fma(s12[g], j00, -(s11[g] * j10));
+        ay[g] = w * fma(s12[g], j11, -(s22[g] * j01));
+        by[g] = w * fma(s22[g], j00, -(s12[g] * j10));
+      }
+  }
+  // f_ab = -sum_gx [dL_a(gx) sum_gy L_b(gy) a_g + L_a(gx) sum_gy dL_b(gy) b_g]
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    double tax[N], tbx[N], tay[N], tby[N];
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) {
+      double p = -0.0, q = -0.0, r = -0.0, t = -0.0;
+#pragma unroll
+      for (int gy = 0; gy < N; ++gy) {
+        const double c0 = lq<N>(b, gy), cd = dlq<N>(b, gy);
+        const int g = gx + N * gy;
+        if (c0 != 0.0) {
+          p = cmul_acc(c0, ax[g], p);
+          r = cmul_acc(c0, ay[g], r);
+        }
+        if (cd != 0.0) {
+          q = cmul_acc(cd, bx[g], q);
+          t = cmul_acc(cd, by[g], t);
+        }
+      }
+      tax[gx] = p;
+      tbx[gx] = q;
+      tay[gx] = r;
+      tby[gx] = t;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double x = -0.0, y = -0.0;
+#pragma unroll
+      for (int gx = 0; gx < N; ++gx) {
+        const double cd = dlq<N>(a, gx), c0 = lq<N>(a, gx);
+        if (cd != 0.0) {
+          x = cmul_acc(cd, tax[gx], x);
+          y = cmul_acc(cd, tay[gx], y);
+        }
+        if (c0 != 0.0) {
+          x = cmul_acc(c0, tbx[gx], x);
+          y = cmul_acc(c0, tby[gx], y);
+        }
+      }
+      fx[a + 3 * b] = -x;
+      fy[a + 3 * b] = -y;
+    }
+  }
+}
+
+// int_K phi_j for local node (a, b): d0 W_a W_b + d1 X_a W_b + d2 W_a X_b
+// with W the Simpson weights and X_a = int xh L_a (exact for the affine det).
+__device__ __forceinline__ double node_area_general(const QuadMap &m, int a, int b) {
+  return fma(m.d0(), q2w(a) * q2w(b), fma(m.d1(), q2xw(a) * q2w(b), m.d2() * (q2w(a) * q2xw(b))));
+}
+
+}  // namespace mevp

@@ -13,6 +13,8 @@ struct mevp_mesh {
   int nx = 0, ny = 0;
   std::vector<double> xline;  // nx+1 vertex x coordinates (rectilinear mesh)
   std::vector<double> yline;  // ny+1 vertex y coordinates
+  bool general = false;       // vertices not on a rectilinear grid
+  std::vector<double> xy;     // general mesh: [(nx+1)(ny+1)][2] vertex coordinates
 };
 
 namespace mevp {
@@ -54,6 +56,7 @@ inline Rheo make_rheo(const mevp_params &p) {
 struct DevState {
   int nx, ny, ne, nw, nh, nn, ns, prec;
   const double *xline, *yline;
+  const double2 *xy;   // general mesh: [(nx+1)(ny+1)] vertices; NULL on rectilinear meshes
   double *lines;       // [hx: nx][1/hx: nx][hy: ny][1/hy: ny], from the mesh lines
   double *vel[2];      // [2][nn] ping-pong
   double *S;           // FP64: [3][ns][ne]
@@ -105,6 +108,10 @@ cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo,
 cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
                                 cudaStream_t st, cudaEvent_t *ev);
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
+// general (non-affine) meshes: element kernel and read-back diagnostics
+cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
+cudaError_t launch_strain_diag_general(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_force_elem_general(const DevState &d, cudaStream_t st);
 
 // FP64 ensemble: persistent element kernel (block size chosen from
 // kF64Blocks) + persistent node kernel (256 threads), over their work lists

@@ -447,6 +447,9 @@ cudaError_t setup_mixed_kernels() {
     e = cudaFuncSetAttribute(k_subcycle_mix<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kFusedSmem);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_subcycle_mix<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFusedSmem);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_ens_mix<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Tile<32, 8>::smem);
   if (e == cudaSuccess)
@@ -555,16 +558,20 @@ cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_p
     const dim3 block(FTX, FTY);
     if (d.ns == 3)
       k_subcycle_mix<3><<<grid, block, kFusedSmem, st>>>(d, a, cur);
-    else
+    else if (d.ns == 6)
       k_subcycle_mix<6><<<grid, block, kFusedSmem, st>>>(d, a, cur);
+    else
+      k_subcycle_mix<8><<<grid, block, kFusedSmem, st>>>(d, a, cur);
     if (ev) cudaEventRecord(ev[1], st);
     if (ev) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
   }
   if (d.ns == 3)
     k_element_mix<3><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, a, cur);
-  else
+  else if (d.ns == 6)
     k_element_mix<6><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, a, cur);
+  else
+    k_element_mix<8><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, a, cur);
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
   k_node_mix<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, a, cur);

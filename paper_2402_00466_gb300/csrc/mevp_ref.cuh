@@ -7,9 +7,10 @@
 //   * DG stress basis (Sec. 2.1: stress in the gradient space of the CG2
 //     velocity, tensor-valued DG): products p_kx(xi) p_ky(eta) of the centred
 //     Legendre functions p0 = 1, p1 = t - 1/2, p2 = (t - 1/2)^2 - 1/12, total
-//     degree <= 1 (3 dofs) or <= 2 (6 dofs), in the order
-//     (0,0) (1,0) (0,1) (2,0) (1,1) (0,2).  Orthogonal, so on rectangles the
-//     local mass matrix is diagonal: int p_k^2 = 1, 1/12, 1/180.
+//     degree <= 1 (3 dofs) or <= 2 (6 dofs), or degree <= 2 in each
+//     variable without the biquadratic product (8 dofs, App. A), in the order
+//     (0,0) (1,0) (0,1) (2,0) (1,1) (0,2) (2,1) (1,2).  Orthogonal, so on
+//     rectangles the local mass matrix is diagonal: int p_k^2 = 1, 1/12, 1/180.
 //   * CG2 velocity basis: Q2 Lagrange L_a(xi) L_b(eta), nodes {0, 1/2, 1},
 //     local node j = a + 3b, with L0 = (1-t)(1-2t), L1 = 4t(1-t), L2 = t(2t-1).
 //   * Exact 1-D moments  IB[k][b] = int_0^1 p_k L_b,  ID[k][a] = int_0^1 p_k L_a'.
@@ -17,7 +18,7 @@
 //     onto the DG space, and the weak divergence of a DG field tested with
 //     Q2, are exact rational matrices (no quadrature needed: the Gauss rule
 //     of App. A integrates these polynomial products exactly).
-//   * Gauss-Legendre rules (App. A: 2x2 points for 3 dofs, 3x3 for 6) with
+//   * Gauss-Legendre rules (App. A: 2x2 points for 3 dofs, 3x3 for 6 and 8) with
 //     closed-form points 1/2 -+ 1/(2 sqrt 3) and 1/2, 1/2 -+ sqrt(15)/10.
 #pragma once
 
@@ -42,10 +43,10 @@ __host__ __device__ constexpr double pnorm(int k) {
 
 // ---- DG index -> 1-D degrees --------------------------------------------
 __host__ __device__ constexpr int dgx(int s) {
-  return s == 1 ? 1 : s == 3 ? 2 : s == 4 ? 1 : 0;
+  return s == 1 ? 1 : s == 3 ? 2 : s == 4 ? 1 : s == 6 ? 2 : s == 7 ? 1 : 0;
 }
 __host__ __device__ constexpr int dgy(int s) {
-  return s == 2 ? 1 : s == 4 ? 1 : s == 5 ? 2 : 0;
+  return s == 2 ? 1 : s == 4 ? 1 : s == 5 ? 2 : s == 6 ? 1 : s == 7 ? 2 : 0;
 }
 __host__ __device__ constexpr double dgmass(int s) { return pnorm(dgx(s)) * pnorm(dgy(s)); }
 
@@ -75,6 +76,7 @@ template <int NGP> __host__ __device__ constexpr double pg(int k, int g) {
 template <int NS> struct DgSpace;
 template <> struct DgSpace<3> { static constexpr int NGP = 2; };
 template <> struct DgSpace<6> { static constexpr int NGP = 3; };
+template <> struct DgSpace<8> { static constexpr int NGP = 3; };
 
 // DG basis function s at 2-D Gauss point g = gx + NGP*gy
 template <int NS> __host__ __device__ constexpr double psi(int s, int g) {
@@ -104,5 +106,43 @@ __host__ __device__ constexpr double geta(int j, int s) {
 }
 // 1-D integral of the Q2 Lagrange functions: Simpson weights 1/6, 2/3, 1/6
 __host__ __device__ constexpr double q2w(int a) { return a == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+// ---- general (bilinear) element maps -------------------------------------
+// In centred coordinates x = t - 1/2 the Q2 Lagrange functions are
+// L0 = 2x^2 - x, L1 = 1 - 4x^2, L2 = 2x^2 + x, with derivatives 4x - 1, -8x,
+// 4x + 1.  Values at 1-D Gauss point g, using the exact x^2 of the rule
+// (1/12 for 2 points; 3/20 and 0 for 3 points).
+template <int NGP> __host__ __device__ constexpr double gsq(int g) {
+  return NGP == 2 ? 1.0 / 12.0 : (g == 1 ? 0.0 : 3.0 / 20.0);
+}
+template <int NGP> __host__ __device__ constexpr double lq(int a, int g) {
+  return a == 0 ? 2.0 * gsq<NGP>(g) - Gauss<NGP>::xh(g)
+       : a == 1 ? 1.0 - 4.0 * gsq<NGP>(g)
+                : 2.0 * gsq<NGP>(g) + Gauss<NGP>::xh(g);
+}
+template <int NGP> __host__ __device__ constexpr double dlq(int a, int g) {
+  return a == 0 ? 4.0 * Gauss<NGP>::xh(g) - 1.0
+       : a == 1 ? -8.0 * Gauss<NGP>::xh(g)
+                : 4.0 * Gauss<NGP>::xh(g) + 1.0;
+}
+// First moments int x p_i p_j over [-1/2, 1/2]: x p0 = p1 and
+// x p1 = p2 + p0/12 give 1/12 for (0,1) and 1/180 for (1,2); all others vanish.
+__host__ __device__ constexpr double xmom(int i, int j) {
+  return (i + j == 1) ? 1.0 / 12.0 : (i + j == 3 && i != 3 && j != 3) ? 1.0 / 180.0 : 0.0;
+}
+// int x L_a over [-1/2, 1/2]: -1/12, 0, 1/12
+__host__ __device__ constexpr double q2xw(int a) {
+  return a == 0 ? -1.0 / 12.0 : a == 1 ? 0.0 : 1.0 / 12.0;
+}
+// The Jacobian determinant of a bilinear map is affine in the centred
+// coordinates, det = d0 + d1 xh + d2 eh, so the local DG mass matrix is
+// M = d0 diag(mass_s) + d1 MX + d2 MY with the exact moment matrices
+//   MX[s][t] = int xh psi_s psi_t,  MY[s][t] = int eh psi_s psi_t.
+__host__ __device__ constexpr double mx(int s, int t) {
+  return dgy(s) == dgy(t) ? xmom(dgx(s), dgx(t)) * pnorm(dgy(s)) : 0.0;
+}
+__host__ __device__ constexpr double my(int s, int t) {
+  return dgx(s) == dgx(t) ? pnorm(dgx(s)) * xmom(dgy(s), dgy(t)) : 0.0;
+}
 
 }  // namespace mevp

@@ -174,17 +174,27 @@ def make_case(name: str, L: float = DOMAIN_M, params: dict | None = None):
 
 
 def small_case(nx: int, ny: int, n_s: int, seed: int, L: float = DOMAIN_M, moving: bool = True,
-               params: dict | None = None):
+               params: dict | None = None, geometry: str = "uniform"):
     """A small seeded case of any size (iid ice, cyclone wind, optional smooth
-    initial velocity and random initial stress) for parity tests."""
+    initial velocity and random initial stress) for parity tests.  geometry:
+    "uniform", "perturbed" (random interior vertex moves, seed + 4000) or
+    "wavy" (smooth curvilinear map)."""
     ne, nn, nv = sizes(nx, ny)
     H, A = ice_iid(nx, ny, seed)
     rng = np.random.Generator(np.random.PCG64(seed + 1000))
-    tau = cyclone_wind_stress(node_coords_uniform(nx, ny, L, L), cyclone_params(seed + 2000, L))
+    if geometry == "uniform":
+        xy = uniform_vertices(nx, ny, L, L)
+    elif geometry == "perturbed":
+        xy = perturbed_vertices(nx, ny, seed + 4000, L=L)
+    elif geometry == "wavy":
+        xy = wavy_vertices(nx, ny, L=L)
+    else:
+        raise ValueError(f"unknown geometry {geometry!r}")
+    tau = cyclone_wind_stress(node_coords(nx, ny, xy), cyclone_params(seed + 2000, L))
     vel0 = smooth_velocity(nx, ny, seed + 3000, L=L) if moving else np.zeros((2, nn))
     S0 = rng.uniform(-5e3, 5e3, (3, n_s, ne)) if moving else np.zeros((3, n_s, ne))
     return dict(name=f"small{nx}x{ny}_dg{n_s}", nx=nx, ny=ny, n_s=n_s, n_a=1, n_sub=10, L=L,
-                xy=uniform_vertices(nx, ny, L, L), H=H, A=A, tau=tau, vel0=vel0, S0=S0,
+                xy=xy, H=H, A=A, tau=tau, vel0=vel0, S0=S0,
                 params=dict(DEFAULT_PARAMS if params is None else params))
 
 
@@ -207,3 +217,42 @@ def make_ensemble(name: str, L: float = DOMAIN_M, params: dict | None = None):
                             S0=np.zeros((3, n_s, ne)),
                             params=dict(DEFAULT_PARAMS if params is None else params)))
     return members
+
+
+def perturbed_vertices(nx: int, ny: int, seed: int, amp: float = 0.2, L: float = DOMAIN_M):
+    """Vertices (N_v, 2) of a non-affine quad mesh: the interior vertices of a
+    uniform mesh moved by U[-amp h, amp h] in each coordinate (PCG64(seed)).
+    amp < 0.25 keeps every element convex."""
+    xy = uniform_vertices(nx, ny, L, L).reshape(ny + 1, nx + 1, 2)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hx, hy = L / nx, L / ny
+    inner = xy[1:-1, 1:-1]
+    inner[..., 0] += rng.uniform(-amp * hx, amp * hx, inner.shape[:2])
+    inner[..., 1] += rng.uniform(-amp * hy, amp * hy, inner.shape[:2])
+    return xy.reshape(-1, 2).copy()
+
+
+def wavy_vertices(nx: int, ny: int, amp: float = 0.3, L: float = DOMAIN_M):
+    """Vertices (N_v, 2) of a smoothly curvilinear mesh: the uniform mesh under
+    x' = x + a h sin(2 pi y/L) sin(pi x/L), y' = y + a h sin(2 pi x/L) sin(pi y/L)
+    (boundary fixed; a = amp, h the element size)."""
+    xy = uniform_vertices(nx, ny, L, L)
+    x, y = xy[:, 0] / L, xy[:, 1] / L
+    h = L / max(nx, ny)
+    out = xy.copy()
+    out[:, 0] += amp * h * np.sin(2 * math.pi * y) * np.sin(math.pi * x)
+    out[:, 1] += amp * h * np.sin(2 * math.pi * x) * np.sin(math.pi * y)
+    return out
+
+
+def node_coords(nx: int, ny: int, xy):
+    """Coordinates (2, N_n) of the CG2 nodes of a mesh with vertices xy: images
+    of the reference nodes under each element's bilinear map (vertex nodes,
+    edge midpoints, element centres)."""
+    v = np.asarray(xy, dtype=np.float64).reshape(ny + 1, nx + 1, 2)
+    out = np.zeros((2 * ny + 1, 2 * nx + 1, 2))
+    out[0::2, 0::2] = v
+    out[0::2, 1::2] = 0.5 * (v[:, :-1] + v[:, 1:])
+    out[1::2, 0::2] = 0.5 * (v[:-1, :] + v[1:, :])
+    out[1::2, 1::2] = 0.25 * (v[:-1, :-1] + v[:-1, 1:] + v[1:, :-1] + v[1:, 1:])
+    return out.reshape(-1, 2).T.copy()

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2402_00466_gb300 import mevp
+from paper_2402_00466_gb300 import workloads as W
 from paper_2402_00466_gb300 import build as B
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
@@ -48,18 +49,33 @@ def test_mesh_create_validation():
     assert e.value.code == -1 and "nx" in str(e.value)
     with pytest.raises(mevp.MevpError):
         mevp.mevp_mesh_create(4, 4, -1.0, 1.0)
-    # non-rectilinear vertices are valid input this build does not handle
     xy = np.zeros((9, 2))
     for j in range(3):
         for i in range(3):
             xy[j * 3 + i] = (i * 1.0, j * 1.0)
-    xy[4, 0] += 0.1
-    with pytest.raises(mevp.MevpError) as e:
-        mevp.mevp_mesh_create(2, 2, 0, 0, xy)
-    assert e.value.code == -7
-    xy[4, 0] -= 0.1
-    m = mevp.mevp_mesh_create(2, 2, 0, 0, xy)
+    m = mevp.mevp_mesh_create(2, 2, 0, 0, xy)  # rectilinear
     mevp.mevp_mesh_destroy(m)
+    # a general (non-rectilinear) mesh of convex counter-clockwise quads
+    g = xy.copy()
+    g[4] += (0.2, -0.1)
+    m = mevp.mevp_mesh_create(2, 2, 0, 0, g)
+    mevp.mevp_mesh_destroy(m)
+    # the centre vertex moved past a corner diagonal: a non-convex element
+    bad = xy.copy()
+    bad[4] = (1.9, 1.9)
+    with pytest.raises(mevp.MevpError) as e:
+        mevp.mevp_mesh_create(2, 2, 0, 0, bad)
+    assert e.value.code == -1 and "convex" in str(e.value)
+    # clockwise vertex order (mirrored mesh) is rejected too
+    mir = xy.copy()
+    mir[:, 0] *= -1.0
+    with pytest.raises(mevp.MevpError) as e:
+        mevp.mevp_mesh_create(2, 2, 0, 0, mir)
+    assert e.value.code == -1
+    nan = g.copy()
+    nan[3, 1] = np.nan
+    with pytest.raises(mevp.MevpError):
+        mevp.mevp_mesh_create(2, 2, 0, 0, nan)
     mevp.mevp_mesh_destroy(None)  # destroying NULL is a no-op
 
 
@@ -68,8 +84,10 @@ def test_workspace_bytes_validation():
     try:
         b3 = mevp.mevp_state_workspace_bytes(m, 3, 1, 0)
         b6 = mevp.mevp_state_workspace_bytes(m, 6, 1, 0)
-        assert b6 > b3 > 0 and b6 % 256 == 0
-        for bad in (1, 2, 4, 8):
+        b8 = mevp.mevp_state_workspace_bytes(m, 8, 1, 0)
+        assert b8 > b6 > b3 > 0 and b6 % 256 == 0
+        assert mevp.mevp_state_workspace_bytes(m, 8, 1, 1) > b8  # mixed adds FP32 copies
+        for bad in (1, 2, 4, 7):
             with pytest.raises(mevp.MevpError):
                 mevp.mevp_state_workspace_bytes(m, bad, 1, 0)
         with pytest.raises(mevp.MevpError) as e:
@@ -79,6 +97,23 @@ def test_workspace_bytes_validation():
             mevp.mevp_state_workspace_bytes(m, 6, 1, 5)
     finally:
         mevp.mevp_mesh_destroy(m)
+
+
+def test_general_mesh_workspace_and_precision():
+    """A general mesh keeps its vertices on the device (more workspace than the
+    rectilinear mesh of the same size) and runs in FP64 only."""
+    xy = W.perturbed_vertices(6, 5, 3)
+    g = mevp.mevp_mesh_create(6, 5, 0, 0, xy)
+    r = mevp.mevp_mesh_create(6, 5, 1e3, 1e3)
+    try:
+        assert (mevp.mevp_state_workspace_bytes(g, 6, 1, 0)
+                > mevp.mevp_state_workspace_bytes(r, 6, 1, 0))
+        with pytest.raises(mevp.MevpError) as e:
+            mevp.mevp_state_workspace_bytes(g, 6, 1, 1)
+        assert e.value.code == -7 and "FP64" in str(e.value)
+    finally:
+        mevp.mevp_mesh_destroy(g)
+        mevp.mevp_mesh_destroy(r)
 
 
 def test_null_state_calls_fail_cleanly():
