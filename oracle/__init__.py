@@ -81,6 +81,8 @@ def _lib(openmp: bool = False):
             lib.orc_velocity.argtypes = [i, i, pp, dp, dp, dp, dp, dp, dp, dp, dp]
             lib.orc_element_map.argtypes = [i, i, dp, i, i, dp, dp]
             lib.orc_max_threads.argtypes = []
+            lib.orc_advect.argtypes = [i, i, dp, i, dp, ctypes.c_double, i, dp, dp]
+            lib.orc_advect_operator.argtypes = [i, i, dp, i, dp, dp, dp, dp, dp]
             _handles[openmp] = lib
         return _handles[openmp]
 
@@ -234,3 +236,24 @@ def subcycles(nx, ny, xy, n_s, n_a, params, H, A, tau, vel0, S0, n_sub, vn=None,
 
 def max_threads(openmp=True):
     return _lib(openmp).orc_max_threads()
+
+
+def advect(nx, ny, xy, n_a, vel, dt, n_steps, H, A, openmp=False):
+    """n_steps DG upwind advection steps of H and A (n_a, N_e) with the CG2
+    velocity vel (2, N_n) held fixed; returns (H, A)."""
+    ne, nn = sizes(nx, ny)
+    Hc, Ac = _adv_in(H, n_a, ne).copy(), _adv_in(A, n_a, ne).copy()
+    _check(_lib(openmp).orc_advect(nx, ny, _p(_c(xy)), n_a, _p(_c(vel).reshape(-1)), float(dt),
+                                   int(n_steps), _p(Hc), _p(Ac)), "advect")
+    return np.ascontiguousarray(Hc.T), np.ascontiguousarray(Ac.T)
+
+
+def advect_operator(nx, ny, xy, n_a, vel, H, A):
+    """The semi-discrete operator L = M^-1 R applied to (H, A); (n_a, N_e) each."""
+    ne, nn = sizes(nx, ny)
+    LH = np.zeros(ne * n_a); LA = np.zeros(ne * n_a)
+    _check(_lib().orc_advect_operator(nx, ny, _p(_c(xy)), n_a, _p(_c(vel).reshape(-1)),
+                                      _p(_adv_in(H, n_a, ne)), _p(_adv_in(A, n_a, ne)),
+                                      _p(LH), _p(LA)), "advect_operator")
+    return (np.ascontiguousarray(LH.reshape(ne, n_a).T),
+            np.ascontiguousarray(LA.reshape(ne, n_a).T))

@@ -666,3 +666,238 @@ int orc_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------
+ * Advection of H and A (the transport equations of Sec. 2, Eq. si:ad, with
+ * zero sources), discretised as Sec. 2.1 states: discontinuous Galerkin in
+ * space with the standard upwind flux, explicit Runge-Kutta in time.  The
+ * paper names no flux details, quadrature or scheme order; this follows the
+ * readings recorded in the design notes:
+ *   - semi-discrete form on element K, test function psi_i of the n_a-dof
+ *     DG space (same basis as the stress, first n_a functions):
+ *       M_K dH/dt = int_K H v . grad psi_i  -  int_dK Hhat (v.n) psi_i
+ *     with Hhat the trace from the element the flow leaves (upwind, chosen
+ *     pointwise at each edge quadrature point); on the domain boundary the
+ *     element's own trace is used both ways;
+ *   - v is the CG2 velocity, held fixed over the step;
+ *   - the integrals are written on the reference square with the
+ *     contravariant velocity  vt = detJ J^-1 v  (vt_xi = J11 v_x - J01 v_y,
+ *     vt_eta = -J10 v_x + J00 v_y), so that  int_K H v.grad psi =
+ *     int_ref H (vt_xi dpsi/dxi + vt_eta dpsi/deta)  and the outward flux
+ *     density per unit reference edge length is +-vt_xi on the east/west
+ *     edges and +-vt_eta on the north/south edges;
+ *   - quadrature: NQ x NQ Gauss points in the element and NQ on each edge,
+ *     NQ = 3 for n_a = 1 or 3 and 4 for n_a = 6 (exact for every polynomial
+ *     integrand of a bilinear element when the upwind side does not change
+ *     along an edge);
+ *   - time stepping by the strong-stability-preserving Runge-Kutta scheme of
+ *     order n+1 for DG degree n: forward Euler (DG0), Heun's two-stage
+ *     scheme (DG1), the Shu-Osher three-stage scheme (DG2).
+ * H, A layout here: [N_e][n_a] (element-major, as in Listing 1).
+ * ---------------------------------------------------------------------- */
+static int adv_nq(int n_a) { return n_a == 6 ? 4 : 3; }
+
+typedef struct {
+  int nx, ny, n_a, nq;
+  const double *xy;
+  double qx[4], qw[4];
+} adv_t;
+
+/* Jacobian of element K at reference point (xi, eta). */
+static void adv_jac(const adv_t *P, int K, double xi, double eta, double J[4]) {
+  int kx = K % P->nx, ky = K / P->nx, vw = P->nx + 1;
+  const double *x00 = P->xy + 2 * (ky * vw + kx);
+  const double *x10 = P->xy + 2 * (ky * vw + kx + 1);
+  const double *x01 = P->xy + 2 * ((ky + 1) * vw + kx);
+  const double *x11 = P->xy + 2 * ((ky + 1) * vw + kx + 1);
+  for (int c = 0; c < 2; ++c) {
+    J[2 * c + 0] = (1.0 - eta) * (x10[c] - x00[c]) + eta * (x11[c] - x01[c]); /* d(x_c)/dxi  */
+    J[2 * c + 1] = (1.0 - xi) * (x01[c] - x00[c]) + xi * (x11[c] - x10[c]);   /* d(x_c)/deta */
+  }
+}
+
+/* CG2 velocity of element K at reference point (xi, eta). */
+static void adv_vel(const adv_t *P, const double *vel, int K, double xi, double eta,
+                    double *vx, double *vy) {
+  int kx = K % P->nx, ky = K / P->nx, nw = 2 * P->nx + 1;
+  size_t nn = (size_t)nw * (2 * P->ny + 1);
+  double phi[9];
+  orc_q2_basis(xi, eta, phi, NULL, NULL);
+  double ax = 0.0, ay = 0.0;
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      size_t node = (size_t)(2 * ky + b) * nw + 2 * kx + a;
+      ax += phi[a + 3 * b] * vel[node];
+      ay += phi[a + 3 * b] * vel[nn + node];
+    }
+  *vx = ax;
+  *vy = ay;
+}
+
+/* Value of the DG field F (coefficients of element K) at (xi, eta). */
+static double adv_eval(const adv_t *P, const double *F, int K, double xi, double eta) {
+  double psi[MAXS];
+  orc_dg_basis(P->n_a, xi, eta, psi);
+  double s = 0.0;
+  for (int i = 0; i < P->n_a; ++i) s += F[(size_t)K * P->n_a + i] * psi[i];
+  return s;
+}
+
+/* Reference gradient of DG basis function i at (xi, eta), by the product
+ * rule on the Legendre factors of orc_dg_basis. */
+static void adv_dpsi(int n_a, double xi, double eta, double *dxi, double *deta) {
+  double xh = xi - 0.5, eh = eta - 0.5;
+  double px[3] = {1.0, xh, xh * xh - 1.0 / 12.0}, dpx[3] = {0.0, 1.0, 2.0 * xh};
+  double py[3] = {1.0, eh, eh * eh - 1.0 / 12.0}, dpy[3] = {0.0, 1.0, 2.0 * eh};
+  static const int kxs[8] = {0, 1, 0, 2, 1, 0, 2, 1}, kys[8] = {0, 0, 1, 0, 1, 2, 1, 2};
+  for (int i = 0; i < n_a; ++i) {
+    dxi[i] = dpx[kxs[i]] * py[kys[i]];
+    deta[i] = px[kxs[i]] * dpy[kys[i]];
+  }
+}
+
+/* L(F) = M^-1 R(F) for both fields F = H, A (same velocity, same upwind
+ * decisions); out_H, out_A [N_e][n_a]. */
+static int adv_operator(const adv_t *P, const double *vel, const double *H, const double *A,
+                        double *out_H, double *out_A) {
+  int ne = P->nx * P->ny, n_a = P->n_a, nq = P->nq;
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int K = 0; K < ne; ++K) {
+    int kx = K % P->nx, ky = K / P->nx;
+    double RH[MAXS] = {0}, RA[MAXS] = {0}, mass[MAXS * MAXS] = {0};
+    /* volume terms and the local mass matrix */
+    for (int gy = 0; gy < nq; ++gy)
+      for (int gx = 0; gx < nq; ++gx) {
+        double xi = P->qx[gx], eta = P->qx[gy], w = P->qw[gx] * P->qw[gy];
+        double J[4];
+        adv_jac(P, K, xi, eta, J);
+        double det = J[0] * J[3] - J[1] * J[2];
+        if (!(det > 0.0)) bad |= 1;
+        double vx, vy;
+        adv_vel(P, vel, K, xi, eta, &vx, &vy);
+        double vt_xi = J[3] * vx - J[1] * vy, vt_eta = -J[2] * vx + J[0] * vy;
+        double h = adv_eval(P, H, K, xi, eta), a = adv_eval(P, A, K, xi, eta);
+        double psi[MAXS], dxi[MAXS], deta[MAXS];
+        orc_dg_basis(n_a, xi, eta, psi);
+        adv_dpsi(n_a, xi, eta, dxi, deta);
+        for (int i = 0; i < n_a; ++i) {
+          double g = vt_xi * dxi[i] + vt_eta * deta[i];
+          RH[i] += w * h * g;
+          RA[i] += w * a * g;
+          for (int j = 0; j < n_a; ++j) mass[i * n_a + j] += w * det * psi[i] * psi[j];
+        }
+      }
+    /* edges: 0 west (xi=0), 1 east (xi=1), 2 south (eta=0), 3 north (eta=1) */
+    for (int e = 0; e < 4; ++e) {
+      int nb;
+      if (e == 0) nb = kx > 0 ? K - 1 : -1;
+      else if (e == 1) nb = kx < P->nx - 1 ? K + 1 : -1;
+      else if (e == 2) nb = ky > 0 ? K - P->nx : -1;
+      else nb = ky < P->ny - 1 ? K + P->nx : -1;
+      for (int q = 0; q < nq; ++q) {
+        double t = P->qx[q], w = P->qw[q];
+        double xi, eta, nxi, neta; /* own and neighbour reference coordinates */
+        if (e == 0) { xi = 0.0; eta = t; nxi = 1.0; neta = t; }
+        else if (e == 1) { xi = 1.0; eta = t; nxi = 0.0; neta = t; }
+        else if (e == 2) { xi = t; eta = 0.0; nxi = t; neta = 1.0; }
+        else { xi = t; eta = 1.0; nxi = t; neta = 0.0; }
+        double J[4];
+        adv_jac(P, K, xi, eta, J);
+        double vx, vy;
+        adv_vel(P, vel, K, xi, eta, &vx, &vy);
+        double f; /* outward flux density per unit reference length */
+        if (e == 0) f = -(J[3] * vx - J[1] * vy);
+        else if (e == 1) f = J[3] * vx - J[1] * vy;
+        else if (e == 2) f = -(-J[2] * vx + J[0] * vy);
+        else f = -J[2] * vx + J[0] * vy;
+        double hh, ah;
+        if (f >= 0.0 || nb < 0) {
+          hh = adv_eval(P, H, K, xi, eta);
+          ah = adv_eval(P, A, K, xi, eta);
+        } else {
+          hh = adv_eval(P, H, nb, nxi, neta);
+          ah = adv_eval(P, A, nb, nxi, neta);
+        }
+        double psi[MAXS];
+        orc_dg_basis(n_a, xi, eta, psi);
+        for (int i = 0; i < n_a; ++i) {
+          RH[i] -= w * f * hh * psi[i];
+          RA[i] -= w * f * ah * psi[i];
+        }
+      }
+    }
+    if (invert_spd(n_a, mass) != ORC_OK) { bad |= 1; continue; }
+    for (int i = 0; i < n_a; ++i) {
+      double sh = 0.0, sa = 0.0;
+      for (int j = 0; j < n_a; ++j) {
+        sh += mass[i * n_a + j] * RH[j];
+        sa += mass[i * n_a + j] * RA[j];
+      }
+      out_H[(size_t)K * n_a + i] = sh;
+      out_A[(size_t)K * n_a + i] = sa;
+    }
+  }
+  return bad ? ORC_ERR_ARG : ORC_OK;
+}
+
+/* n_steps advection steps of length dt (SSP Runge-Kutta of order n_a's
+ * degree + 1), H and A [N_e][n_a] in/out, vel [2][N_n] fixed. */
+int orc_advect(int nx, int ny, const double *xy, int n_a, const double *vel, double dt,
+               int n_steps, double *H, double *A) {
+  if (nx < 1 || ny < 1 || !xy || !vel || !H || !A || n_steps < 0) return ORC_ERR_ARG;
+  if (!(n_a == 1 || n_a == 3 || n_a == 6)) return ORC_ERR_ARG;
+  adv_t P;
+  P.nx = nx; P.ny = ny; P.n_a = n_a; P.nq = adv_nq(n_a); P.xy = xy;
+  orc_gauss(P.nq, P.qx, P.qw);
+  size_t n = (size_t)nx * ny * n_a;
+  double *LH = (double *)malloc(sizeof(double) * n), *LA = (double *)malloc(sizeof(double) * n);
+  double *H1 = (double *)malloc(sizeof(double) * n), *A1 = (double *)malloc(sizeof(double) * n);
+  double *H2 = (double *)malloc(sizeof(double) * n), *A2 = (double *)malloc(sizeof(double) * n);
+  int rc = (LH && LA && H1 && A1 && H2 && A2) ? ORC_OK : ORC_ERR_OOM;
+  for (int it = 0; it < n_steps && rc == ORC_OK; ++it) {
+    /* stage 1: U1 = U + dt L(U) */
+    rc = adv_operator(&P, vel, H, A, LH, LA);
+    if (rc) break;
+    for (size_t k = 0; k < n; ++k) { H1[k] = H[k] + dt * LH[k]; A1[k] = A[k] + dt * LA[k]; }
+    if (n_a == 1) {
+      memcpy(H, H1, sizeof(double) * n);
+      memcpy(A, A1, sizeof(double) * n);
+      continue;
+    }
+    rc = adv_operator(&P, vel, H1, A1, LH, LA);
+    if (rc) break;
+    if (n_a == 3) {
+      /* Heun: U = U/2 + (U1 + dt L(U1))/2 */
+      for (size_t k = 0; k < n; ++k) {
+        H[k] = 0.5 * H[k] + 0.5 * (H1[k] + dt * LH[k]);
+        A[k] = 0.5 * A[k] + 0.5 * (A1[k] + dt * LA[k]);
+      }
+      continue;
+    }
+    /* Shu-Osher: U2 = 3U/4 + (U1 + dt L(U1))/4, U = U/3 + 2(U2 + dt L(U2))/3 */
+    for (size_t k = 0; k < n; ++k) {
+      H2[k] = 0.75 * H[k] + 0.25 * (H1[k] + dt * LH[k]);
+      A2[k] = 0.75 * A[k] + 0.25 * (A1[k] + dt * LA[k]);
+    }
+    rc = adv_operator(&P, vel, H2, A2, LH, LA);
+    if (rc) break;
+    for (size_t k = 0; k < n; ++k) {
+      H[k] = H[k] / 3.0 + 2.0 * (H2[k] + dt * LH[k]) / 3.0;
+      A[k] = A[k] / 3.0 + 2.0 * (A2[k] + dt * LA[k]) / 3.0;
+    }
+  }
+  free(LH); free(LA); free(H1); free(A1); free(H2); free(A2);
+  return rc;
+}
+
+/* The semi-discrete operator alone, L(H) = M^-1 R(H) (for the pins). */
+int orc_advect_operator(int nx, int ny, const double *xy, int n_a, const double *vel,
+                        const double *H, const double *A, double *LH, double *LA) {
+  if (nx < 1 || ny < 1 || !xy || !vel || !H || !A || !LH || !LA) return ORC_ERR_ARG;
+  if (!(n_a == 1 || n_a == 3 || n_a == 6)) return ORC_ERR_ARG;
+  adv_t P;
+  P.nx = nx; P.ny = ny; P.n_a = n_a; P.nq = adv_nq(n_a); P.xy = xy;
+  orc_gauss(P.nq, P.qx, P.qw);
+  return adv_operator(&P, vel, H, A, LH, LA);
+}

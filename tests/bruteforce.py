@@ -225,3 +225,135 @@ class Mesh:
             F = self.divergence(S)
             vel = self.velocity(F, vel, vn, tau, m, l, p)
         return vel, S, E
+
+
+# --------------------------------------------------------------------------
+# Advection (transport of H, A with the CG2 velocity), written independently
+# of the oracle: physical gradients through J^-T, physical outward normals of
+# the counter-clockwise element boundary (v.n ds = v_x dy - v_y dx), the
+# shifted-Legendre DG basis, and 10-point rules everywhere.
+# --------------------------------------------------------------------------
+def _q2_at(xi, eta):
+    phi, _, _ = q2(np.atleast_1d(xi), np.atleast_1d(eta))
+    return phi
+
+
+class Advection:
+    def __init__(self, nx, ny, xy, n_a, nq=10):
+        self.nx, self.ny, self.n_a = nx, ny, n_a
+        self.ne = nx * ny
+        self.nw = 2 * nx + 1
+        self.nn = self.nw * (2 * ny + 1)
+        self.xy = np.asarray(xy, dtype=np.float64).reshape(ny + 1, nx + 1, 2)
+        self.x1, self.w1 = gauss01(nq)
+        XI, ET = np.meshgrid(self.x1, self.x1)
+        self.vxi, self.veta, self.vw = XI.ravel(), ET.ravel(), np.outer(self.w1, self.w1).ravel()
+
+    def corners(self, K):
+        kx, ky = K % self.nx, K // self.nx
+        v = self.xy
+        return v[ky, kx], v[ky, kx + 1], v[ky + 1, kx], v[ky + 1, kx + 1]
+
+    def xmap(self, K, xi, eta):
+        x00, x10, x01, x11 = self.corners(K)
+        xi, eta = np.asarray(xi)[..., None], np.asarray(eta)[..., None]
+        return (x00 * (1 - xi) * (1 - eta) + x10 * xi * (1 - eta) + x01 * (1 - xi) * eta
+                + x11 * xi * eta)
+
+    def jac(self, K, xi, eta):
+        x00, x10, x01, x11 = self.corners(K)
+        xi, eta = np.asarray(xi)[..., None], np.asarray(eta)[..., None]
+        dxi = (x10 - x00) * (1 - eta) + (x11 - x01) * eta
+        deta = (x01 - x00) * (1 - xi) + (x11 - x10) * xi
+        return dxi, deta  # columns of J: d x/d xi, d x/d eta
+
+    def vel_at(self, vel, K, xi, eta):
+        kx, ky = K % self.nx, K // self.nx
+        nodes = np.array([(2 * ky + b) * self.nw + 2 * kx + a for b in range(3) for a in range(3)])
+        phi = _q2_at(xi, eta)  # (nq, 9)
+        return phi @ vel[0][nodes], phi @ vel[1][nodes]
+
+    def basis(self, xi, eta):
+        return dg_bf(self.n_a, np.asarray(xi), np.asarray(eta))
+
+    def dbasis(self, xi, eta, h=0.5):
+        # derivatives of the basis by central differences, exact for the
+        # degree <= 2 (per variable) polynomials of the advection space
+        xi, eta = np.asarray(xi), np.asarray(eta)
+        dx = (self.basis(xi + h, eta) - self.basis(xi - h, eta)) / (2 * h)
+        de = (self.basis(xi, eta + h) - self.basis(xi, eta - h)) / (2 * h)
+        return dx, de
+
+    def to_bf(self, F_doc):
+        """(n_a, N_e) documented coefficients -> (N_e, n_a) brute-force coefficients."""
+        xs = np.array([0.1, 0.35, 0.6, 0.9])
+        XI, ET = np.meshgrid(xs, xs)
+        pd = dg_documented(self.n_a, XI.ravel(), ET.ravel())
+        pb = self.basis(XI.ravel(), ET.ravel())
+        vals = pd @ F_doc  # (ns, N_e)
+        return np.linalg.lstsq(pb, vals, rcond=None)[0].T
+
+    def to_doc(self, F_bf):
+        xs = np.array([0.1, 0.35, 0.6, 0.9])
+        XI, ET = np.meshgrid(xs, xs)
+        pd = dg_documented(self.n_a, XI.ravel(), ET.ravel())
+        pb = self.basis(XI.ravel(), ET.ravel())
+        vals = pb @ F_bf.T
+        return np.linalg.lstsq(pd, vals, rcond=None)[0]
+
+    def operator(self, vel, F_doc):
+        """M^-1 R(F) in documented coefficients, (n_a, N_e)."""
+        F = self.to_bf(F_doc)
+        out = np.zeros_like(F)
+        for K in range(self.ne):
+            kx, ky = K % self.nx, K // self.nx
+            xi, eta, w = self.vxi, self.veta, self.vw
+            jx, je = self.jac(K, xi, eta)
+            det = jx[:, 0] * je[:, 1] - je[:, 0] * jx[:, 1]
+            vx, vy = self.vel_at(vel, K, xi, eta)
+            psi = self.basis(xi, eta)
+            dpx, dpe = self.dbasis(xi, eta)
+            # physical gradient: grad = J^-T (d/dxi, d/deta)
+            gx = (je[:, 1, None] * dpx - jx[:, 1, None] * dpe) / det[:, None]
+            gy = (-je[:, 0, None] * dpx + jx[:, 0, None] * dpe) / det[:, None]
+            h = psi @ F[K]
+            R = ((w * det * h)[:, None] * (vx[:, None] * gx + vy[:, None] * gy)).sum(0)
+            M = np.einsum("q,qi,qj->ij", w * det, psi, psi)
+            # counter-clockwise boundary: S (x00->x10), E (x10->x11), N (x11->x01), W (x01->x00)
+            t = self.x1
+            edges = [(t, 0 * t, lambda s: (s, 1.0), ky > 0, K - self.nx),                 # south
+                     (1 + 0 * t, t, lambda s: (0.0, s), kx < self.nx - 1, K + 1),       # east
+                     (1 - t, 1 + 0 * t, lambda s: (s, 0.0), ky < self.ny - 1, K + self.nx),  # north
+                     (0 * t, 1 - t, lambda s: (1.0, s), kx > 0, K - 1)]                 # west
+            for exi, eeta, nbmap, has_nb, nb in edges:
+                # tangent of the counter-clockwise traversal by the chain rule
+                jx, je = self.jac(K, exi, eeta)
+                dxi_dt = (exi[-1] - exi[0]) / (t[-1] - t[0])
+                deta_dt = (eeta[-1] - eeta[0]) / (t[-1] - t[0])
+                tx = jx[:, 0] * dxi_dt + je[:, 0] * deta_dt
+                ty = jx[:, 1] * dxi_dt + je[:, 1] * deta_dt
+                vx, vy = self.vel_at(vel, K, exi, eeta)
+                flux = vx * ty - vy * tx  # v.n ds/dt
+                own = self.basis(exi, eeta) @ F[K]
+                if has_nb:
+                    s = eeta if exi[0] == exi[-1] else exi
+                    nxi, neta = nbmap(s)
+                    nxi = np.broadcast_to(nxi, s.shape)
+                    neta = np.broadcast_to(neta, s.shape)
+                    other = self.basis(nxi, neta) @ F[nb]
+                else:
+                    other = own
+                hat = np.where(flux >= 0, own, other)
+                R -= ((self.w1 * flux * hat)[:, None] * self.basis(exi, eeta)).sum(0)
+            out[K] = np.linalg.solve(M, R)
+        return self.to_doc(out)
+
+    def integral(self, F_doc):
+        """sum_K int_K F dx."""
+        F = self.to_bf(F_doc)
+        tot = 0.0
+        for K in range(self.ne):
+            jx, je = self.jac(K, self.vxi, self.veta)
+            det = jx[:, 0] * je[:, 1] - je[:, 0] * jx[:, 1]
+            tot += (self.vw * det * (self.basis(self.vxi, self.veta) @ F[K])).sum()
+        return tot
