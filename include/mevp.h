@@ -172,6 +172,20 @@ MEVP_API int mevp_set_velocity(mevp_state *state, const double *uv, int on_devic
 /* Stress [3][n_stress][N_e]. */
 MEVP_API int mevp_set_stress(mevp_state *state, const double *S, int on_device);
 
+/* Advect H and A by n_steps >= 0 steps of length params.dt with the
+ * state's current velocity held fixed: the transport equations of Sec. 2
+ * (zero sources) discretised as Sec. 2.1 states, discontinuous Galerkin in
+ * the n_adv-dof space of H, A with the standard upwind flux (chosen pointwise
+ * at the edge quadrature points; on the domain boundary the element's own
+ * trace) and explicit Runge-Kutta in time: forward Euler for DG0, Heun's
+ * method for DG1, the three-stage Shu-Osher scheme for DG2.  Quadrature:
+ * 3 x 3 points per element and 3 per edge for DG0/DG1, 4 x 4 and 4 for DG2.
+ * No limiter: the clamps of the stress update (max(0,H), clamp(A,0,1))
+ * absorb undershoots.  Asynchronous on the state's stream; the new H, A
+ * take effect at the next mevp_begin_step.  MEVP_ERR_STATE without
+ * parameters. */
+MEVP_API int mevp_advect(mevp_state *state, int n_steps);
+
 /* Start an outer time step: v^n := current velocity, and recompute from H, A,
  * the forcing and the parameters the per-element ice strength
  * P = P* max(0,H) exp(-C (1 - clamp(A,0,1))) and the per-node constants of

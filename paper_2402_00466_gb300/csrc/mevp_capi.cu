@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, xy, lines, pstar, flags, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, xy, lines, pstar, flags, adv1, adv2, Pg, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -80,6 +80,9 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.lines = take(sizeof(double) * 2 * (m->nx + m->ny));
   L.pstar = take(sizeof(double) * ne);
   L.flags = take(sizeof(int) * 4);
+  L.adv1 = take(sizeof(double) * 2 * na * ne);
+  L.adv2 = take(na == 6 ? sizeof(double) * 2 * na * ne : 0);
+  L.Pg = take(na > 1 ? sizeof(double) * (ns == 3 ? 4 : 9) * ne : 0);
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(sizeof(double) * 3 * ns * ne);
@@ -272,7 +275,10 @@ int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, i
   if (!mesh || !bytes) return fail(MEVP_ERR_ARG, "workspace_bytes: NULL argument");
   if (n_stress != 3 && n_stress != 6 && n_stress != 8)
     return fail(MEVP_ERR_ARG, "n_stress=%d: DG stress needs 3, 6 or 8 dofs", n_stress);
-  if (n_adv != 1) return fail(MEVP_ERR_UNSUPPORTED, "n_adv=%d: this build handles DG0 (1)", n_adv);
+  if (n_adv != 1 && n_adv != 3 && n_adv != 6)
+    return fail(MEVP_ERR_ARG, "n_adv=%d: H, A need 1, 3 or 6 dofs (DG0, DG1, DG2)", n_adv);
+  if (n_adv != 1 && precision != MEVP_FP64)
+    return fail(MEVP_ERR_UNSUPPORTED, "n_adv=%d: DG1/DG2 ice fields run in FP64 only", n_adv);
   if (precision != MEVP_FP64 && precision != MEVP_MIXED)
     return fail(MEVP_ERR_ARG, "precision=%d unknown", precision);
   if (mesh->general && precision != MEVP_FP64)
@@ -330,12 +336,15 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.nh = 2 * mesh->ny + 1;
   d.nn = d.nw * d.nh;
   d.ns = n_stress;
+  d.na = n_adv;
   d.prec = precision;
   d.xline = (const double *)(b + L.xline);
   d.yline = (const double *)(b + L.yline);
   d.xy = mesh->general ? (const double2 *)(b + L.xy) : nullptr;
   d.lines = (double *)(b + L.lines);
   s->pstar_buf = (double *)(b + L.pstar);
+  s->adv1 = (double *)(b + L.adv1);
+  s->adv2 = (double *)(b + L.adv2);
   d.flags = (int *)(b + L.flags);
   d.pstar = nullptr;
   d.vel[0] = (double *)(b + L.vel0);
@@ -348,6 +357,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.tau = (double *)(b + L.tau);
   d.vo = (double *)(b + L.vo);
   d.Pe = (double *)(b + L.Pe);
+  d.Pg = (double *)(b + L.Pg);
   d.nodec = (double *)(b + L.nodec);
   d.mass = (double *)(b + L.mass);
   d.fbuf = (double *)(b + L.fbuf);
@@ -481,6 +491,20 @@ int mevp_set_stress(mevp_state *s, const double *S, int on_device) {
   if (rc || s->prec != MEVP_MIXED) return rc;
   cudaError_t e = mevp::launch_stress_to_f32(s->d, s->cur, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_stress convert");
+  return MEVP_OK;
+}
+
+int mevp_advect(mevp_state *s, int n_steps) {
+  int rc = check_state(s);
+  if (rc) return rc;
+  if (n_steps < 0) return fail(MEVP_ERR_ARG, "advect: n_steps=%d < 0", n_steps);
+  if (!s->have_params) return fail(MEVP_ERR_STATE, "advect: parameters not set");
+  if (n_steps == 0) return MEVP_OK;
+  cudaError_t e = cudaSuccess;
+  if (s->prec == MEVP_MIXED) e = mevp::launch_vel_join(s->d, s->cur, s->stream);
+  for (int k = 0; k < n_steps && e == cudaSuccess; ++k)
+    e = mevp::launch_advect_step(s->d, s->d.vel[s->cur], s->prm.dt, s->adv1, s->adv2, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "advect launch");
   return MEVP_OK;
 }
 
@@ -802,6 +826,7 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
   d.nh = 2 * ny + 1;
   d.nn = (int)nn;
   d.ns = n_stress;
+  d.na = 1;
   d.prec = MEVP_FP64;
   d.xline = xline;
   d.yline = yline;

@@ -119,11 +119,14 @@ __device__ __forceinline__ void gauss_eval(const T F[NS], T out[DgSpace<NS>::NGP
 }
 
 // Relaxed stress update from the strain invariants (coefficients) and the
-// element's ice strength: Ph = P/(2 alpha), fac = 1 - 1/alpha, ie = 1/e.
-template <int NS, typename T>
-__device__ __forceinline__ void relax_stress(T S11[NS], T S12[NS], T S22[NS], const T Pc[NS],
-                                             const T Qc[NS], const T Gc[NS], T Ph, T dmin2,
-                                             T fac, T ie) {
+// ice strength: Ph = P/(2 alpha) per element (DG0 H, A; VAR = false) or
+// Phg[g] per Gauss point (DG1/DG2 H, A; VAR = true), fac = 1 - 1/alpha,
+// ie = 1/e.  With a constant P the isotropic -P/2 term projects onto the
+// constant DG function alone; a varying one is projected with the rest.
+template <int NS, bool VAR, typename T>
+__device__ __forceinline__ void relax_stress_p(T S11[NS], T S12[NS], T S22[NS], const T Pc[NS],
+                                               const T Qc[NS], const T Gc[NS], T Ph,
+                                               const T *Phg, T dmin2, T fac, T ie) {
   constexpr int NG = DgSpace<NS>::NGP * DgSpace<NS>::NGP;
   T pgv[NG], qgv[NG], ggv[NG];
   gauss_eval<NS>(Pc, pgv);
@@ -135,8 +138,10 @@ __device__ __forceinline__ void relax_stress(T S11[NS], T S12[NS], T S22[NS], co
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     const T d2 = fma(ggv[g], ggv[g], fma(qgv[g], qgv[g], fma(pgv[g], pgv[g], dmin2)));
-    const T X = Ph * rsqrt_t(d2);
-    const T xp = X * pgv[g], xq = X * qgv[g], xg = X * ggv[g];
+    const T Pg = VAR ? Phg[g] : Ph;
+    const T X = Pg * rsqrt_t(d2);
+    const T xp = VAR ? fma(X, pgv[g], -Pg) : X * pgv[g];
+    const T xq = X * qgv[g], xg = X * ggv[g];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const double w = proj<NS>(s, g);
@@ -149,12 +154,19 @@ __device__ __forceinline__ void relax_stress(T S11[NS], T S12[NS], T S22[NS], co
   }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const T base = (s == 0) ? Ap[s] - Ph : Ap[s];
+    const T base = (!VAR && s == 0) ? Ap[s] - Ph : Ap[s];
     const T q = ie * AQ[s];
     S11[s] = fma(fac, S11[s], base + q);
     S22[s] = fma(fac, S22[s], base - q);
     S12[s] = fma(fac, S12[s], ie * AG[s]);
   }
+}
+
+template <int NS, typename T>
+__device__ __forceinline__ void relax_stress(T S11[NS], T S12[NS], T S22[NS], const T Pc[NS],
+                                             const T Qc[NS], const T Gc[NS], T Ph, T dmin2,
+                                             T fac, T ie) {
+  relax_stress_p<NS, false, T>(S11, S12, S22, Pc, Qc, Gc, Ph, nullptr, dmin2, fac, ie);
 }
 
 // Element forces f_j = -int sigma : grad phi_j on a rectangle hx x hy

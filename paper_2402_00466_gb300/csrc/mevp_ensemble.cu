@@ -262,6 +262,9 @@ int mevp_ensemble_create(mevp_state *const *members, int n, mevp_ensemble **out)
       return efail(MEVP_ERR_UNSUPPORTED,
                    "ensemble_create: member %d has a general mesh; ensembles take rectilinear "
                    "meshes", i);
+    if (members[i]->na != 1)
+      return efail(MEVP_ERR_UNSUPPORTED,
+                   "ensemble_create: member %d has DG1/DG2 ice fields; ensembles take DG0", i);
     if (members[i]->ns == 8)
       return efail(MEVP_ERR_UNSUPPORTED,
                    "ensemble_create: member %d has 8 stress dofs; ensembles take 3 or 6", i);

@@ -52,7 +52,7 @@ __device__ __forceinline__ void strain_dg(const double u[9], const double v[9], 
 
 // One element of the FP64 subcycle (strain, stress update in place, element
 // forces into the force buffer).
-template <int NS>
+template <int NS, bool VAR = false>
 __device__ __forceinline__ void elem_f64(const DevState &d, const Rheo &r, int cur, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
   const double hx = __ldg(d.lines + kx), ihx = __ldg(d.lines + d.nx + kx);
@@ -69,8 +69,16 @@ __device__ __forceinline__ void elem_f64(const DevState &d, const Rheo &r, int c
     S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
     S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
   }
-  const double Ph = __ldg(d.Pe + K) * r.hainv;
-  relax_stress<NS>(S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
+  if constexpr (VAR) {  // DG1/DG2 H, A: ice strength per Gauss point
+    constexpr int NG = DgSpace<NS>::NGP * DgSpace<NS>::NGP;
+    double Phg[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) Phg[g] = __ldg(d.Pg + (size_t)g * d.ne + K) * r.hainv;
+    relax_stress_p<NS, true>(S11, S12, S22, Pc, Qc, Gc, 0.0, Phg, r.dmin2, r.fac, r.ie);
+  } else {
+    const double Ph = __ldg(d.Pe + K) * r.hainv;
+    relax_stress<NS>(S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
+  }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     d.S[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
@@ -86,10 +94,10 @@ __device__ __forceinline__ void elem_f64(const DevState &d, const Rheo &r, int c
   }
 }
 
-template <int NS>
+template <int NS, bool VAR = false>
 __global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, int cur) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K < d.ne) elem_f64<NS>(d, r, cur, K);
+  if (K < d.ne) elem_f64<NS, VAR>(d, r, cur, K);
 }
 
 // Sum of the element forces at node (ix, iy) over the elements that contain
@@ -262,6 +270,57 @@ __global__ void k_strength(DevState d, double Pstar, double C) {
   d.Pe[K] = (d.pstar ? d.pstar[K] : Pstar) * h * exp(-C * (1.0 - a));
 }
 
+// Value at 2-D Gauss point (gx, gy) of the N-point rule of the DG1/DG2 field
+// F ([na][ne]) of element K.
+template <int N>
+__device__ __forceinline__ double dg_at_gauss(const double *F, int na, size_t ne, int K, int gx,
+                                              int gy) {
+  double v = 0.0;
+  for (int i = 0; i < na; ++i) v = fma(F[(size_t)i * ne + K], pg<N>(dgx(i), gx) * pg<N>(dgy(i), gy), v);
+  return v;
+}
+
+// DG1/DG2 H, A: the ice strength P = P* max(0,H) exp(-C(1 - clamp(A,0,1)))
+// at each Gauss point of the stress rule (Listing 1 evaluates H, A there).
+template <int N>
+__global__ void k_strength_gauss(DevState d, double Pstar, double C) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const double ps = d.pstar ? d.pstar[K] : Pstar;
+  for (int gy = 0; gy < N; ++gy)
+    for (int gx = 0; gx < N; ++gx) {
+      const double h = fmax(0.0, dg_at_gauss<N>(d.H, d.na, d.ne, K, gx, gy));
+      const double a = fmin(1.0, fmax(0.0, dg_at_gauss<N>(d.A, d.na, d.ne, K, gx, gy)));
+      d.Pg[(size_t)(gx + N * gy) * d.ne + K] = ps * h * exp(-C * (1.0 - a));
+    }
+}
+
+// int_K max(0, H) phi_j for DG1/DG2 H with the N-point rule of the stress
+// space, phi_j the Q2 function of local node (a, b).
+template <int N>
+__device__ __forceinline__ double mass_integral_gauss(const DevState &d, int kx, int ky, int a,
+                                                      int b) {
+  const int K = ky * d.nx + kx;
+  QuadMap m;
+  if (d.xy) {
+    m = quad_map(d.xy, d.nx, kx, ky);
+  } else {
+    m.Ax = d.xline[kx + 1] - d.xline[kx];
+    m.By = d.yline[ky + 1] - d.yline[ky];
+    m.Ay = m.Bx = m.cx = m.cy = 0.0;
+  }
+  const double d0 = m.d0(), d1 = m.d1(), d2 = m.d2();
+  double acc = 0.0;
+  for (int gy = 0; gy < N; ++gy)
+    for (int gx = 0; gx < N; ++gx) {
+      const double det = fma(d1, Gauss<N>::xh(gx), fma(d2, Gauss<N>::xh(gy), d0));
+      const double h = fmax(0.0, dg_at_gauss<N>(d.H, d.na, d.ne, K, gx, gy));
+      const double w = Gauss<N>::w(gx) * Gauss<N>::w(gy) * det;
+      acc = fma(w * h, lq<N>(a, gx) * lq<N>(b, gy), acc);
+    }
+  return acc;
+}
+
 // Lumped mass m_j = rho_ice sum_K max(0,H_K) int_K phi_j and area
 // l_j = sum_K int_K phi_j (hx hy w_a w_b on a rectangle, w = 1/6, 2/3, 1/6;
 // the exact integral against the affine det J on a general element), then the
@@ -285,7 +344,12 @@ __global__ void k_node_constants(DevState d, int cur, mevp_params p, int has_vo)
         w = area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
       }
       l += w;
-      mh += fmax(0.0, d.H[ky * d.nx + kx]) * w;
+      if (d.na == 1)
+        mh += fmax(0.0, d.H[ky * d.nx + kx]) * w;
+      else if (d.ns == 3)
+        mh += mass_integral_gauss<2>(d, kx, ky, ix - 2 * kx, iy - 2 * ky);
+      else
+        mh += mass_integral_gauss<3>(d, kx, ky, ix - 2 * kx, iy - 2 * ky);
     }
   }
   const double m = p.rho_ice * mh;
@@ -386,7 +450,12 @@ cudaError_t launch_nan_check(const DevState &d, int cur, cudaStream_t st) {
 cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                            cudaStream_t st) {
   if (!d.xy) k_mesh_lines<<<blocks(d.nx + d.ny, 256), 256, 0, st>>>(d);
-  k_strength<<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
+  if (d.na == 1)
+    k_strength<<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
+  else if (d.ns == 3)
+    k_strength_gauss<2><<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
+  else
+    k_strength_gauss<3><<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
   k_node_constants<<<blocks(d.nn, 256), 256, 0, st>>>(d, cur, p, has_vo ? 1 : 0);
   return cudaGetLastError();
 }
@@ -394,14 +463,24 @@ cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo,
 cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
                                 cudaStream_t st, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[0], st);
+  const int eg = blocks(d.ne, kElemBlock);
   if (d.xy)
     launch_element_general(d, r, cur, st);
-  else if (d.ns == 3)
-    k_element_f64<3><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
-  else if (d.ns == 6)
-    k_element_f64<6><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
-  else
-    k_element_f64<8><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, r, cur);
+  else if (d.na == 1) {
+    if (d.ns == 3)
+      k_element_f64<3><<<eg, kElemBlock, 0, st>>>(d, r, cur);
+    else if (d.ns == 6)
+      k_element_f64<6><<<eg, kElemBlock, 0, st>>>(d, r, cur);
+    else
+      k_element_f64<8><<<eg, kElemBlock, 0, st>>>(d, r, cur);
+  } else {
+    if (d.ns == 3)
+      k_element_f64<3, true><<<eg, kElemBlock, 0, st>>>(d, r, cur);
+    else if (d.ns == 6)
+      k_element_f64<6, true><<<eg, kElemBlock, 0, st>>>(d, r, cur);
+    else
+      k_element_f64<8, true><<<eg, kElemBlock, 0, st>>>(d, r, cur);
+  }
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
   k_node_f64<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, cur, has_vo ? 1 : 0);

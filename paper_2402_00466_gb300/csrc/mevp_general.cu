@@ -16,7 +16,7 @@ namespace {
 
 constexpr int kGenBlock = 128;
 
-template <int NS>
+template <int NS, bool VAR>
 __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int cur, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
   const QuadMap m = quad_map(d.xy, d.nx, kx, ky);
@@ -43,8 +43,16 @@ __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int c
     S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
     S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
   }
-  const double Ph = __ldg(d.Pe + K) * r.hainv;
-  relax_general<NS>(m, F, S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
+  if constexpr (VAR) {  // DG1/DG2 H, A: ice strength per Gauss point
+    constexpr int NG = DgSpace<NS>::NGP * DgSpace<NS>::NGP;
+    double Phg[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) Phg[g] = __ldg(d.Pg + (size_t)g * d.ne + K) * r.hainv;
+    relax_general<NS, true>(m, F, S11, S12, S22, Pc, Qc, Gc, 0.0, r.dmin2, r.fac, r.ie, Phg);
+  } else {
+    const double Ph = __ldg(d.Pe + K) * r.hainv;
+    relax_general<NS>(m, F, S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
+  }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     d.S[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
@@ -60,10 +68,10 @@ __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int c
   }
 }
 
-template <int NS>
+template <int NS, bool VAR>
 __global__ void __launch_bounds__(kGenBlock) k_element_gen(DevState d, Rheo r, int cur) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K < d.ne) elem_gen<NS>(d, r, cur, K);
+  if (K < d.ne) elem_gen<NS, VAR>(d, r, cur, K);
 }
 
 // Strain coefficients E11, E12, E22 of the current velocity (read-back).
@@ -117,12 +125,16 @@ inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
 cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
   const int g = blocks(d.ne, kGenBlock);
+  const bool var = d.na > 1;
   if (d.ns == 3)
-    k_element_gen<3><<<g, kGenBlock, 0, st>>>(d, r, cur);
+    var ? k_element_gen<3, true><<<g, kGenBlock, 0, st>>>(d, r, cur)
+        : k_element_gen<3, false><<<g, kGenBlock, 0, st>>>(d, r, cur);
   else if (d.ns == 6)
-    k_element_gen<6><<<g, kGenBlock, 0, st>>>(d, r, cur);
+    var ? k_element_gen<6, true><<<g, kGenBlock, 0, st>>>(d, r, cur)
+        : k_element_gen<6, false><<<g, kGenBlock, 0, st>>>(d, r, cur);
   else
-    k_element_gen<8><<<g, kGenBlock, 0, st>>>(d, r, cur);
+    var ? k_element_gen<8, true><<<g, kGenBlock, 0, st>>>(d, r, cur)
+        : k_element_gen<8, false><<<g, kGenBlock, 0, st>>>(d, r, cur);
   return cudaGetLastError();
 }
 

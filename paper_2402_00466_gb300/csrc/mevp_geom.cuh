@@ -239,12 +239,15 @@ __device__ __forceinline__ void strain_general(const QuadMap &m, const MassFacto
 // Relaxed stress update on a general element from the strain coefficients:
 // S <- fac S + M^-1 int psi detJ (X (p +- Q/e), X G/e) - Ph e_0, with
 // X = Ph / sqrt(Delta^2), Ph = P/(2 alpha) (invariant form of Listing 1).
-template <int NS>
+// VAR: per-Gauss-point strength Phg (DG1/DG2 H, A), whose -P/2 term is
+// projected with the rest; otherwise the element constant Ph.
+template <int NS, bool VAR = false>
 __device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor<NS> &F,
                                               double S11[NS], double S12[NS], double S22[NS],
                                               const double Pc[NS], const double Qc[NS],
                                               const double Gc[NS], double Ph, double dmin2,
-                                              double fac, double ie) {
+                                              double fac, double ie,
+                                              const double *Phg = nullptr) {
   constexpr int N = DgSpace<NS>::NGP, NG = N * N;
   double RP[NS], RQ[NS], RG[NS];
   {
@@ -261,8 +264,9 @@ __device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor
         jac_at<N>(m, gx, gy, j00, j01, j10, j11);
         const double det = fma(j00, j11, -(j01 * j10));
         const double d2 = fma(ggv[g], ggv[g], fma(qgv[g], qgv[g], fma(pgv[g], pgv[g], dmin2)));
-        const double Xd = Ph * rsqrt(d2) * det;
-        pgv[g] *= Xd;
+        const double Pg = VAR ? Phg[g] : Ph;
+        const double Xd = Pg * rsqrt(d2) * det;
+        pgv[g] = VAR ? fma(Xd, pgv[g], -(Pg * det)) : pgv[g] * Xd;
         qgv[g] *= Xd;
         ggv[g] *= Xd;
       }
@@ -275,7 +279,7 @@ __device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor
   mass_solve<NS>(F, RG);
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const double base = (s == 0) ? RP[s] - Ph : RP[s];
+    const double base = (!VAR && s == 0) ? RP[s] - Ph : RP[s];
     const double q = ie * RQ[s];
     S11[s] = fma(fac, S11[s], base + q);
     S22[s] = fma(fac, S22[s], base - q);

@@ -55,6 +55,7 @@ inline Rheo make_rheo(const mevp_params &p) {
 // Device view of a state (all pointers into the workspace).
 struct DevState {
   int nx, ny, ne, nw, nh, nn, ns, prec;
+  int na;              // DG dofs of H and A per element (1, 3 or 6)
   const double *xline, *yline;
   const double2 *xy;   // general mesh: [(nx+1)(ny+1)] vertices; NULL on rectilinear meshes
   double *lines;       // [hx: nx][1/hx: nx][hy: ny][1/hy: ny], from the mesh lines
@@ -64,7 +65,8 @@ struct DevState {
   double *H, *A;       // [ne]
   double *tau;         // [2][nn]
   double *vo;          // [2][nn]
-  double *Pe;          // [ne] ice strength per element
+  double *Pe;          // [ne] ice strength per element (DG0 H, A)
+  double *Pg;          // [NGP^2][ne] ice strength per Gauss point (DG1/DG2 H, A)
   const double *pstar; // [ne] per-element P* field, or NULL (params.Pstar everywhere)
   double *nodec;       // [6][nn] cA, cB, cK, qx, qy, cD
   double *mass;        // [nn]
@@ -143,6 +145,10 @@ cudaError_t launch_vel_join(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_stress_to_f32(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_stress_to_f64(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_diag(const DevState &d, cudaStream_t st);
+// One advection step of H and A (in place) with the FP64 velocity vel;
+// T1, T2: scratch of 2 n_a N_e doubles each (T2 used for n_a = 6 only).
+cudaError_t launch_advect_step(const DevState &d, const double *vel, double dt, double *T1,
+                               double *T2, cudaStream_t st);
 // sets flags[0] when the current velocity holds a non-finite value
 cudaError_t launch_nan_check(const DevState &d, int cur, cudaStream_t st);
 
@@ -172,6 +178,7 @@ struct mevp_state {
   bool has_pstar = false;  // per-element P* field set (mevp_set_strength_field)
   double *pstar_buf = nullptr;
   bool fused = true;  // mixed precision: one fused launch per subcycle
+  double *adv1 = nullptr, *adv2 = nullptr;  // advection stage buffers [2][na][ne]
   int nan_every = 0;         // watchdog interval in subcycles (0 = off)
   long long since_check = 0; // subcycles since the last watchdog scan
   bool use_graphs = true;  // replay captured subcycle chunks (non-default streams)

@@ -70,6 +70,7 @@ def load(build_if_stale: bool = True):
             "mevp_set_velocity": (i, [vp, vp, i]),
             "mevp_set_stress": (i, [vp, vp, i]),
             "mevp_begin_step": (i, [vp]),
+            "mevp_advect": (i, [vp, i]),
             "mevp_run_subcycles": (i, [vp, i]),
             "mevp_read_field": (i, [vp, i, vp, sz, i]),
             "mevp_sync": (i, [vp]),
@@ -207,6 +208,10 @@ def mevp_begin_step(state):
     _check(load().mevp_begin_step(state))
 
 
+def mevp_advect(state, n_steps: int = 1):
+    _check(load().mevp_advect(state, int(n_steps)))
+
+
 def mevp_run_subcycles(state, n: int):
     _check(load().mevp_run_subcycles(state, int(n)))
 
@@ -331,6 +336,7 @@ class State:
     def set_velocity(self, uv): mevp_set_velocity(self.state, uv)
     def set_stress(self, S): mevp_set_stress(self.state, S)
     def begin_step(self): mevp_begin_step(self.state)
+    def advect(self, n_steps=1): mevp_advect(self.state, n_steps)
     def run_subcycles(self, n): mevp_run_subcycles(self.state, n)
     def sync(self): mevp_sync(self.state)
     def set_strength_field(self, Pstar): mevp_set_strength_field(self.state, Pstar)

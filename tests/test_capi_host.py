@@ -90,9 +90,17 @@ def test_workspace_bytes_validation():
         for bad in (1, 2, 4, 7):
             with pytest.raises(mevp.MevpError):
                 mevp.mevp_state_workspace_bytes(m, bad, 1, 0)
+        # DG1/DG2 ice fields: FP64 only; their workspace holds the
+        # per-Gauss-point strength and the advection stage buffers
+        assert mevp.mevp_state_workspace_bytes(m, 6, 3, 0) > b6
+        assert mevp.mevp_state_workspace_bytes(m, 6, 6, 0) > mevp.mevp_state_workspace_bytes(m, 6, 3, 0)
         with pytest.raises(mevp.MevpError) as e:
-            mevp.mevp_state_workspace_bytes(m, 6, 3, 0)
+            mevp.mevp_state_workspace_bytes(m, 6, 3, 1)
         assert e.value.code == -7
+        for bad in (0, 2, 4):
+            with pytest.raises(mevp.MevpError) as e:
+                mevp.mevp_state_workspace_bytes(m, 6, bad, 0)
+            assert e.value.code == -1
         with pytest.raises(mevp.MevpError):
             mevp.mevp_state_workspace_bytes(m, 6, 1, 5)
     finally:
