@@ -29,7 +29,16 @@ namespace mevp {
 
 namespace {
 
-constexpr int kElemBlock = 128;
+// Element kernel block size and the minimum resident blocks per SM asked of
+// the compiler (which caps the registers per thread at
+// 65536 / (block * min blocks)).
+#ifndef MEVP_F64_ELEM_BLOCK
+#define MEVP_F64_ELEM_BLOCK 128
+#endif
+#ifndef MEVP_F64_ELEM_MIN_BLOCKS
+#define MEVP_F64_ELEM_MIN_BLOCKS 1
+#endif
+constexpr int kElemBlock = MEVP_F64_ELEM_BLOCK;
 constexpr int kNodeBlock = 256;
 
 // Strain coefficients E11, E12, E22 (for the diagnostic read-back):
@@ -95,7 +104,12 @@ __device__ __forceinline__ void elem_f64(const DevState &d, const Rheo &r, int c
 }
 
 template <int NS, bool VAR = false>
-__global__ void __launch_bounds__(kElemBlock) k_element_f64(DevState d, Rheo r, int cur) {
+#ifdef MEVP_F64_ELEM_MAXREG
+__global__ void __maxnreg__(MEVP_F64_ELEM_MAXREG)
+#else
+__global__ void __launch_bounds__(kElemBlock, MEVP_F64_ELEM_MIN_BLOCKS)
+#endif
+    k_element_f64(DevState d, Rheo r, int cur) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K < d.ne) elem_f64<NS, VAR>(d, r, cur, K);
 }
