@@ -195,12 +195,12 @@ def run_reference(a):
 
 
 # Mixed path, one fused launch per subcycle.  Algorithmic HBM bytes per
-# element-subcycle as SURVEY 8(d) counts them for a single pass (FP32 stress
+# element-subcycle of the workload's single-pass count (FP32 stress
 # R+W, FP32 H and A, vertices, 4 nodes x (FP64 v R + W, v^n R, tau R, m R)):
 # 424 B for DG2; the same count gives 352 B for DG1.  This design touches
 # fewer: FP32 stress R+W, FP32 ice strength, 4 nodes x (16 B velocity record
 # R + W, 16 B constant record R) = 340 B (DG2) / 268 B (DG1).
-MIXED_SURVEY_BYTES = {6: 424, 3: 352}
+MIXED_SINGLE_PASS_BYTES = {6: 424, 3: 352}
 MIXED_OWN_BYTES = {6: 144 + 4 + 4 * 48, 3: 72 + 4 + 4 * 48}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # per-kernel CUDA events on every 10th subcycle of the timed region (events
@@ -270,13 +270,13 @@ def roofline_for(precision, case, kt, total_ms, steps):
                      "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
                      "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak}, **common)
     # mixed: one fused launch per subcycle, HBM-bound
-    ach = MIXED_SURVEY_BYTES[ns] * ne / el_s / 1e9
+    ach = MIXED_SINGLE_PASS_BYTES[ns] * ne / el_s / 1e9
     own = MIXED_OWN_BYTES[ns] * ne / el_s / 1e9
     return dict({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                  "frac": ach / hbm_peak, "traffic": None, "kernel": f"k_subcycle_mix<{ns}>",
                  "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                 "bytes_per_element": MIXED_SURVEY_BYTES[ns],
-                 "bytes_source": "SURVEY 8(d) single-pass count",
+                 "bytes_per_element": MIXED_SINGLE_PASS_BYTES[ns],
+                 "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x (v R+W, v^n, tau, m)",
                  "own_bytes_per_element": MIXED_OWN_BYTES[ns],
                  "achieved_own_bytes": own, "frac_own_bytes": own / hbm_peak,
                  "fp32_TFLOPs_approx": (ELEM_FLOPS[ns] * 1.1 + 4 * 40) * ne / el_s / 1e12,
@@ -380,12 +380,12 @@ def run_ensemble(a, torch, dist, ws, rank):
     hbm_peak, hbm_kind = load_peaks()
     roofline = None
     if a.precision == "mixed":
-        byts = sum(c["nx"] * c["ny"] * MIXED_SURVEY_BYTES[c["n_s"]] for c in members)
+        byts = sum(c["nx"] * c["ny"] * MIXED_SINGLE_PASS_BYTES[c["n_s"]] for c in members)
         ach = byts / sub_s / 1e9
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                     "frac": ach / hbm_peak, "traffic": None,
                     "kernel": "k_ens_mix<%d,%d>" % shapes[shape],
-                    "bytes_per_element": "SURVEY 8(d): 424 (DG2) / 352 (DG1)",
+                    "bytes_per_element": "single-pass count: 424 (DG2) / 352 (DG1)",
                     "peak_kind": hbm_kind}
     else:
         flops = sum(c["nx"] * c["ny"] * ELEM_FLOPS[c["n_s"]] for c in members)
