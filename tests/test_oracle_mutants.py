@@ -45,6 +45,52 @@ MUTANTS = [
 ]
 
 
+# mistakes in the transport (advection) part, against its own pins
+ADVECTION_MUTANTS = [
+    ("volume term sign", "RH[i] += w * h * g;", "RH[i] -= w * h * g;"),
+    ("east flux sign", "else if (e == 1) f = J[3] * vx - J[1] * vy;",
+     "else if (e == 1) f = -(J[3] * vx - J[1] * vy);"),
+    ("downwind instead of upwind", "if (f >= 0.0 || nb < 0) {", "if (f < 0.0 || nb < 0) {"),
+    ("contravariant velocity transposed", "double vt_xi = J[3] * vx - J[1] * vy,",
+     "double vt_xi = J[3] * vx - J[2] * vy,"),
+    ("west neighbour trace on the wrong edge",
+     "if (e == 0) { xi = 0.0; eta = t; nxi = 1.0; neta = t; }",
+     "if (e == 0) { xi = 0.0; eta = t; nxi = 0.0; neta = t; }"),
+    ("Heun weights", "H[k] = 0.5 * H[k] + 0.5 * (H1[k] + dt * LH[k]);",
+     "H[k] = 0.25 * H[k] + 0.75 * (H1[k] + dt * LH[k]);"),
+    ("RK3 second stage weights", "H2[k] = 0.75 * H[k] + 0.25 * (H1[k] + dt * LH[k]);",
+     "H2[k] = 0.5 * H[k] + 0.5 * (H1[k] + dt * LH[k]);"),
+    ("mass matrix without det J", "mass[i * n_a + j] += w * det * psi[i] * psi[j];",
+     "mass[i * n_a + j] += w * psi[i] * psi[j];"),
+    ("product rule of the basis gradient", "deta[i] = px[kxs[i]] * dpy[kys[i]];",
+     "deta[i] = dpx[kxs[i]] * py[kys[i]];"),
+    ("edge weight dropped", "RH[i] -= w * f * hh * psi[i];", "RH[i] -= f * hh * psi[i];"),
+    ("DG2 rule too low", "static int adv_nq(int n_a) { return n_a == 6 ? 4 : 3; }",
+     "static int adv_nq(int n_a) { return n_a == 6 ? 3 : 3; }"),
+    ("Euler step sign", "H1[k] = H[k] + dt * LH[k];", "H1[k] = H[k] - dt * LH[k];"),
+]
+
+
+def _run_pins_against(src, tmp_path, pins):
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src)
+    so = tmp_path / "mutant.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                    "-D_POSIX_C_SOURCE=199309L", "-o", str(so), str(mut), "-lm"], check=True)
+    env = dict(os.environ, MEVP_ORACLE_LIB=str(so))
+    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins),
+                           "-x", "-q", "-p", "no:cacheprovider"], env=env, cwd=ROOT,
+                          capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.parametrize("name,old,new", ADVECTION_MUTANTS, ids=[m[0] for m in ADVECTION_MUTANTS])
+def test_advection_mutant_is_caught_by_the_pins(name, old, new, tmp_path):
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique/found: {name}"
+    r = _run_pins_against(src.replace(old, new), tmp_path, "test_oracle_advection_pins.py")
+    assert r.returncode != 0, f"mutant survived the pins: {name}\n{r.stdout[-2000:]}"
+
+
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_mutant_is_caught_by_the_pins(name, old, new, tmp_path):
     src = open(oracle._SRC).read()
