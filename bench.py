@@ -41,6 +41,29 @@ UNIT = "element-subcycles/s"
 # Gauss evaluation 132, rheology 99, projection 240, update 62, element
 # forces 254.  DG1: 153, 36, 44, 63, 32, 146.
 ELEM_FLOPS = {3: 474, 6: 1055}
+# The same count for the general-quad element kernel k_element_gen (bilinear
+# map and L D L^T of the local mass matrix per element, Gauss-point strain,
+# stress and forces with det J cancelled): DG2 = map 18, mass factor 147,
+# reference gradients 252, strain integrands 165, moments 195 + 195,
+# solves 198 + 198, invariants 24, Gauss evaluation 132 + 132, rheology 183,
+# update 61, force integrands 192, force sums 270.
+GEN_ELEM_FLOPS = {3: 1051, 6: 2362, 8: 2990}
+# Transport step (k_advect, rectilinear mesh), per element and Runge-Kutta
+# stage: volume terms at NQ x NQ points (velocity, contravariant flux,
+# traces, basis gradients), NQ points on each of the 4 edges (velocity,
+# normal flux, upwind trace, test functions), inverse mass, stage
+# combination.  Stages per step: 1 (DG0), 2 (DG1), 3 (DG2).
+ADV_FLOPS = {1: 195, 3: 885, 6: 2628}
+# Gradient of the kinetic energy (hand-written reverse mode), per element and
+# subcycle of the objective: the forward subcycle twice (checkpointed sweep and
+# the per-segment recomputation: element kernel + 4 nodes of the node kernel)
+# plus the reverse element kernel (forward recompute of strain and Gauss
+# values 189 / 400, transposed divergence, reverse rheology and projection,
+# transposed strain operator: 840 (DG1) / 1844 (DG2)) and 4 nodes of the
+# reverse node kernel (~47 flops: transposed 2x2 solve, drag derivative).
+ADJ_ELEM_FLOPS = {3: 840, 6: 1844}
+ADJ_NODE_FLOPS = 47
+ADV_STAGES = {1: 1, 3: 2, 6: 3}
 NODE_FLOPS_PER_NODE = 32.5          # node kernel (force gather, velocity update)
 # Algorithmic HBM bytes per element-subcycle: state touched once (stress R+W,
 # ice strength, vertices amortised, 4 nodes x (v R, v W, node constants R)).
@@ -160,6 +183,8 @@ def run_reference(a):
         return 0
     import oracle
     case = W.make_case(a.workload)
+    if case["n_sub"] == 0:
+        return run_reference_advection(a, case)
     ne = case["nx"] * case["ny"]
     args = (case["nx"], case["ny"], case["xy"], case["n_s"], 1, case["params"], case["H"],
             case["A"], case["tau"], case["vel0"], case["S0"])
@@ -189,6 +214,48 @@ def run_reference(a):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{k_sub} of {case['n_sub']} subcycles per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def advection_sample(case, nxs=128):
+    """A bounded CPU sample of a transport workload: the nxs x nxs corner of
+    its mesh, ice fields and a velocity of the same recipe."""
+    nx, ny, na = case["nx"], case["ny"], case["n_a"]
+    L = case["L"]
+    xs = W.uniform_vertices(nxs, nxs, L * nxs / nx, L * nxs / ny)
+    Hs = case["H"].reshape(na, ny, nx)[:, :nxs, :nxs].reshape(na, -1)
+    As = case["A"].reshape(na, ny, nx)[:, :nxs, :nxs].reshape(na, -1)
+    vs = W.smooth_velocity(nxs, nxs, 15, amp=0.3, L=L * nxs / nx)
+    return nxs, xs, Hs, As, vs
+
+
+def run_reference_advection(a, case):
+    import oracle
+    na = case["n_a"]
+    nxs, xs, Hs, As, vs = advection_sample(case)
+    dt = case["params"]["dt"]
+    for _ in range(a.warmup):
+        oracle.advect(nxs, nxs, xs, na, vs, dt, 1, Hs, As, openmp=True)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        oracle.advect(nxs, nxs, xs, na, vs, dt, 1, Hs, As, openmp=True)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = nxs * nxs * a.steps / total
+    unit = "element-steps/s"
+    line = {
+        "impl": "reference", "metric": "DG upwind advection of H and A: element-steps/s",
+        "value": value, "unit": unit, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "nx": case["nx"], "ny": case["ny"], "n_adv": na},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": oracle.max_threads(True),
+                         "kind": "oracle",
+                         "sample": f"one advection step of a {nxs}x{nxs} corner per step"},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -261,11 +328,12 @@ def roofline_for(precision, case, kt, total_ms, steps):
     common = {"element_kernel_ms_mean": el_s * 1e3, "node_kernel_ms_mean": nd_s * 1e3,
               "element_share_of_subcycle": el_ms / max(el_ms + nd_ms, 1e-12)}
     if precision == "fp64":
-        ach = ELEM_FLOPS[ns] * ne / el_s / 1e12
+        general = case.get("geometry", "uniform") != "uniform"
+        ach = (GEN_ELEM_FLOPS if general else ELEM_FLOPS)[ns] * ne / el_s / 1e12
         bytes_sub = HBM_BYTES.get(("fp64", ns), 0) * ne
         return dict({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": f"k_element_f64<{ns}>",
+                     "kernel": f"k_element_gen<{ns}>" if general else f"k_element_f64<{ns}>",
                      "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
                      "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
                      "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak}, **common)
@@ -418,11 +486,169 @@ def run_ensemble(a, torch, dist, ws, rank):
     return 0
 
 
+def run_advection(a, torch, dist, ws, rank):
+    """Transport workload: `steps` advection steps of DG H and A with the
+    velocity held fixed, timed with CUDA events on the launching stream (L2
+    flushed between steps)."""
+    from paper_2402_00466_gb300 import mevp
+
+    if a.precision != "fp64":
+        raise SystemExit("the transport workload is FP64 (DG1/DG2 ice fields)")
+    dev = torch.cuda.current_device()
+    case = W.make_case(a.workload)
+    nx, ny, na = case["nx"], case["ny"], case["n_a"]
+    ne = nx * ny
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    st = mevp.State(nx, ny, case["n_s"], vertex_xy=case["xy"], n_adv=na,
+                    params=case["params"])
+    st.set_ice(case["H"], case["A"])
+    st.set_forcing(case["tau"])
+    st.set_velocity(case["vel0"])
+    for _ in range(a.warmup):
+        flush.zero_()
+        st.advect(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(a.steps)]
+    for k in range(a.steps):
+        flush.zero_()
+        evs[k][0].record()
+        st.advect(1)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in evs)
+    if ws > 1:
+        total_ms = reduce_max(total_ms, dist, "cuda")
+    st.close()
+    value = whole_job_throughput(ne * a.steps, ws, total_ms / 1e3)
+    stage_s = total_ms / 1e3 / (a.steps * ADV_STAGES[na])
+    ach = ADV_FLOPS[na] * ne / stage_s / 1e12
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        import oracle
+        nxs, xs, Hs, As, vs = advection_sample(case)
+        nsteps, t_cpu = 0, 0.0
+        while t_cpu < 10.0 and nsteps < 20:
+            t0 = time.perf_counter()
+            oracle.advect(nxs, nxs, xs, na, vs, case["params"]["dt"], 1, Hs, As, openmp=True)
+            t_cpu += time.perf_counter() - t0
+            nsteps += 1
+        cpu = {"value": nxs * nxs * nsteps / t_cpu, "unit": "element-steps/s",
+               "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"{nsteps} advection steps of a {nxs}x{nxs} mesh, FP64 C oracle, OpenMP",
+               "seconds": t_cpu}
+    if rank == 0:
+        line = {
+            "metric": "DG upwind advection of H and A: element-steps/s", "value": value,
+            "unit": "element-steps/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": a.workload, "nx": nx, "ny": ny, "n_adv": na,
+                       "rk_stages": ADV_STAGES[na],
+                       "l2": "flushed between timed steps (512 MB write)"},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": f"k_advect<{na}>", "flops_per_element_stage": ADV_FLOPS[na],
+                         "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"},
+            "cpu_baseline": cpu, "e2e": None,
+            "gpu_launches": a.steps * ADV_STAGES[na],
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_adjoint(a, torch, dist, ws, rank):
+    """Adjoint workload: `steps` gradient evaluations (dJ/dP*, dJ/dtau of the
+    kinetic energy after n_sub subcycles, checkpoints every k), device
+    outputs, CUDA events on the launching stream."""
+    from paper_2402_00466_gb300 import mevp
+
+    if a.precision != "fp64":
+        raise SystemExit("the adjoint runs on FP64 states")
+    dev = torch.cuda.current_device()
+    case = W.make_case(a.workload)
+    nx, ny, ns, n_sub = case["nx"], case["ny"], case["n_s"], case["n_sub"]
+    k = W.CONFIGS[a.workload]["adjoint_every"]
+    ne, nn, _ = W.sizes(nx, ny)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    st = mevp.State(nx, ny, ns, vertex_xy=case["xy"], params=case["params"])
+    st.set_ice(case["H"], case["A"])
+    st.set_forcing(case["tau"])
+    st.set_velocity(case["vel0"])
+    st.begin_step()
+    for _ in range(a.warmup):
+        flush.zero_()
+        st.adjoint_kinetic_energy(n_sub, k, device=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(a.steps)]
+    for i in range(a.steps):
+        flush.zero_()
+        evs[i][0].record()
+        st.adjoint_kinetic_energy(n_sub, k, device=True)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in evs)
+    if ws > 1:
+        total_ms = reduce_max(total_ms, dist, "cuda")
+    st.close()
+    value = whole_job_throughput(ne * n_sub * a.steps, ws, total_ms / 1e3)
+    per_es = 2 * (ELEM_FLOPS[ns] + 4 * NODE_FLOPS_PER_NODE) + ADJ_ELEM_FLOPS[ns] + 4 * ADJ_NODE_FLOPS
+    ach = per_es * ne * n_sub * a.steps / (total_ms / 1e3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": "adjoint of the mEVP subcycle: objective element-subcycles/s",
+            "value": value, "unit": "element-subcycles/s", "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": a.workload, "nx": nx, "ny": ny, "n_stress": ns,
+                       "n_sub": n_sub, "checkpoint_every": k,
+                       "gradients": "dJ/dP* [N_e], dJ/dtau [2][N_n], J = 1/2 sum m |v|^2",
+                       "l2": "flushed between timed steps (512 MB write)"},
+            "gradients_per_s": a.steps / (total_ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "whole gradient (2 forward sweeps + reverse sweep)",
+                         "flops_per_element_subcycle": per_es,
+                         "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"},
+            "cpu_baseline": None, "e2e": None,
+            "gpu_launches": a.steps * (n_sub * 2 * 2 + n_sub * 2 + 3),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def _run_ours(a, torch, dist, ws, rank):
     from paper_2402_00466_gb300 import mevp
 
     if a.workload in W.ENSEMBLES:
         return run_ensemble(a, torch, dist, ws, rank)
+    if W.CONFIGS[a.workload]["n_sub"] == 0:
+        return run_advection(a, torch, dist, ws, rank)
+    if "adjoint_every" in W.CONFIGS[a.workload]:
+        return run_adjoint(a, torch, dist, ws, rank)
     dev = torch.cuda.current_device()
 
     def barrier():
@@ -478,7 +704,8 @@ def _run_ours(a, torch, dist, ws, rank):
     st.close()
 
     variants = None
-    if not a.no_variants and ws == 1:
+    general = case.get("geometry", "uniform") != "uniform"
+    if not a.no_variants and ws == 1 and not general:
         variants = {}
         other = "mixed" if a.precision == "fp64" else "fp64"
         mv = measure(mevp, torch, barrier, 1, case, other, a.steps, a.warmup, flush)

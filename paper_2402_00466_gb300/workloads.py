@@ -40,6 +40,17 @@ CONFIGS = {
     # 256x256 quads, DG1 stress, 100 subcycles
     "mesh256_dg1": dict(nx=256, ny=256, n_s=3, n_a=1, n_sub=100, ice="grf", seeds=(7, 8),
                         wind_seed=14),
+    # 256x256 smoothly curvilinear quads (general bilinear elements), DG2, 500 subcycles
+    "mesh256_dg2_wavy": dict(nx=256, ny=256, n_s=6, n_a=1, n_sub=500, ice="grf", seeds=(2, 3),
+                             wind_seed=12, geometry="wavy"),
+    # gradient of the final kinetic energy w.r.t. the P* field and the wind
+    # stress after 100 subcycles on the 256x256 DG1 mesh, checkpoint every 10
+    "adjoint256_dg1": dict(nx=256, ny=256, n_s=3, n_a=1, n_sub=100, ice="grf", seeds=(7, 8),
+                           wind_seed=14, adjoint_every=10, vel_seed=16),
+    # transport of DG2 H and A on 1024x1024 quads with a smooth velocity held
+    # fixed (the step before the subcycles); one advection step per bench step
+    "advect1024_dg2": dict(nx=1024, ny=1024, n_s=6, n_a=6, n_sub=0, ice="grf", seeds=(4, 5),
+                           wind_seed=13, vel_seed=15),
 }
 
 # Ensemble of independent square domains on the 512 km square: sides drawn
@@ -166,10 +177,23 @@ def make_case(name: str, L: float = DOMAIN_M, params: dict | None = None):
         H, A = ice_iid(nx, ny, cfg["seeds"][0])
     else:
         H, A = ice_grf(nx, ny, cfg["seeds"], L)
-    tau = cyclone_wind_stress(node_coords_uniform(nx, ny, L, L), cyclone_params(cfg["wind_seed"], L))
-    return dict(name=name, nx=nx, ny=ny, n_s=cfg["n_s"], n_a=cfg["n_a"], n_sub=cfg["n_sub"],
-                L=L, xy=uniform_vertices(nx, ny, L, L), H=H, A=A, tau=tau,
-                vel0=np.zeros((2, nn)), S0=np.zeros((3, cfg["n_s"], ne)),
+    geometry = cfg.get("geometry", "uniform")
+    xy = wavy_vertices(nx, ny, L=L) if geometry == "wavy" else uniform_vertices(nx, ny, L, L)
+    n_a = cfg["n_a"]
+    if n_a > 1:
+        # DG1/DG2 ice: the random-field means plus seeded slopes and curvatures
+        rng = np.random.Generator(np.random.PCG64(cfg["seeds"][0] + 100))
+        Hd, Ad = np.zeros((n_a, ne)), np.zeros((n_a, ne))
+        Hd[0], Ad[0] = H[0], A[0]
+        Hd[1:] = rng.uniform(-0.1, 0.1, (n_a - 1, ne))
+        Ad[1:] = rng.uniform(-0.02, 0.02, (n_a - 1, ne))
+        H, A = Hd, Ad
+    tau = cyclone_wind_stress(node_coords(nx, ny, xy), cyclone_params(cfg["wind_seed"], L))
+    vel0 = (smooth_velocity(nx, ny, cfg["vel_seed"], amp=0.3, L=L) if "vel_seed" in cfg
+            else np.zeros((2, nn)))
+    return dict(name=name, nx=nx, ny=ny, n_s=cfg["n_s"], n_a=n_a, n_sub=cfg["n_sub"],
+                L=L, xy=xy, geometry=geometry, H=H, A=A, tau=tau,
+                vel0=vel0, S0=np.zeros((3, cfg["n_s"], ne)),
                 params=dict(DEFAULT_PARAMS if params is None else params))
 
 
