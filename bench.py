@@ -69,6 +69,14 @@ NODE_FLOPS_PER_NODE = 32.5          # node kernel (force gather, velocity update
 # ice strength, vertices amortised, 4 nodes x (v R, v W, node constants R)).
 HBM_BYTES = {("fp64", 6): 608, ("fp64", 3): 464}
 
+# DRAM bytes per launch of the dominant kernel, from one ncu capture of the
+# same command line (ncu flushes the caches before a profiled launch, so this
+# is the launch's cold-cache traffic); keyed by (workload, precision, kernel)
+# and valid while that kernel is unchanged.  Summaries: profiles/.
+NCU_TRAFFIC = {
+    ("mesh256_dg2", "fp64", "k_element_f64<6>"): 14248448 + 768,
+}
+
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -318,6 +326,14 @@ def measure(mevp, torch, barrier, ws, case, precision, steps, warmup, flush, tim
 
 
 def roofline_for(precision, case, kt, total_ms, steps):
+    r = _roofline_for(precision, case, kt, total_ms, steps)
+    r["traffic"] = NCU_TRAFFIC.get((case["name"], precision, r["kernel"]))
+    if r["traffic"] is not None:
+        r["traffic_note"] = "ncu dram__bytes_read+write per launch, cold cache"
+    return r
+
+
+def _roofline_for(precision, case, kt, total_ms, steps):
     ns, ne, n_sub = case["n_s"], case["nx"] * case["ny"], case["n_sub"]
     el_ms, el_n = kt["element"]
     nd_ms, nd_n = kt["node"]

@@ -338,6 +338,12 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.ns = n_stress;
   d.na = n_adv;
   d.prec = precision;
+  d.nsm = 1;
+  if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+      d.nsm < 1) {
+    cudaGetLastError();
+    d.nsm = 1;
+  }
   d.xline = (const double *)(b + L.xline);
   d.yline = (const double *)(b + L.yline);
   d.xy = mesh->general ? (const double2 *)(b + L.xy) : nullptr;
@@ -827,6 +833,12 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
   d.nn = (int)nn;
   d.ns = n_stress;
   d.na = 1;
+  d.nsm = 1;
+  if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      d.nsm < 1) {
+    cudaGetLastError();
+    d.nsm = 1;
+  }
   d.prec = MEVP_FP64;
   d.xline = xline;
   d.yline = yline;

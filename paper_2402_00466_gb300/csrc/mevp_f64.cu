@@ -29,16 +29,13 @@ namespace mevp {
 
 namespace {
 
-// Element kernel block size and the minimum resident blocks per SM asked of
-// the compiler (which caps the registers per thread at
-// 65536 / (block * min blocks)).
-#ifndef MEVP_F64_ELEM_BLOCK
-#define MEVP_F64_ELEM_BLOCK 128
-#endif
-#ifndef MEVP_F64_ELEM_MIN_BLOCKS
-#define MEVP_F64_ELEM_MIN_BLOCKS 1
-#endif
-constexpr int kElemBlock = MEVP_F64_ELEM_BLOCK;
+// The single-state FP64 kernels are persistent: one block per SM, each block
+// taking an equal contiguous share of the element warps (node slots), so that
+// every SM gets the same work whatever the mesh size -- a plain grid of
+// independent blocks leaves part of the chip idle in its last wave.  512
+// threads at one block per SM caps the element kernel at 128 registers.
+constexpr int kElemBlock = 512;
+constexpr int kNodeSlotThreads = 768;
 constexpr int kNodeBlock = 256;
 
 // Strain coefficients E11, E12, E22 (for the diagnostic read-back):
@@ -104,14 +101,15 @@ __device__ __forceinline__ void elem_f64(const DevState &d, const Rheo &r, int c
 }
 
 template <int NS, bool VAR = false>
-#ifdef MEVP_F64_ELEM_MAXREG
-__global__ void __maxnreg__(MEVP_F64_ELEM_MAXREG)
-#else
-__global__ void __launch_bounds__(kElemBlock, MEVP_F64_ELEM_MIN_BLOCKS)
-#endif
-    k_element_f64(DevState d, Rheo r, int cur) {
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K < d.ne) elem_f64<NS, VAR>(d, r, cur, K);
+__global__ void __launch_bounds__(kElemBlock, 1) k_element_f64(DevState d, Rheo r, int cur) {
+  const int nwarps = (d.ne + 31) >> 5;
+  const int w0 = (int)((long long)nwarps * blockIdx.x / gridDim.x);
+  const int w1 = (int)((long long)nwarps * (blockIdx.x + 1) / gridDim.x);
+  const int lane = threadIdx.x & 31;
+  for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += kElemBlock / 32) {
+    const int K = (w << 5) + lane;
+    if (K < d.ne) elem_f64<NS, VAR>(d, r, cur, K);
+  }
 }
 
 // Sum of the element forces at node (ix, iy) over the elements that contain
@@ -221,12 +219,16 @@ __device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int ha
 //   a = m(1+beta)/dt + c,  b = m f,  c = l Cw rho_w |v_o - v^{p-1}|
 //   r = m beta/dt v^{p-1} + (m/dt v^n + l tau) + F + c v_o
 //   (a + i b) v^p = r   (complex notation)
-__global__ void __launch_bounds__(kNodeBlock) k_node_f64(DevState d, int cur, int has_vo) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kNodeSlotThreads, 1) k_node_f64(DevState d, int cur,
+                                                                   int has_vo) {
   const int sw = d.nx + 1;
-  if (slot >= sw * (d.ny + 1)) return;
-  const int ky = slot / sw, kx = slot - ky * sw;
-  node_slot_f64(d, cur, has_vo, kx, ky);
+  const int nslots = sw * (d.ny + 1);
+  const int s0 = (int)((long long)nslots * blockIdx.x / gridDim.x);
+  const int s1 = (int)((long long)nslots * (blockIdx.x + 1) / gridDim.x);
+  for (int slot = s0 + (int)threadIdx.x; slot < s1; slot += kNodeSlotThreads) {
+    const int ky = slot / sw, kx = slot - ky * sw;
+    node_slot_f64(d, cur, has_vo, kx, ky);
+  }
 }
 
 // Ensemble kernels: persistent, grid-stride over (member, block) work items.
@@ -477,7 +479,7 @@ cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo,
 cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
                                 cudaStream_t st, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[0], st);
-  const int eg = blocks(d.ne, kElemBlock);
+  const int eg = d.nsm;  // persistent: one block per SM
   if (d.xy)
     launch_element_general(d, r, cur, st);
   else if (d.na == 1) {
@@ -497,7 +499,8 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
   }
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
-  k_node_f64<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, cur, has_vo ? 1 : 0);
+  (void)slots;
+  k_node_f64<<<d.nsm, kNodeSlotThreads, 0, st>>>(d, cur, has_vo ? 1 : 0);
   if (ev) cudaEventRecord(ev[2], st);
   return cudaGetLastError();
 }

@@ -56,6 +56,7 @@ inline Rheo make_rheo(const mevp_params &p) {
 struct DevState {
   int nx, ny, ne, nw, nh, nn, ns, prec;
   int na;              // DG dofs of H and A per element (1, 3 or 6)
+  int nsm;             // SMs of the device (grid of the persistent kernels)
   const double *xline, *yline;
   const double2 *xy;   // general mesh: [(nx+1)(ny+1)] vertices; NULL on rectilinear meshes
   double *lines;       // [hx: nx][1/hx: nx][hy: ny][1/hy: ny], from the mesh lines
