@@ -254,54 +254,26 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma,
 // 1024^2).  The owned nodes' velocity and constant records, needed only by
 // the node stage, are copied into shared memory asynchronously from the start.
 template <int TX, int TY> struct Tile {
-  static constexpr int SX = TX - 1, SY = TY - 1;  // owned 2x2 node slots
-  static constexpr int NSLOT = SX * SY;
-  static constexpr size_t smem = sizeof(float4) * 2 * 4 * NSLOT + sizeof(float2) * 9 * TX * TY;
+  static constexpr int NW = 2 * (TX - 1), NH = 2 * (TY - 1);  // owned-node window
+  static constexpr size_t smem = sizeof(float4) * 2 * NW * NH + sizeof(float2) * 9 * TX * TY;
 };
-
-// Velocity update of one owned node (ix, iy) = (2 sx + dx, 2 sy + dy) of slot
-// (sx, sy) (tile element (ex, ey) = (sx + 1, sy + 1)), from the element
-// forces in shared memory in the fixed order SW, SE, NW, NE.
-template <int TX, int TY, int DX, int DY>
-__device__ __forceinline__ float4 slot_node(const MixArgs &ma, float2 (*fs)[TY][TX], int ex,
-                                            int ey, float4 v, float4 k, float2 o) {
-  float2 tf[4];
-  int n;
-  if (DX == 0 && DY == 0) {  // vertex: SW, SE, NW, NE
-    tf[0] = fs[8][ey - 1][ex - 1]; tf[1] = fs[6][ey - 1][ex];
-    tf[2] = fs[2][ey][ex - 1];     tf[3] = fs[0][ey][ex];
-    n = 4;
-  } else if (DX == 1 && DY == 0) {  // horizontal edge: S, N
-    tf[0] = fs[7][ey - 1][ex]; tf[1] = fs[1][ey][ex];
-    n = 2;
-  } else if (DX == 0 && DY == 1) {  // vertical edge: W, E
-    tf[0] = fs[5][ey][ex - 1]; tf[1] = fs[3][ey][ex];
-    n = 2;
-  } else {  // centre
-    tf[0] = fs[4][ey][ex];
-    n = 1;
-  }
-  return node_update_mix(ma, v, k, o, tf, n);
-}
 
 template <int NS, int TX, int TY>
 __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, int cur, int bx,
                                          int by, float4 *smem) {
-  constexpr int SX = Tile<TX, TY>::SX, NSLOT = Tile<TX, TY>::NSLOT;
-  // owned node records, slot-major per node type q = dx + 2 dy: [4][NSLOT]
-  float4 *sv = smem;              // velocity records
-  float4 *sk = sv + 4 * NSLOT;    // constant records
-  float2(*fs)[TY][TX] = (float2(*)[TY][TX])(sk + 4 * NSLOT);  // [9][TY][TX] forces
+  constexpr int TNW = Tile<TX, TY>::NW, TNH = Tile<TX, TY>::NH;
+  float4 *sv = smem;              // [TNH][TNW] velocity records of the owned nodes
+  float4 *sk = sv + TNW * TNH;    // [TNH][TNW] constant records of the owned nodes
+  float2(*fs)[TY][TX] = (float2(*)[TY][TX])(sk + TNW * TNH);  // [9][TY][TX] forces
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
   const int x0 = bx * (TX - 1), y0 = by * (TY - 1);
   const int ixs = 2 * x0, iys = 2 * y0;
   const float4 *__restrict__ vel = d.vel4[cur];
   // The node stage's inputs do not depend on the element stage: start their
   // copies now, so that they arrive while the elements are computed.
-  for (int i = tid; i < 4 * NSLOT; i += TX * TY) {
-    const int q = i / NSLOT, sl = i - q * NSLOT;
-    const int sy = sl / SX, sx = sl - sy * SX;
-    const int gx = ixs + 2 * sx + (q & 1), gy = iys + 2 * sy + (q >> 1);
+  for (int i = tid; i < TNW * TNH; i += TX * TY) {
+    const int r = i / TNW, c = i - r * TNW;
+    const int gx = ixs + c, gy = iys + r;
     if (gx < d.nw && gy < d.nh) {
       const size_t node = (size_t)gy * d.nw + gx;
       cp_async16(sv + i, vel + node);
@@ -338,31 +310,39 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
   for (int j = 0; j < 9; ++j) fs[j][ly][lx] = f[j];
   cp_async_wait_all();
   __syncthreads();
-  const int ixe = (x0 + TX - 1 >= d.nx) ? d.nw : ixs + 2 * SX;
-  const int iye = (y0 + TY - 1 >= d.ny) ? d.nh : iys + 2 * Tile<TX, TY>::SY;
+  const int ixe = (x0 + TX - 1 >= d.nx) ? d.nw : ixs + TNW;
+  const int iye = (y0 + TY - 1 >= d.ny) ? d.nh : iys + TNH;
   float4 *__restrict__ vq = d.vel4[cur ^ 1];
-  // the owned nodes as (node type q, slot) work items, type-major: the
-  // threads of a warp take consecutive slots of one node type, so a warp's
-  // control flow (number of element contributions) stays uniform
-  for (int t = tid; t < 4 * NSLOT; t += TX * TY) {
-    const int q = t / NSLOT, sl = t - q * NSLOT;
-    const int sy = sl / SX, sx = sl - sy * SX;
-    const int jx = ixs + 2 * sx + (q & 1), jy = iys + 2 * sy + (q >> 1);
-    if (jx >= ixe || jy >= iye) continue;
-    const size_t node = (size_t)jy * d.nw + jx;
-    float4 out;
-    if (jx == 0 || jy == 0 || jx == d.nw - 1 || jy == d.nh - 1) {
-      out = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-      const float4 v = sv[t], k = sk[t];
-      const float2 o = ocean(d, ma, node);
-      const int ex = sx + 1, ey = sy + 1;
-      if (q == 0) out = slot_node<TX, TY, 0, 0>(ma, fs, ex, ey, v, k, o);
-      else if (q == 1) out = slot_node<TX, TY, 1, 0>(ma, fs, ex, ey, v, k, o);
-      else if (q == 2) out = slot_node<TX, TY, 0, 1>(ma, fs, ex, ey, v, k, o);
-      else out = slot_node<TX, TY, 1, 1>(ma, fs, ex, ey, v, k, o);
+  // interior window first (constant width: cheap index arithmetic) ...
+  for (int t = tid; t < TNW * TNH; t += TX * TY) {
+    const int r = t / TNW;
+    const int ix = ixs + (t - r * TNW), iy = iys + r;
+    if (ix >= ixe || iy >= iye) continue;
+    const size_t node = (size_t)iy * d.nw + ix;
+    if (ix == 0 || iy == 0 || ix == d.nw - 1 || iy == d.nh - 1) {
+      vq[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
     }
-    vq[node] = out;
+    // local tile coordinates of the element whose lower-left node is (ix, iy)
+    const int ex = (ix >> 1) - x0 + 1, ey = (iy >> 1) - y0 + 1;
+    float2 tf[4];
+    int n;
+    const bool odd_x = ix & 1, odd_y = iy & 1;
+    if (!odd_x && !odd_y) {  // vertex: SW, SE, NW, NE
+      tf[0] = fs[8][ey - 1][ex - 1]; tf[1] = fs[6][ey - 1][ex];
+      tf[2] = fs[2][ey][ex - 1];     tf[3] = fs[0][ey][ex];
+      n = 4;
+    } else if (odd_x && !odd_y) {  // horizontal edge: S, N
+      tf[0] = fs[7][ey - 1][ex]; tf[1] = fs[1][ey][ex];
+      n = 2;
+    } else if (!odd_x && odd_y) {  // vertical edge: W, E
+      tf[0] = fs[5][ey][ex - 1]; tf[1] = fs[3][ey][ex];
+      n = 2;
+    } else {  // centre
+      tf[0] = fs[4][ey][ex];
+      n = 1;
+    }
+    vq[node] = node_update_mix(ma, sv[t], sk[t], ocean(d, ma, node), tf, n);
   }
   // ... then the domain's last boundary column / row, owned by the last tiles
   if (ixe == d.nw)
