@@ -46,15 +46,27 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+CHECKED_BUILD = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(CHECKED_BUILD, "libmevp.so")
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile every translation unit and link libmevp.so.  checked=True
+    builds the bounds-checked variant (-DMEVP_CHECKED: every kernel access
+    tested, failures reported by mevp_sync as MEVP_ERR_BOUNDS) into
+    _build_checked/ instead."""
+    build_dir, lib = (CHECKED_BUILD, CHECKED_LIB) if checked else (BUILD, LIB)
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DMEVP_CHECKED",)
+    if not force and os.path.exists(lib) and all(
+            os.path.getmtime(p) <= os.path.getmtime(lib) for p in _deps()):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-I", os.path.join(ROOT, "include"),
                "-c", src, "-o", obj]
         if verbose:
@@ -71,15 +83,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--checked", action="store_true", help="bounds-checked variant")
     a = ap.parse_args()
-    print(build(force=a.force, verbose=a.verbose))
+    print(build(force=a.force, verbose=a.verbose, checked=a.checked))

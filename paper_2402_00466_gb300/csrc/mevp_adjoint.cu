@@ -370,6 +370,7 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
                                            double *J, double *dJ_dPstar, double *dJ_dtau,
                                            int on_device) {
   using namespace mevp;
+  NvtxRange nvtx_range_("mevp_adjoint_kinetic_energy");
   int rc = api_check_state(s);
   if (rc) return rc;
   if (s->prec != MEVP_FP64) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: FP64 states only");

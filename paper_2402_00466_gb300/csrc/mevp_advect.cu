@@ -72,16 +72,21 @@ __device__ __forceinline__ AdvGeom adv_geom(const DevState &d, int kx, int ky) {
   AdvGeom G;
   if (d.xy) {
     const size_t vw = (size_t)d.nx + 1;
-    const double2 p00 = d.xy[(size_t)ky * vw + kx], p10 = d.xy[(size_t)ky * vw + kx + 1];
-    const double2 p01 = d.xy[(size_t)(ky + 1) * vw + kx];
-    const double2 p11 = d.xy[(size_t)(ky + 1) * vw + kx + 1];
-    G.m = quad_map(d.xy, d.nx, kx, ky);
+    const long long nv = (long long)vw * (d.ny + 1);
+    const double2 p00 = ck_ld(d.flags, d.xy, (long long)(ky * vw + kx), nv, 175);
+    const double2 p10 = ck_ld(d.flags, d.xy, (long long)(ky * vw + kx + 1), nv, 175);
+    const double2 p01 = ck_ld(d.flags, d.xy, (long long)((ky + 1) * vw + kx), nv, 175);
+    const double2 p11 = ck_ld(d.flags, d.xy, (long long)((ky + 1) * vw + kx + 1), nv, 175);
+    G.m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
     G.ex[0] = p01.x - p00.x; G.ey[0] = p01.y - p00.y;
     G.ex[1] = p11.x - p10.x; G.ey[1] = p11.y - p10.y;
     G.ex[2] = p10.x - p00.x; G.ey[2] = p10.y - p00.y;
     G.ex[3] = p11.x - p01.x; G.ey[3] = p11.y - p01.y;
   } else {
-    const double hx = d.xline[kx + 1] - d.xline[kx], hy = d.yline[ky + 1] - d.yline[ky];
+    const double hx = ck_ld(d.flags, d.xline, kx + 1, d.nx + 1, 175) -
+                      ck_ld(d.flags, d.xline, kx, d.nx + 1, 175);
+    const double hy = ck_ld(d.flags, d.yline, ky + 1, d.ny + 1, 175) -
+                      ck_ld(d.flags, d.yline, ky, d.ny + 1, 175);
     G.m.Ax = hx; G.m.Ay = 0.0; G.m.Bx = 0.0; G.m.By = hy; G.m.cx = 0.0; G.m.cy = 0.0;
     G.ex[0] = G.ex[1] = 0.0; G.ey[0] = G.ey[1] = hy;
     G.ex[2] = G.ex[3] = hx; G.ey[2] = G.ey[3] = 0.0;
@@ -103,15 +108,16 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
   const size_t ne = d.ne, nn = d.nn;
   const AdvGeom G = adv_geom(d, kx, ky);
   const QuadMap &m = G.m;
+  const long long nf = (long long)d.na * d.ne;
   double h[NA], a[NA];
 #pragma unroll
   for (int i = 0; i < NA; ++i) {
-    h[i] = g.Hin[(size_t)i * ne + K];
-    a[i] = g.Ain[(size_t)i * ne + K];
+    h[i] = ck_ld(d.flags, g.Hin, (long long)i * ne + K, nf, 171);
+    a[i] = ck_ld(d.flags, g.Ain, (long long)i * ne + K, nf, 171);
   }
   double vx[9], vy[9];
-  gather9(g.vel, d.nw, kx, ky, vx);
-  gather9(g.vel + nn, d.nw, kx, ky, vy);
+  gather9(g.vel, d.nw, kx, ky, vx, d.flags, d.nn);
+  gather9(g.vel + nn, d.nw, kx, ky, vy, d.flags, d.nn);
   double RH[NA], RA[NA];
 #pragma unroll
   for (int i = 0; i < NA; ++i) RH[i] = RA[i] = 0.0;
@@ -169,8 +175,8 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
     if (nb >= 0) {
 #pragma unroll
       for (int i = 0; i < NA; ++i) {
-        hn[i] = g.Hin[(size_t)i * ne + nb];
-        an[i] = g.Ain[(size_t)i * ne + nb];
+        hn[i] = ck_ld(d.flags, g.Hin, (long long)i * ne + nb, nf, 172);
+        an[i] = ck_ld(d.flags, g.Ain, (long long)i * ne + nb, nf, 172);
       }
     }
     // edge vector t (along eta on west/east edges, along xi on south/north
@@ -246,10 +252,12 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
   }
 #pragma unroll
   for (int i = 0; i < NA; ++i) {
-    const size_t o = (size_t)i * ne + K;
+    const long long o = (long long)i * ne + K;
     const double hs = fma(g.dt, RH[i], h[i]), as = fma(g.dt, RA[i], a[i]);
-    g.Hout[o] = g.a == 0.0 ? g.b * hs : fma(g.a, g.H0[o], g.b * hs);
-    g.Aout[o] = g.a == 0.0 ? g.b * as : fma(g.a, g.A0[o], g.b * as);
+    const double h0 = g.a == 0.0 ? 0.0 : ck_ld(d.flags, g.H0, o, nf, 173);
+    const double a0 = g.a == 0.0 ? 0.0 : ck_ld(d.flags, g.A0, o, nf, 173);
+    ck_st(d.flags, g.Hout, o, nf, 174, g.a == 0.0 ? g.b * hs : fma(g.a, h0, g.b * hs));
+    ck_st(d.flags, g.Aout, o, nf, 174, g.a == 0.0 ? g.b * as : fma(g.a, a0, g.b * as));
   }
 }
 

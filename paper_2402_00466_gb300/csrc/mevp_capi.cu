@@ -192,7 +192,13 @@ extern "C" {
 
 const char *mevp_last_error(void) { return g_err.c_str(); }
 
-const char *mevp_version(void) { return "mevp-gb300 0.1 (sm_103a)"; }
+const char *mevp_version(void) {
+#ifdef MEVP_CHECKED
+  return "mevp-gb300 0.1 (sm_103a, bounds-checked)";
+#else
+  return "mevp-gb300 0.1 (sm_103a)";
+#endif
+}
 
 int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_xy,
                      mevp_mesh **out) {
@@ -501,6 +507,7 @@ int mevp_set_stress(mevp_state *s, const double *S, int on_device) {
 }
 
 int mevp_advect(mevp_state *s, int n_steps) {
+  mevp::NvtxRange nvtx_range_("mevp_advect");
   int rc = check_state(s);
   if (rc) return rc;
   if (n_steps < 0) return fail(MEVP_ERR_ARG, "advect: n_steps=%d < 0", n_steps);
@@ -515,6 +522,7 @@ int mevp_advect(mevp_state *s, int n_steps) {
 }
 
 int mevp_begin_step(mevp_state *s) {
+  mevp::NvtxRange nvtx_range_("mevp_begin_step");
   int rc = check_state(s);
   if (rc) return rc;
   if (!s->have_params) return fail(MEVP_ERR_STATE, "begin_step: parameters not set");
@@ -527,6 +535,7 @@ int mevp_begin_step(mevp_state *s) {
 }
 
 int mevp_run_subcycles(mevp_state *s, int n) {
+  mevp::NvtxRange nvtx_range_("mevp_run_subcycles");
   int rc = check_state(s);
   if (rc) return rc;
   if (n < 0) return fail(MEVP_ERR_ARG, "run_subcycles: n=%d < 0", n);
@@ -640,6 +649,7 @@ int mevp_timing_read(mevp_state *s, double *ms, long long *launches) {
 }
 
 int mevp_read_field(mevp_state *s, int field, double *dst, size_t count, int on_device) {
+  mevp::NvtxRange nvtx_range_("mevp_read_field");
   int rc = check_state(s);
   if (rc) return rc;
   if (!dst) return fail(MEVP_ERR_ARG, "read_field: dst is NULL");
@@ -692,6 +702,16 @@ int mevp_sync(mevp_state *s) {
   if (rc) return rc;
   MEVP_CUDA(cudaStreamSynchronize(s->stream), "sync");
   MEVP_CUDA(cudaGetLastError(), "sync");
+#ifdef MEVP_CHECKED
+  {
+    int site = 0;
+    MEVP_CUDA(cudaMemcpy(&site, s->d.flags + 1, sizeof(int), cudaMemcpyDeviceToHost), "sync");
+    if (site) {
+      MEVP_CUDA(cudaMemset(s->d.flags + 1, 0, sizeof(int)), "sync");
+      return fail(MEVP_ERR_BOUNDS, "sync: out-of-bounds access at kernel site %d", site);
+    }
+  }
+#endif
   if (s->nan_every > 0) {
     int flag = 0;
     MEVP_CUDA(cudaMemcpy(&flag, s->d.flags, sizeof(int), cudaMemcpyDeviceToHost), "sync");
@@ -783,6 +803,7 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
                                           const double *H, const double *A, const double *tau,
                                           const double *v_ocean, double *vel, double *S, int n,
                                           void *cuda_stream) {
+  mevp::NvtxRange nvtx_range_("mevp_run_subcycles_noalloc");
   if (nx < 1 || ny < 1)
     return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: nx=%d ny=%d must be >= 1", nx, ny);
   if (n_stress != 3 && n_stress != 6)

@@ -350,6 +350,7 @@ int mevp_ensemble_begin_step(mevp_ensemble *e) {
 }
 
 int mevp_ensemble_run_subcycles(mevp_ensemble *e, int n) {
+  mevp::NvtxRange nvtx_range_("mevp_ensemble_run_subcycles");
   int rc = check_ensemble(e);
   if (rc) return rc;
   if (n < 0) return efail(MEVP_ERR_ARG, "ensemble_run_subcycles: n=%d < 0", n);
@@ -360,6 +361,7 @@ int mevp_ensemble_run_subcycles(mevp_ensemble *e, int n) {
 }
 
 int mevp_ensemble_autotune(mevp_ensemble *e, int trial_subcycles, int *best) {
+  mevp::NvtxRange nvtx_range_("mevp_ensemble_autotune");
   int rc = check_ensemble(e);
   if (rc) return rc;
   if (trial_subcycles < 1) return efail(MEVP_ERR_ARG, "ensemble_autotune: trial_subcycles < 1");

@@ -61,42 +61,45 @@ __device__ __forceinline__ void strain_dg(const double u[9], const double v[9], 
 template <int NS, bool VAR = false>
 __device__ __forceinline__ void elem_f64(const DevState &d, const Rheo &r, int cur, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
-  const double hx = __ldg(d.lines + kx), ihx = __ldg(d.lines + d.nx + kx);
-  const double hy = __ldg(d.lines + 2 * d.nx + ky), ihy = __ldg(d.lines + 2 * d.nx + d.ny + ky);
+  const long long nl = 2LL * (d.nx + d.ny);
+  const double hx = ck_ldg(d.flags, (const double *)d.lines, kx, nl, 101);
+  const double ihx = ck_ldg(d.flags, (const double *)d.lines, d.nx + kx, nl, 101);
+  const double hy = ck_ldg(d.flags, (const double *)d.lines, 2 * d.nx + ky, nl, 101);
+  const double ihy = ck_ldg(d.flags, (const double *)d.lines, 2 * d.nx + d.ny + ky, nl, 101);
   double u[9], v[9];
-  gather9(d.vel[cur], d.nw, kx, ky, u);
-  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+  gather9(d.vel[cur], d.nw, kx, ky, u, d.flags, d.nn);
+  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v, d.flags, d.nn);
   double Pc[NS], Qc[NS], Gc[NS];
   strain_invariants<NS>(u, v, ihx, ihy, r.ie, Pc, Qc, Gc);
   double S11[NS], S12[NS], S22[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
-    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
-    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+    S11[s] = ck_ld(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S12[s] = ck_ld(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S22[s] = ck_ld(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
   }
   if constexpr (VAR) {  // DG1/DG2 H, A: ice strength per Gauss point
     constexpr int NG = DgSpace<NS>::NGP * DgSpace<NS>::NGP;
     double Phg[NG];
 #pragma unroll
-    for (int g = 0; g < NG; ++g) Phg[g] = __ldg(d.Pg + (size_t)g * d.ne + K) * r.hainv;
+    for (int g = 0; g < NG; ++g) Phg[g] = ck_ldg(d.flags, d.Pg, (long long)g * d.ne + K, (long long)NG * d.ne, 104) * r.hainv;
     relax_stress_p<NS, true>(S11, S12, S22, Pc, Qc, Gc, 0.0, Phg, r.dmin2, r.fac, r.ie);
   } else {
-    const double Ph = __ldg(d.Pe + K) * r.hainv;
+    const double Ph = ck_ldg(d.flags, d.Pe, (long long)K, (long long)d.ne, 104) * r.hainv;
     relax_stress<NS>(S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
   }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    d.S[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
-    d.S[(size_t)(1 * NS + s) * d.ne + K] = S12[s];
-    d.S[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
+    ck_st(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 105, S11[s]);
+    ck_st(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 105, S12[s]);
+    ck_st(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 105, S22[s]);
   }
   double fx[9], fy[9];
   element_forces_t<NS>(S11, S12, S22, hx, hy, fx, fy);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    d.fbuf[(size_t)j * d.ne + K] = fx[j];
-    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+    ck_st(d.flags, d.fbuf, (long long)j * d.ne + K, 18LL * d.ne, 106, fx[j]);
+    ck_st(d.flags, d.fbuf, (long long)(9 + j) * d.ne + K, 18LL * d.ne, 106, fy[j]);
   }
 }
 
@@ -159,42 +162,44 @@ __device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int ha
       if (ix >= d.nw || iy >= d.nh) continue;
       const size_t node = (size_t)iy * d.nw + ix;
       if (ix == 0 || iy == 0 || ix == d.nw - 1 || iy == d.nh - 1) {
-        vq[node] = 0.0;
-        vq[nn + node] = 0.0;
+        ck_st(d.flags, vq, (long long)node, 2LL * nn, 115, 0.0);
+        ck_st(d.flags, vq, (long long)(nn + node), 2LL * nn, 115, 0.0);
         continue;
       }
       const double *__restrict__ fb = d.fbuf;
+      const long long nf = 18LL * ne;
       double Fx, Fy;
       if (dx == 0 && dy == 0) {  // vertex node: 4 elements
         const size_t Ksw = (size_t)(ky - 1) * d.nx + kx - 1, Kse = Ksw + 1;
         const size_t Knw = (size_t)ky * d.nx + kx - 1, Kne = Knw + 1;
-        Fx = __ldg(fb + 8 * ne + Ksw) + __ldg(fb + 6 * ne + Kse);
-        Fx = Fx + __ldg(fb + 2 * ne + Knw);
-        Fx = Fx + __ldg(fb + 0 * ne + Kne);
-        Fy = __ldg(fb + 17 * ne + Ksw) + __ldg(fb + 15 * ne + Kse);
-        Fy = Fy + __ldg(fb + 11 * ne + Knw);
-        Fy = Fy + __ldg(fb + 9 * ne + Kne);
+        Fx = ck_ldg(d.flags, fb, (long long)(8 * ne + Ksw), nf, 111) + ck_ldg(d.flags, fb, (long long)(6 * ne + Kse), nf, 111);
+        Fx = Fx + ck_ldg(d.flags, fb, (long long)(2 * ne + Knw), nf, 111);
+        Fx = Fx + ck_ldg(d.flags, fb, (long long)(0 * ne + Kne), nf, 111);
+        Fy = ck_ldg(d.flags, fb, (long long)(17 * ne + Ksw), nf, 111) + ck_ldg(d.flags, fb, (long long)(15 * ne + Kse), nf, 111);
+        Fy = Fy + ck_ldg(d.flags, fb, (long long)(11 * ne + Knw), nf, 111);
+        Fy = Fy + ck_ldg(d.flags, fb, (long long)(9 * ne + Kne), nf, 111);
       } else if (dx == 1 && dy == 0) {  // horizontal edge: S then N element
         const size_t Ks = (size_t)(ky - 1) * d.nx + kx, Kn = (size_t)ky * d.nx + kx;
-        Fx = __ldg(fb + 7 * ne + Ks) + __ldg(fb + 1 * ne + Kn);
-        Fy = __ldg(fb + 16 * ne + Ks) + __ldg(fb + 10 * ne + Kn);
+        Fx = ck_ldg(d.flags, fb, (long long)(7 * ne + Ks), nf, 111) + ck_ldg(d.flags, fb, (long long)(1 * ne + Kn), nf, 111);
+        Fy = ck_ldg(d.flags, fb, (long long)(16 * ne + Ks), nf, 111) + ck_ldg(d.flags, fb, (long long)(10 * ne + Kn), nf, 111);
       } else if (dx == 0 && dy == 1) {  // vertical edge: W then E element
         const size_t Kw = (size_t)ky * d.nx + kx - 1, Ke = Kw + 1;
-        Fx = __ldg(fb + 5 * ne + Kw) + __ldg(fb + 3 * ne + Ke);
-        Fy = __ldg(fb + 14 * ne + Kw) + __ldg(fb + 12 * ne + Ke);
+        Fx = ck_ldg(d.flags, fb, (long long)(5 * ne + Kw), nf, 111) + ck_ldg(d.flags, fb, (long long)(3 * ne + Ke), nf, 111);
+        Fy = ck_ldg(d.flags, fb, (long long)(14 * ne + Kw), nf, 111) + ck_ldg(d.flags, fb, (long long)(12 * ne + Ke), nf, 111);
       } else {  // element centre
         const size_t K = (size_t)ky * d.nx + kx;
-        Fx = __ldg(fb + 4 * ne + K);
-        Fy = __ldg(fb + 13 * ne + K);
+        Fx = ck_ldg(d.flags, fb, (long long)(4 * ne + K), nf, 111);
+        Fy = ck_ldg(d.flags, fb, (long long)(13 * ne + K), nf, 111);
       }
-      const double vx = vp[node], vy = vp[nn + node];
-      const double cA = __ldg(d.nodec + 0 * nn + node), cB = __ldg(d.nodec + 1 * nn + node);
-      const double cK = __ldg(d.nodec + 2 * nn + node), qx = __ldg(d.nodec + 3 * nn + node);
-      const double qy = __ldg(d.nodec + 4 * nn + node), cD = __ldg(d.nodec + 5 * nn + node);
+      const double vx = ck_ld(d.flags, vp, (long long)node, 2LL * nn, 112);
+      const double vy = ck_ld(d.flags, vp, (long long)(nn + node), 2LL * nn, 112);
+      const double cA = ck_ldg(d.flags, (const double *)d.nodec, (long long)(0 * nn + node), 6LL * nn, 113), cB = ck_ldg(d.flags, (const double *)d.nodec, (long long)(1 * nn + node), 6LL * nn, 113);
+      const double cK = ck_ldg(d.flags, (const double *)d.nodec, (long long)(2 * nn + node), 6LL * nn, 113), qx = ck_ldg(d.flags, (const double *)d.nodec, (long long)(3 * nn + node), 6LL * nn, 113);
+      const double qy = ck_ldg(d.flags, (const double *)d.nodec, (long long)(4 * nn + node), 6LL * nn, 113), cD = ck_ldg(d.flags, (const double *)d.nodec, (long long)(5 * nn + node), 6LL * nn, 113);
       double ox = 0.0, oy = 0.0;
       if (has_vo) {
-        ox = __ldg(d.vo + node);
-        oy = __ldg(d.vo + nn + node);
+        ox = ck_ldg(d.flags, (const double *)d.vo, (long long)node, 2LL * nn, 114);
+        oy = ck_ldg(d.flags, (const double *)d.vo, (long long)(nn + node), 2LL * nn, 114);
       }
       const double dvx = ox - vx, dvy = oy - vy;
       const double c = cD * sqrt(dvx * dvx + dvy * dvy);
@@ -208,8 +213,8 @@ __device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int ha
         ux = fma(a, rx, cB * ry) * inv;
         uy = fma(a, ry, -cB * rx) * inv;
       }
-      vq[node] = ux;
-      vq[nn + node] = uy;
+      ck_st(d.flags, vq, (long long)node, 2LL * nn, 115, ux);
+      ck_st(d.flags, vq, (long long)(nn + node), 2LL * nn, 115, uy);
     }
   }
 }
@@ -319,7 +324,7 @@ __device__ __forceinline__ double mass_integral_gauss(const DevState &d, int kx,
   const int K = ky * d.nx + kx;
   QuadMap m;
   if (d.xy) {
-    m = quad_map(d.xy, d.nx, kx, ky);
+    m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
   } else {
     m.Ax = d.xline[kx + 1] - d.xline[kx];
     m.By = d.yline[ky + 1] - d.yline[ky];
@@ -354,7 +359,7 @@ __global__ void k_node_constants(DevState d, int cur, mevp_params p, int has_vo)
       if (kx < 0 || kx >= d.nx) continue;
       double w;
       if (d.xy) {
-        w = node_area_general(quad_map(d.xy, d.nx, kx, ky), ix - 2 * kx, iy - 2 * ky);
+        w = node_area_general(quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1)), ix - 2 * kx, iy - 2 * ky);
       } else {
         const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
         w = area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
@@ -391,8 +396,8 @@ __global__ void k_strain_diag(DevState d, int cur) {
   const double ihx = 1.0 / (d.xline[kx + 1] - d.xline[kx]);
   const double ihy = 1.0 / (d.yline[ky + 1] - d.yline[ky]);
   double u[9], v[9];
-  gather9(d.vel[cur], d.nw, kx, ky, u);
-  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+  gather9(d.vel[cur], d.nw, kx, ky, u, d.flags, d.nn);
+  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v, d.flags, d.nn);
   double E11[NS], E12[NS], E22[NS];
   strain_dg<NS>(u, v, ihx, ihy, E11, E12, E22);
 #pragma unroll
@@ -413,16 +418,16 @@ __global__ void k_force_elem(DevState d) {
   double S11[NS], S12[NS], S22[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
-    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
-    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+    S11[s] = ck_ld(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S12[s] = ck_ld(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S22[s] = ck_ld(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
   }
   double fx[9], fy[9];
   element_forces_t<NS>(S11, S12, S22, hx, hy, fx, fy);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    d.fbuf[(size_t)j * d.ne + K] = fx[j];
-    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+    ck_st(d.flags, d.fbuf, (long long)j * d.ne + K, 18LL * d.ne, 106, fx[j]);
+    ck_st(d.flags, d.fbuf, (long long)(9 + j) * d.ne + K, 18LL * d.ne, 106, fy[j]);
   }
 }
 

@@ -19,14 +19,14 @@ constexpr int kGenBlock = 128;
 template <int NS, bool VAR>
 __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int cur, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
-  const QuadMap m = quad_map(d.xy, d.nx, kx, ky);
+  const QuadMap m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
   MassFactor<NS> F;
   mass_factor<NS>(m, F);
   double Pc[NS], Qc[NS], Gc[NS];
   {
     double u[9], v[9];
-    gather9(d.vel[cur], d.nw, kx, ky, u);
-    gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+    gather9(d.vel[cur], d.nw, kx, ky, u, d.flags, d.nn);
+    gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v, d.flags, d.nn);
     double E11[NS], E22[NS], Esh[NS];
     strain_general<NS>(m, F, u, v, E11, E22, Esh);
 #pragma unroll
@@ -39,32 +39,32 @@ __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int c
   double S11[NS], S12[NS], S22[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
-    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
-    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+    S11[s] = ck_ld(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S12[s] = ck_ld(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S22[s] = ck_ld(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
   }
   if constexpr (VAR) {  // DG1/DG2 H, A: ice strength per Gauss point
     constexpr int NG = DgSpace<NS>::NGP * DgSpace<NS>::NGP;
     double Phg[NG];
 #pragma unroll
-    for (int g = 0; g < NG; ++g) Phg[g] = __ldg(d.Pg + (size_t)g * d.ne + K) * r.hainv;
+    for (int g = 0; g < NG; ++g) Phg[g] = ck_ldg(d.flags, d.Pg, (long long)g * d.ne + K, (long long)NG * d.ne, 104) * r.hainv;
     relax_general<NS, true>(m, F, S11, S12, S22, Pc, Qc, Gc, 0.0, r.dmin2, r.fac, r.ie, Phg);
   } else {
-    const double Ph = __ldg(d.Pe + K) * r.hainv;
+    const double Ph = ck_ldg(d.flags, d.Pe, (long long)K, (long long)d.ne, 104) * r.hainv;
     relax_general<NS>(m, F, S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
   }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    d.S[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
-    d.S[(size_t)(1 * NS + s) * d.ne + K] = S12[s];
-    d.S[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
+    ck_st(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 105, S11[s]);
+    ck_st(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 105, S12[s]);
+    ck_st(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 105, S22[s]);
   }
   double fx[9], fy[9];
   forces_general<NS>(m, S11, S12, S22, fx, fy);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    d.fbuf[(size_t)j * d.ne + K] = fx[j];
-    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+    ck_st(d.flags, d.fbuf, (long long)j * d.ne + K, 18LL * d.ne, 106, fx[j]);
+    ck_st(d.flags, d.fbuf, (long long)(9 + j) * d.ne + K, 18LL * d.ne, 106, fy[j]);
   }
 }
 
@@ -80,12 +80,12 @@ __global__ void k_strain_diag_gen(DevState d, int cur) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
   const int ky = K / d.nx, kx = K - ky * d.nx;
-  const QuadMap m = quad_map(d.xy, d.nx, kx, ky);
+  const QuadMap m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
   MassFactor<NS> F;
   mass_factor<NS>(m, F);
   double u[9], v[9];
-  gather9(d.vel[cur], d.nw, kx, ky, u);
-  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v);
+  gather9(d.vel[cur], d.nw, kx, ky, u, d.flags, d.nn);
+  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v, d.flags, d.nn);
   double E11[NS], E22[NS], Esh[NS];
   strain_general<NS>(m, F, u, v, E11, E22, Esh);
 #pragma unroll
@@ -102,20 +102,20 @@ __global__ void k_force_elem_gen(DevState d) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
   const int ky = K / d.nx, kx = K - ky * d.nx;
-  const QuadMap m = quad_map(d.xy, d.nx, kx, ky);
+  const QuadMap m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
   double S11[NS], S12[NS], S22[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
-    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
-    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+    S11[s] = ck_ld(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S12[s] = ck_ld(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
+    S22[s] = ck_ld(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, 3LL * d.ns * d.ne, 103);
   }
   double fx[9], fy[9];
   forces_general<NS>(m, S11, S12, S22, fx, fy);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    d.fbuf[(size_t)j * d.ne + K] = fx[j];
-    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+    ck_st(d.flags, d.fbuf, (long long)j * d.ne + K, 18LL * d.ne, 106, fx[j]);
+    ck_st(d.flags, d.fbuf, (long long)(9 + j) * d.ne + K, 18LL * d.ne, 106, fy[j]);
   }
 }
 

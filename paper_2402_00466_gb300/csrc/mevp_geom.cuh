@@ -33,14 +33,16 @@
 
 namespace mevp {
 
-// The 9 values of a CG2 nodal field on element (kx, ky), local node a + 3b.
+// The 9 values of a CG2 nodal field f[0, nn) on element (kx, ky), local node
+// a + 3b (flags, nn: bounds checks of checked builds).
 __device__ __forceinline__ void gather9(const double *__restrict__ f, int nw, int kx, int ky,
-                                        double out[9]) {
-  const double *base = f + (size_t)(2 * ky) * nw + 2 * kx;
+                                        double out[9], int *flags, long long nn) {
+  const long long base = (long long)(2 * ky) * nw + 2 * kx;
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) out[a + 3 * b] = __ldg(base + (size_t)b * nw + a);
+    for (int a = 0; a < 3; ++a)
+      out[a + 3 * b] = ck_ldg(flags, f, base + (long long)b * nw + a, nn, 102);
 }
 
 // Centred bilinear map of one element.
@@ -53,10 +55,18 @@ struct QuadMap {
 };
 
 __device__ __forceinline__ QuadMap quad_map(const double2 *__restrict__ xy, int nx, int kx,
-                                            int ky) {
-  const size_t vw = (size_t)nx + 1;
-  const double2 p00 = xy[(size_t)ky * vw + kx], p10 = xy[(size_t)ky * vw + kx + 1];
-  const double2 p01 = xy[(size_t)(ky + 1) * vw + kx], p11 = xy[(size_t)(ky + 1) * vw + kx + 1];
+                                            int ky, int *flags = nullptr, long long nv = 0) {
+  const long long vw = (long long)nx + 1;
+#ifdef MEVP_CHECKED
+  const double2 p00 = ck_ld(flags, xy, ky * vw + kx, nv, 141);
+  const double2 p10 = ck_ld(flags, xy, ky * vw + kx + 1, nv, 141);
+  const double2 p01 = ck_ld(flags, xy, (ky + 1) * vw + kx, nv, 141);
+  const double2 p11 = ck_ld(flags, xy, (ky + 1) * vw + kx + 1, nv, 141);
+#else
+  (void)flags; (void)nv;
+  const double2 p00 = xy[ky * vw + kx], p10 = xy[ky * vw + kx + 1];
+  const double2 p01 = xy[(ky + 1) * vw + kx], p11 = xy[(ky + 1) * vw + kx + 1];
+#endif
   const double bx = p10.x - p00.x, by = p10.y - p00.y;  // bottom edge
   const double tx = p11.x - p01.x, ty = p11.y - p01.y;  // top edge
   const double lx = p01.x - p00.x, ly = p01.y - p00.y;  // left edge

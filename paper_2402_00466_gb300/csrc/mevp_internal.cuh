@@ -7,7 +7,20 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mevp.h"
+
+namespace mevp {
+// NVTX range over one C-ABI call (host side; shows the call in a profiler's
+// timeline, free otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace mevp
 
 struct mevp_mesh {
   int nx = 0, ny = 0;
@@ -82,6 +95,35 @@ struct DevState {
   float2 *vo2;         // [nn] ocean velocity
   float2 *lines32;     // [nx + ny] (h, 1/h) per mesh column, then per row
 };
+
+// ---- bounds-checked accesses (builds with -DMEVP_CHECKED) -----------------
+// In a checked build every global access of the subcycle, transport and
+// preparation kernels goes through these: an index outside [0, n) records
+// its site number in flags[1] (the first one wins), and the access is
+// skipped (a load returns 0).  mevp_sync reports it as MEVP_ERR_BOUNDS.  In
+// a normal build they are the plain access.
+__device__ __forceinline__ bool ck_ok(int *flags, long long i, long long n, int site) {
+#ifdef MEVP_CHECKED
+  if (i >= 0 && i < n) return true;
+  if (flags) atomicCAS(flags + 1, 0, site);
+  return false;
+#else
+  (void)flags; (void)i; (void)n; (void)site;
+  return true;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ T ck_ld(int *flags, const T *p, long long i, long long n, int site) {
+  return ck_ok(flags, i, n, site) ? p[i] : T{};
+}
+template <typename T>
+__device__ __forceinline__ T ck_ldg(int *flags, const T *p, long long i, long long n, int site) {
+  return ck_ok(flags, i, n, site) ? __ldg(p + i) : T{};
+}
+template <typename T>
+__device__ __forceinline__ void ck_st(int *flags, T *p, long long i, long long n, int site, T v) {
+  if (ck_ok(flags, i, n, site)) p[i] = v;
+}
 
 // Scalar constants of the mixed-precision kernels (FP32).
 struct MixArgs {

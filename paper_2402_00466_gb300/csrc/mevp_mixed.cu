@@ -83,11 +83,12 @@ template <int NS>
 __device__ __forceinline__ void load_stress(const DevState &d, int cur, size_t K, float S11[NS],
                                             float S12[NS], float S22[NS]) {
   const float *__restrict__ Sin = d.S32[cur];
+  const long long n = 3LL * d.ns * d.ne;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    S11[s] = __ldg(Sin + (size_t)(0 * NS + s) * d.ne + K);
-    S12[s] = __ldg(Sin + (size_t)(1 * NS + s) * d.ne + K);
-    S22[s] = __ldg(Sin + (size_t)(2 * NS + s) * d.ne + K);
+    S11[s] = ck_ldg(d.flags, Sin, (long long)(0 * NS + s) * d.ne + (long long)K, n, 152);
+    S12[s] = ck_ldg(d.flags, Sin, (long long)(1 * NS + s) * d.ne + (long long)K, n, 152);
+    S22[s] = ck_ldg(d.flags, Sin, (long long)(2 * NS + s) * d.ne + (long long)K, n, 152);
   }
 }
 
@@ -96,17 +97,20 @@ __device__ __forceinline__ void store_stress(const DevState &d, int cur, size_t 
                                              const float S11[NS], const float S12[NS],
                                              const float S22[NS]) {
   float *__restrict__ Sout = d.S32[cur ^ 1];
+  const long long n = 3LL * d.ns * d.ne;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    Sout[(size_t)(0 * NS + s) * d.ne + K] = S11[s];
-    Sout[(size_t)(1 * NS + s) * d.ne + K] = S12[s];
-    Sout[(size_t)(2 * NS + s) * d.ne + K] = S22[s];
+    ck_st(d.flags, Sout, (long long)(0 * NS + s) * d.ne + (long long)K, n, 153, S11[s]);
+    ck_st(d.flags, Sout, (long long)(1 * NS + s) * d.ne + (long long)K, n, 153, S12[s]);
+    ck_st(d.flags, Sout, (long long)(2 * NS + s) * d.ne + (long long)K, n, 153, S22[s]);
   }
 }
 
 __device__ __forceinline__ void line_geometry(const DevState &d, int kx, int ky, float &hx,
                                               float &ihx, float &hy, float &ihy) {
-  const float2 gx = __ldg(d.lines32 + kx), gy = __ldg(d.lines32 + d.nx + ky);
+  const long long nl = (long long)d.nx + d.ny;
+  const float2 gx = ck_ldg(d.flags, (const float2 *)d.lines32, kx, nl, 155);
+  const float2 gy = ck_ldg(d.flags, (const float2 *)d.lines32, (long long)d.nx + ky, nl, 155);
   hx = gx.x;
   ihx = gx.y;
   hy = gy.x;
@@ -124,18 +128,20 @@ __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs 
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) pv[c + 3 * b] = __ldg(vel + base + (size_t)b * d.nw + c);
+    for (int c = 0; c < 3; ++c)
+      pv[c + 3 * b] = ck_ldg(d.flags, vel, (long long)(base + (size_t)b * d.nw + c), d.nn, 151);
   float S11[NS], S12[NS], S22[NS];
   load_stress<NS>(d, cur, K, S11, S12, S22);
   float hx, ihx, hy, ihy;
   line_geometry(d, kx, ky, hx, ihx, hy, ihy);
   float fx[9], fy[9];
-  element_core<NS>(pv, S11, S12, S22, __ldg(d.Pe32 + K), hx, ihx, hy, ihy, a, fx, fy);
+  element_core<NS>(pv, S11, S12, S22, ck_ldg(d.flags, (const float *)d.Pe32, K, d.ne, 154), hx,
+                   ihx, hy, ihy, a, fx, fy);
   store_stress<NS>(d, cur, K, S11, S12, S22);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    d.fbuf32[(size_t)j * d.ne + K] = fx[j];
-    d.fbuf32[(size_t)(9 + j) * d.ne + K] = fy[j];
+    ck_st(d.flags, d.fbuf32, (long long)j * d.ne + K, 18LL * d.ne, 158, fx[j]);
+    ck_st(d.flags, d.fbuf32, (long long)(9 + j) * d.ne + K, 18LL * d.ne, 158, fy[j]);
   }
 }
 
@@ -193,7 +199,8 @@ __device__ __forceinline__ float4 node_update_mix(const MixArgs &ma, float4 v, f
 }
 
 __device__ __forceinline__ float2 ocean(const DevState &d, const MixArgs &ma, size_t node) {
-  return ma.has_vo ? __ldg(d.vo2 + node) : make_float2(0.f, 0.f);
+  return ma.has_vo ? ck_ldg(d.flags, (const float2 *)d.vo2, (long long)node, d.nn, 157)
+                   : make_float2(0.f, 0.f);
 }
 
 __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma, int cur) {
@@ -213,12 +220,15 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma,
       if (ix >= d.nw || iy >= d.nh) continue;
       const size_t node = (size_t)iy * d.nw + ix;
       if (ix == 0 || iy == 0 || ix == d.nw - 1 || iy == d.nh - 1) {
-        vq[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ck_st(d.flags, vq, (long long)node, d.nn, 161, make_float4(0.f, 0.f, 0.f, 0.f));
         continue;
       }
       float2 t[4];
       int n;
-      auto F = [&](int j, size_t K) { return make_float2(__ldg(fb + j * ne + K), __ldg(fb + (9 + j) * ne + K)); };
+      auto F = [&](int j, size_t K) {
+        return make_float2(ck_ldg(d.flags, fb, (long long)(j * ne + K), 18LL * ne, 158),
+                           ck_ldg(d.flags, fb, (long long)((9 + j) * ne + K), 18LL * ne, 158));
+      };
       if (dx == 0 && dy == 0) {
         const size_t Ksw = (size_t)(ky - 1) * d.nx + kx - 1, Kse = Ksw + 1;
         const size_t Knw = (size_t)ky * d.nx + kx - 1, Kne = Knw + 1;
@@ -235,7 +245,10 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma,
         t[0] = F(4, (size_t)ky * d.nx + kx);
         n = 1;
       }
-      vq[node] = node_update_mix(ma, vp[node], __ldg(d.nodec4 + node), ocean(d, ma, node), t, n);
+      ck_st(d.flags, vq, (long long)node, d.nn, 161,
+            node_update_mix(ma, ck_ld(d.flags, vp, (long long)node, d.nn, 151),
+                            ck_ldg(d.flags, (const float4 *)d.nodec4, (long long)node, d.nn, 156),
+                            ocean(d, ma, node), t, n));
     }
   }
 }
@@ -288,13 +301,14 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
     const size_t K = (size_t)ky * d.nx + kx;
     float S11[NS], S12[NS], S22[NS];
     load_stress<NS>(d, cur, K, S11, S12, S22);
-    const float P = __ldg(d.Pe32 + K);
+    const float P = ck_ldg(d.flags, (const float *)d.Pe32, (long long)K, d.ne, 154);
     const size_t base = (size_t)(2 * ky) * d.nw + 2 * kx;
     float4 pv[9];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) pv[c + 3 * b] = __ldg(vel + base + (size_t)b * d.nw + c);
+      for (int c = 0; c < 3; ++c)
+        pv[c + 3 * b] = ck_ldg(d.flags, vel, (long long)(base + (size_t)b * d.nw + c), d.nn, 151);
     float hx, ihx, hy, ihy;
     line_geometry(d, kx, ky, hx, ihx, hy, ihy);
     float fx[9], fy[9];
@@ -320,11 +334,12 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
     if (ix >= ixe || iy >= iye) continue;
     const size_t node = (size_t)iy * d.nw + ix;
     if (ix == 0 || iy == 0 || ix == d.nw - 1 || iy == d.nh - 1) {
-      vq[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+      ck_st(d.flags, vq, (long long)node, d.nn, 161, make_float4(0.f, 0.f, 0.f, 0.f));
       continue;
     }
     // local tile coordinates of the element whose lower-left node is (ix, iy)
     const int ex = (ix >> 1) - x0 + 1, ey = (iy >> 1) - y0 + 1;
+    if (!ck_ok(d.flags, ex - 1, TX - 1, 159) || !ck_ok(d.flags, ey - 1, TY - 1, 159)) continue;
     float2 tf[4];
     int n;
     const bool odd_x = ix & 1, odd_y = iy & 1;
@@ -342,15 +357,18 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
       tf[0] = fs[4][ey][ex];
       n = 1;
     }
-    vq[node] = node_update_mix(ma, sv[t], sk[t], ocean(d, ma, node), tf, n);
+    ck_st(d.flags, vq, (long long)node, d.nn, 161,
+          node_update_mix(ma, sv[t], sk[t], ocean(d, ma, node), tf, n));
   }
   // ... then the domain's last boundary column / row, owned by the last tiles
   if (ixe == d.nw)
     for (int iy = iys + tid; iy < iye; iy += TX * TY)
-      vq[(size_t)iy * d.nw + d.nw - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      ck_st(d.flags, vq, (long long)iy * d.nw + d.nw - 1, d.nn, 161,
+            make_float4(0.f, 0.f, 0.f, 0.f));
   if (iye == d.nh)
     for (int ix = ixs + tid; ix < ixe; ix += TX * TY)
-      vq[(size_t)(d.nh - 1) * d.nw + ix] = make_float4(0.f, 0.f, 0.f, 0.f);
+      ck_st(d.flags, vq, (long long)(d.nh - 1) * d.nw + ix, d.nn, 161,
+            make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
 constexpr int FTX = 32, FTY = 16;  // single-domain tile

@@ -22,7 +22,8 @@ MEVP_FP64, MEVP_MIXED = 0, 1
 FIELDS = dict(U=0, V=1, S11=2, S12=3, S22=4, E11=5, E12=6, E22=7, FORCE_X=8, FORCE_Y=9, H=10,
               A=11, NODAL_MASS=12)
 ERRORS = {-1: "MEVP_ERR_ARG", -2: "MEVP_ERR_CUDA", -3: "MEVP_ERR_OOM", -4: "MEVP_ERR_STATE",
-          -5: "MEVP_ERR_NAN", -6: "MEVP_ERR_TIMEOUT", -7: "MEVP_ERR_UNSUPPORTED"}
+          -5: "MEVP_ERR_NAN", -6: "MEVP_ERR_TIMEOUT", -7: "MEVP_ERR_UNSUPPORTED",
+          -8: "MEVP_ERR_BOUNDS"}
 PARAM_NAMES = ("Pstar", "C", "e", "DeltaMin", "alpha", "beta", "dt", "rho_ice", "rho_water",
                "Cw", "coriolis_f")
 
@@ -51,7 +52,10 @@ def load(build_if_stale: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build_if_stale else _build.LIB
+        # MEVP_LIBRARY: load another build of the same sources (the
+        # bounds-checked build of the tests) instead of the in-tree library
+        override = os.environ.get("MEVP_LIBRARY")
+        path = override if override else (_build.build() if build_if_stale else _build.LIB)
         if not os.path.exists(path):
             raise ImportError(f"libmevp.so not found at {path}; run paper_2402_00466_gb300.build")
         lib = ctypes.CDLL(path)
