@@ -371,11 +371,22 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
             make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
-constexpr int FTX = 32, FTY = 16;  // single-domain tile
+// Single-domain tile (elements per CTA, halo included) and the minimum
+// resident CTAs per SM asked of the compiler.
+#ifndef MEVP_MIX_TX
+#define MEVP_MIX_TX 32
+#endif
+#ifndef MEVP_MIX_TY
+#define MEVP_MIX_TY 16
+#endif
+#ifndef MEVP_MIX_MINB
+#define MEVP_MIX_MINB 2
+#endif
+constexpr int FTX = MEVP_MIX_TX, FTY = MEVP_MIX_TY;
 constexpr size_t kFusedSmem = Tile<FTX, FTY>::smem;
 
 template <int NS>
-__global__ void __launch_bounds__(FTX *FTY) k_subcycle_mix(DevState d, MixArgs ma, int cur) {
+__global__ void __launch_bounds__(FTX *FTY, MEVP_MIX_MINB) k_subcycle_mix(DevState d, MixArgs ma, int cur) {
   extern __shared__ float4 smem[];
   mix_tile<NS, FTX, FTY>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
 }

@@ -28,7 +28,7 @@ def test_checked_build_reports_nothing_and_matches_bitwise(tmp_path):
     lib = B.build(checked=True)
     out = tmp_path / "checked.npz"
     env = dict(os.environ, MEVP_LIBRARY=lib)
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "checked_cases.py"), str(out)],
+    r = subprocess.run([sys.executable, "-m", "tests.checked_cases", str(out)],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     checked = dict(np.load(out))
