@@ -647,7 +647,8 @@ def run_adjoint(a, torch, dist, ws, rank):
                          "flops_per_element_subcycle": per_es,
                          "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"},
             "cpu_baseline": None, "e2e": None,
-            "gpu_launches": a.steps * (n_sub * 2 * 2 + n_sub * 2 + 3),
+            # forward sweep 2n, seeds 3, recompute 2n, reverse 2n, gradients 1
+            "gpu_launches": a.steps * (6 * n_sub + 4),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
