@@ -353,11 +353,16 @@ def _roofline_for(precision, case, kt, total_ms, steps):
                      "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
                      "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
                      "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak}, **common)
-    # mixed: one fused launch per subcycle, HBM-bound
+    # mixed: one fused launch per subcycle, HBM-bound; the library takes
+    # 32x8-element tiles once they fill four rounds of CTAs per SM, else 32x4
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    big = ((case["nx"] + 29) // 31) * ((case["ny"] + 5) // 7) >= 16 * nsm
     ach = MIXED_SINGLE_PASS_BYTES[ns] * ne / el_s / 1e9
     own = MIXED_OWN_BYTES[ns] * ne / el_s / 1e9
     return dict({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                 "frac": ach / hbm_peak, "traffic": None, "kernel": f"k_subcycle_mix<{ns}>",
+                 "frac": ach / hbm_peak, "traffic": None,
+                 "kernel": f"k_subcycle_mix<{ns},32,{8 if big else 4}>",
                  "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
                  "bytes_per_element": MIXED_SINGLE_PASS_BYTES[ns],
                  "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x (v R+W, v^n, tau, m)",

@@ -134,9 +134,10 @@ MEVP_API int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int
                                size_t *bytes);
 
 /* Create a state for n_stress in {3, 6, 8} (DG1, DG2 and the 8-dof stress of
- * App. A; Gauss rule 2x2, 3x3, 3x3), n_adv = 1 (DG0 H, A) and precision
- * MEVP_FP64 or MEVP_MIXED (rectilinear meshes; general meshes take
- * MEVP_FP64, else MEVP_ERR_UNSUPPORTED), bound to the current CUDA device and to cuda_stream (a
+ * App. A; Gauss rule 2x2, 3x3, 3x3), n_adv in {1, 3, 6} (DG0, DG1, DG2 H and
+ * A; with DG1/DG2 the ice strength of Listing 1 varies over the Gauss points)
+ * and precision MEVP_FP64 or MEVP_MIXED (rectilinear meshes; general meshes
+ * take MEVP_FP64, else MEVP_ERR_UNSUPPORTED), bound to the current CUDA device and to cuda_stream (a
  * cudaStream_t; NULL = legacy default stream).  MEVP_MIXED computes strain,
  * viscosities, stress and element forces in FP32 (the FP32 stress update of
  * Sec. 4, extended to every element stage), keeps the velocity state as

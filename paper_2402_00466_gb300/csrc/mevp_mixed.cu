@@ -62,11 +62,36 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // Element step in FP32 from the 9 nodal velocity records (u_hi, u_lo, v_hi,
 // v_lo) and the element's stress (in/out): strain from pair differences
 // against the centre node, relaxed stress update, element forces.
-template <int NS>
+// The element's ice strength: P (DG0 H, A) or, with VAR, P at each Gauss
+// point (DG1/DG2 H, A), both scaled by 1/(2 alpha).
+template <int NS, bool VAR> struct Strength {
+  float Ph;
+  float Phg[VAR ? DgSpace<NS>::NGP * DgSpace<NS>::NGP : 1];
+};
+
+template <int NS, bool VAR>
+__device__ __forceinline__ Strength<NS, VAR> load_strength(const DevState &d, const MixArgs &a,
+                                                           size_t K) {
+  Strength<NS, VAR> p;
+  if constexpr (VAR) {
+    constexpr int NG = DgSpace<NS>::NGP * DgSpace<NS>::NGP;
+    p.Ph = 0.f;
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      p.Phg[g] = ck_ldg(d.flags, (const float *)d.Pg32, (long long)g * d.ne + (long long)K,
+                        (long long)NG * d.ne, 154) * a.hainv;
+  } else {
+    p.Ph = ck_ldg(d.flags, (const float *)d.Pe32, (long long)K, d.ne, 154) * a.hainv;
+    p.Phg[0] = 0.f;
+  }
+  return p;
+}
+
+template <int NS, bool VAR>
 __device__ __forceinline__ void element_core(const float4 pv[9], float S11[NS], float S12[NS],
-                                             float S22[NS], float P, float hx, float ihx,
-                                             float hy, float ihy, const MixArgs &a, float fx[9],
-                                             float fy[9]) {
+                                             float S22[NS], const Strength<NS, VAR> &P, float hx,
+                                             float ihx, float hy, float ihy, const MixArgs &a,
+                                             float fx[9], float fy[9]) {
   float du[9], dv[9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
@@ -75,7 +100,7 @@ __device__ __forceinline__ void element_core(const float4 pv[9], float S11[NS], 
   }
   float Pc[NS], Qc[NS], Gc[NS];
   strain_invariants<NS>(du, dv, ihx, ihy, a.ie, Pc, Qc, Gc);
-  relax_stress<NS>(S11, S12, S22, Pc, Qc, Gc, P * a.hainv, a.dmin2, a.fac, a.ie);
+  relax_stress_p<NS, VAR, float>(S11, S12, S22, Pc, Qc, Gc, P.Ph, P.Phg, a.dmin2, a.fac, a.ie);
   element_forces_t<NS>(S11, S12, S22, hx, hy, fx, fy);
 }
 
@@ -117,7 +142,7 @@ __device__ __forceinline__ void line_geometry(const DevState &d, int kx, int ky,
   ihy = gy.y;
 }
 
-template <int NS>
+template <int NS, bool VAR>
 __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs a, int cur) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
@@ -135,8 +160,8 @@ __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs 
   float hx, ihx, hy, ihy;
   line_geometry(d, kx, ky, hx, ihx, hy, ihy);
   float fx[9], fy[9];
-  element_core<NS>(pv, S11, S12, S22, ck_ldg(d.flags, (const float *)d.Pe32, K, d.ne, 154), hx,
-                   ihx, hy, ihy, a, fx, fy);
+  element_core<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K), hx, ihx, hy, ihy, a,
+                        fx, fy);
   store_stress<NS>(d, cur, K, S11, S12, S22);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
@@ -271,7 +296,7 @@ template <int TX, int TY> struct Tile {
   static constexpr size_t smem = sizeof(float4) * 2 * NW * NH + sizeof(float2) * 9 * TX * TY;
 };
 
-template <int NS, int TX, int TY>
+template <int NS, int TX, int TY, bool VAR = false>
 __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, int cur, int bx,
                                          int by, float4 *smem) {
   constexpr int TNW = Tile<TX, TY>::NW, TNH = Tile<TX, TY>::NH;
@@ -301,7 +326,7 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
     const size_t K = (size_t)ky * d.nx + kx;
     float S11[NS], S12[NS], S22[NS];
     load_stress<NS>(d, cur, K, S11, S12, S22);
-    const float P = ck_ldg(d.flags, (const float *)d.Pe32, (long long)K, d.ne, 154);
+    const Strength<NS, VAR> P = load_strength<NS, VAR>(d, ma, K);
     const size_t base = (size_t)(2 * ky) * d.nw + 2 * kx;
     float4 pv[9];
 #pragma unroll
@@ -312,7 +337,7 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
     float hx, ihx, hy, ihy;
     line_geometry(d, kx, ky, hx, ihx, hy, ihy);
     float fx[9], fy[9];
-    element_core<NS>(pv, S11, S12, S22, P, hx, ihx, hy, ihy, ma, fx, fy);
+    element_core<NS, VAR>(pv, S11, S12, S22, P, hx, ihx, hy, ihy, ma, fx, fy);
 #pragma unroll
     for (int j = 0; j < 9; ++j) f[j] = make_float2(fx[j], fy[j]);
     if (lx >= 1 && ly >= 1) store_stress<NS>(d, cur, K, S11, S12, S22);
@@ -371,24 +396,45 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
             make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
-// Single-domain tile (elements per CTA, halo included) and the minimum
-// resident CTAs per SM asked of the compiler.
-#ifndef MEVP_MIX_TX
-#define MEVP_MIX_TX 32
-#endif
-#ifndef MEVP_MIX_TY
-#define MEVP_MIX_TY 16
-#endif
-#ifndef MEVP_MIX_MINB
-#define MEVP_MIX_MINB 2
-#endif
-constexpr int FTX = MEVP_MIX_TX, FTY = MEVP_MIX_TY;
-constexpr size_t kFusedSmem = Tile<FTX, FTY>::smem;
-
-template <int NS>
-__global__ void __launch_bounds__(FTX *FTY, MEVP_MIX_MINB) k_subcycle_mix(DevState d, MixArgs ma, int cur) {
+// Single-domain tiles (elements per CTA, halo included), with 1024 threads
+// per SM resident (64 registers a thread).  Measured at 1024^2 DG2 (us per
+// subcycle): 32x8 82.7, 64x4 83.6, 32x4 84.0, 16x8 84.1, 32x16 87.8,
+// 64x8 90.5, 32x32 100; at 256^2 the smaller 32x4 tiles win (12.4 vs 12.7 us)
+// because 32x8 tiles no longer fill four rounds of CTAs per SM.
+template <int NS, int TX, int TY, bool VAR>
+__global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY))
+    k_subcycle_mix(DevState d, MixArgs ma, int cur) {
   extern __shared__ float4 smem[];
-  mix_tile<NS, FTX, FTY>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+  mix_tile<NS, TX, TY, VAR>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+}
+
+template <int NS, int TX, int TY>
+cudaError_t launch_fused(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {
+  const dim3 grid((d.nx + TX - 2) / (TX - 1), (d.ny + TY - 2) / (TY - 1));
+  if (d.na > 1)
+    k_subcycle_mix<NS, TX, TY, true><<<grid, dim3(TX, TY), Tile<TX, TY>::smem, st>>>(d, a, cur);
+  else
+    k_subcycle_mix<NS, TX, TY, false><<<grid, dim3(TX, TY), Tile<TX, TY>::smem, st>>>(d, a, cur);
+  return cudaGetLastError();
+}
+
+template <int NS, int TX, int TY>
+cudaError_t fused_attribute() {
+  cudaError_t e = cudaFuncSetAttribute(k_subcycle_mix<NS, TX, TY, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Tile<TX, TY>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_subcycle_mix<NS, TX, TY, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile<TX, TY>::smem);
+  return e;
+}
+
+template <int TX, int TY>
+cudaError_t fused_attributes() {
+  cudaError_t e = fused_attribute<3, TX, TY>();
+  if (e == cudaSuccess) e = fused_attribute<6, TX, TY>();
+  if (e == cudaSuccess) e = fused_attribute<8, TX, TY>();
+  return e;
 }
 
 // Ensemble: one persistent launch per subcycle over the (member, tile) work
@@ -456,7 +502,14 @@ __global__ void k_consts_to_f32(DevState d, double dt, int has_vo) {
     if (has_vo)
       d.vo2[i] = make_float2(__double2float_rn(d.vo[i]), __double2float_rn(d.vo[nn + i]));
   }
-  if (i < (size_t)d.ne) d.Pe32[i] = __double2float_rn(d.Pe[i]);
+  if (i < (size_t)d.ne) {
+    d.Pe32[i] = __double2float_rn(d.Pe[i]);
+    if (d.na > 1) {
+      const int ng = d.ns == 3 ? 4 : 9;
+      for (int g = 0; g < ng; ++g)
+        d.Pg32[(size_t)g * d.ne + i] = __double2float_rn(d.Pg[(size_t)g * d.ne + i]);
+    }
+  }
   if (i < (size_t)d.nx)
     d.lines32[i] = make_float2(__double2float_rn(d.lines[i]), __double2float_rn(d.lines[d.nx + i]));
   if (i < (size_t)d.ny)
@@ -469,29 +522,22 @@ inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
 cudaError_t setup_mixed_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_subcycle_mix<3>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kFusedSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_subcycle_mix<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kFusedSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_subcycle_mix<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kFusedSmem);
+  cudaError_t e = fused_attributes<32, 8>();
+  if (e == cudaSuccess) e = fused_attributes<32, 4>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_ens_mix<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Tile<32, 8>::smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ens_mix<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Tile<32, 16>::smem);
+    e = cudaFuncSetAttribute(k_ens_mix<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<32, 4>::smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ens_mix<64, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Tile<64, 8>::smem);
+    e = cudaFuncSetAttribute(k_ens_mix<64, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<64, 4>::smem);
   return e;
 }
 
 // Mixed ensemble tile shapes (TX, TY) the autotuner chooses from.
-const int kMixTiles[kMixTileCount][2] = {{32, 8}, {32, 16}, {64, 8}};
+const int kMixTiles[kMixTileCount][2] = {{32, 8}, {32, 4}, {64, 4}};
 
 int mixed_tile_count(int tile, int nx, int ny, int *tiles_x, int *tiles_y) {
   const int tx = kMixTiles[tile][0], ty = kMixTiles[tile][1];
@@ -507,10 +553,10 @@ cudaError_t launch_ensemble_mixed(const EnsMember *mem, const EnsWork *work, int
       k_ens_mix<32, 8><<<grid, dim3(32, 8), Tile<32, 8>::smem, st>>>(mem, work, nwork, flip);
       break;
     case 1:
-      k_ens_mix<32, 16><<<grid, dim3(32, 16), Tile<32, 16>::smem, st>>>(mem, work, nwork, flip);
+      k_ens_mix<32, 4><<<grid, dim3(32, 4), Tile<32, 4>::smem, st>>>(mem, work, nwork, flip);
       break;
     default:
-      k_ens_mix<64, 8><<<grid, dim3(64, 8), Tile<64, 8>::smem, st>>>(mem, work, nwork, flip);
+      k_ens_mix<64, 4><<<grid, dim3(64, 4), Tile<64, 4>::smem, st>>>(mem, work, nwork, flip);
       break;
   }
   return cudaGetLastError();
@@ -523,11 +569,10 @@ int mixed_tile_ctas_per_sm(int tile) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<32, 8>, 256, Tile<32, 8>::smem);
       break;
     case 1:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<32, 16>, 512,
-                                                    Tile<32, 16>::smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<32, 4>, 128, Tile<32, 4>::smem);
       break;
     default:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<64, 8>, 512, Tile<64, 8>::smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_mix<64, 4>, 256, Tile<64, 4>::smem);
       break;
   }
   return n > 0 ? n : 1;
@@ -583,24 +628,31 @@ cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_p
   const MixArgs a = make_mixargs(r, p, has_vo);
   if (ev) cudaEventRecord(ev[0], st);
   if (fused) {
-    const dim3 grid((d.nx + FTX - 2) / (FTX - 1), (d.ny + FTY - 2) / (FTY - 1));
-    const dim3 block(FTX, FTY);
+    // 32x8 tiles once they fill four rounds of CTAs on every SM, else 32x4
+    const long long big = (long long)((d.nx + 29) / 31) * ((d.ny + 5) / 7);
+    const bool small = big < 4LL * 4 * d.nsm;
+    cudaError_t e;
     if (d.ns == 3)
-      k_subcycle_mix<3><<<grid, block, kFusedSmem, st>>>(d, a, cur);
+      e = small ? launch_fused<3, 32, 4>(d, a, cur, st) : launch_fused<3, 32, 8>(d, a, cur, st);
     else if (d.ns == 6)
-      k_subcycle_mix<6><<<grid, block, kFusedSmem, st>>>(d, a, cur);
+      e = small ? launch_fused<6, 32, 4>(d, a, cur, st) : launch_fused<6, 32, 8>(d, a, cur, st);
     else
-      k_subcycle_mix<8><<<grid, block, kFusedSmem, st>>>(d, a, cur);
+      e = small ? launch_fused<8, 32, 4>(d, a, cur, st) : launch_fused<8, 32, 8>(d, a, cur, st);
     if (ev) cudaEventRecord(ev[1], st);
     if (ev) cudaEventRecord(ev[2], st);
-    return cudaGetLastError();
+    return e;
   }
+  const int eg = blocks(d.ne, kElemBlock);
+  const bool var = d.na > 1;
   if (d.ns == 3)
-    k_element_mix<3><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, a, cur);
+    var ? k_element_mix<3, true><<<eg, kElemBlock, 0, st>>>(d, a, cur)
+        : k_element_mix<3, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
   else if (d.ns == 6)
-    k_element_mix<6><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, a, cur);
+    var ? k_element_mix<6, true><<<eg, kElemBlock, 0, st>>>(d, a, cur)
+        : k_element_mix<6, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
   else
-    k_element_mix<8><<<blocks(d.ne, kElemBlock), kElemBlock, 0, st>>>(d, a, cur);
+    var ? k_element_mix<8, true><<<eg, kElemBlock, 0, st>>>(d, a, cur)
+        : k_element_mix<8, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
   k_node_mix<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, a, cur);

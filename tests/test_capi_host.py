@@ -90,13 +90,13 @@ def test_workspace_bytes_validation():
         for bad in (1, 2, 4, 7):
             with pytest.raises(mevp.MevpError):
                 mevp.mevp_state_workspace_bytes(m, bad, 1, 0)
-        # DG1/DG2 ice fields: FP64 only; their workspace holds the
-        # per-Gauss-point strength and the advection stage buffers
+        # DG1/DG2 ice fields: the workspace holds the per-Gauss-point
+        # strength (and its FP32 copy in the mixed path) and the advection
+        # stage buffers
         assert mevp.mevp_state_workspace_bytes(m, 6, 3, 0) > b6
         assert mevp.mevp_state_workspace_bytes(m, 6, 6, 0) > mevp.mevp_state_workspace_bytes(m, 6, 3, 0)
-        with pytest.raises(mevp.MevpError) as e:
-            mevp.mevp_state_workspace_bytes(m, 6, 3, 1)
-        assert e.value.code == -7
+        assert (mevp.mevp_state_workspace_bytes(m, 6, 3, 1)
+                > mevp.mevp_state_workspace_bytes(m, 6, 1, 1))
         for bad in (0, 2, 4):
             with pytest.raises(mevp.MevpError) as e:
                 mevp.mevp_state_workspace_bytes(m, 6, bad, 0)
