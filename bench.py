@@ -358,15 +358,17 @@ def _roofline_for(precision, case, kt, total_ms, steps):
     import torch
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     big = ((case["nx"] + 29) // 31) * ((case["ny"] + 5) // 7) >= 16 * nsm
-    ach = MIXED_SINGLE_PASS_BYTES[ns] * ne / el_s / 1e9
-    own = MIXED_OWN_BYTES[ns] * ne / el_s / 1e9
+    general = case.get("geometry", "uniform") != "uniform"
+    extra = 24 if general else 0  # FP32 map record (A, B, c) per element
+    ach = (MIXED_SINGLE_PASS_BYTES[ns] + extra) * ne / el_s / 1e9
+    own = (MIXED_OWN_BYTES[ns] + extra) * ne / el_s / 1e9
     return dict({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                  "frac": ach / hbm_peak, "traffic": None,
-                 "kernel": f"k_subcycle_mix<{ns},32,{8 if big else 4}>",
+                 "kernel": f"k_subcycle_mix{'_gen' if general else ''}<{ns},32,{8 if big else 4}>",
                  "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                 "bytes_per_element": MIXED_SINGLE_PASS_BYTES[ns],
+                 "bytes_per_element": MIXED_SINGLE_PASS_BYTES[ns] + extra,
                  "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x (v R+W, v^n, tau, m)",
-                 "own_bytes_per_element": MIXED_OWN_BYTES[ns],
+                 "own_bytes_per_element": MIXED_OWN_BYTES[ns] + extra,
                  "achieved_own_bytes": own, "frac_own_bytes": own / hbm_peak,
                  "fp32_TFLOPs_approx": (ELEM_FLOPS[ns] * 1.1 + 4 * 40) * ne / el_s / 1e12,
                  "fp32_peak_TFLOPs": FP32_PEAK_TFLOPS}, **common)
@@ -727,7 +729,7 @@ def _run_ours(a, torch, dist, ws, rank):
 
     variants = None
     general = case.get("geometry", "uniform") != "uniform"
-    if not a.no_variants and ws == 1 and not general:
+    if not a.no_variants and ws == 1:
         variants = {}
         other = "mixed" if a.precision == "fp64" else "fp64"
         mv = measure(mevp, torch, barrier, 1, case, other, a.steps, a.warmup, flush)
@@ -738,7 +740,7 @@ def _run_ours(a, torch, dist, ws, rank):
                                                     a.steps)}
         stable_ab = max(300.0, 4e6 / (case["L"] / nx))  # stable when alpha*h >~ 4e6 m
         variants["mixed_field_error"] = field_error(mevp, case, n_sub, stable_ab)
-        if a.workload != "mesh1024_dg2":
+        if a.workload != "mesh1024_dg2" and not general:
             big = W.make_case("mesh1024_dg2")
             for prec in ("fp64", "mixed"):
                 mb = measure(mevp, torch, barrier, 1, big, prec, 2 if prec == "fp64" else 5, 3,

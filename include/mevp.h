@@ -123,7 +123,7 @@ enum mevp_field {
  * square, evaluated on the fly per Gauss point (Sec. 3.2), and must be a
  * convex quadrilateral with counter-clockwise vertices (Jacobian determinant
  * positive at its four corners, hence everywhere), else MEVP_ERR_ARG.
- * General meshes run in FP64 only.  No device memory is allocated.
+ * No device memory is allocated.
  * nx, ny >= 1 and (2nx+1)(2ny+1) < 2^31. */
 MEVP_API int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_xy,
                      mevp_mesh **out);
@@ -136,8 +136,7 @@ MEVP_API int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int
 /* Create a state for n_stress in {3, 6, 8} (DG1, DG2 and the 8-dof stress of
  * App. A; Gauss rule 2x2, 3x3, 3x3), n_adv in {1, 3, 6} (DG0, DG1, DG2 H and
  * A; with DG1/DG2 the ice strength of Listing 1 varies over the Gauss points)
- * and precision MEVP_FP64 or MEVP_MIXED (rectilinear meshes; general meshes
- * take MEVP_FP64, else MEVP_ERR_UNSUPPORTED), bound to the current CUDA device and to cuda_stream (a
+ * and precision MEVP_FP64 or MEVP_MIXED, bound to the current CUDA device and to cuda_stream (a
  * cudaStream_t; NULL = legacy default stream).  MEVP_MIXED computes strain,
  * viscosities, stress and element forces in FP32 (the FP32 stress update of
  * Sec. 4, extended to every element stage), keeps the velocity state as

@@ -45,14 +45,15 @@ __device__ __forceinline__ void gather9(const double *__restrict__ f, int nw, in
       out[a + 3 * b] = ck_ldg(flags, f, base + (long long)b * nw + a, nn, 102);
 }
 
-// Centred bilinear map of one element.
-struct QuadMap {
-  double Ax, Ay, Bx, By, cx, cy;
+// Centred bilinear map of one element, in working precision T.
+template <typename T> struct QuadMapT {
+  T Ax, Ay, Bx, By, cx, cy;
   // det J = d0 + d1 xh + d2 eh
-  __device__ __forceinline__ double d0() const { return fma(Ax, By, -(Bx * Ay)); }
-  __device__ __forceinline__ double d1() const { return fma(Ax, cy, -(cx * Ay)); }
-  __device__ __forceinline__ double d2() const { return fma(cx, By, -(Bx * cy)); }
+  __device__ __forceinline__ T d0() const { return fma(Ax, By, -(Bx * Ay)); }
+  __device__ __forceinline__ T d1() const { return fma(Ax, cy, -(cx * Ay)); }
+  __device__ __forceinline__ T d2() const { return fma(cx, By, -(Bx * cy)); }
 };
+using QuadMap = QuadMapT<double>;
 
 __device__ __forceinline__ QuadMap quad_map(const double2 *__restrict__ xy, int nx, int kx,
                                             int ky, int *flags = nullptr, long long nv = 0) {
@@ -82,27 +83,26 @@ __device__ __forceinline__ QuadMap quad_map(const double2 *__restrict__ xy, int 
 }
 
 // Jacobian entries at 2-D Gauss point (gx, gy) of an NGP rule.
-template <int N>
-__device__ __forceinline__ void jac_at(const QuadMap &m, int gx, int gy, double &j00,
-                                       double &j01, double &j10, double &j11) {
+template <int N, typename T>
+__device__ __forceinline__ void jac_at(const QuadMapT<T> &m, int gx, int gy, T &j00, T &j01,
+                                       T &j10, T &j11) {
   const double xh = Gauss<N>::xh(gx), eh = Gauss<N>::xh(gy);
-  j00 = eh == 0.0 ? m.Ax : fma(m.cx, eh, m.Ax);
-  j10 = eh == 0.0 ? m.Ay : fma(m.cy, eh, m.Ay);
-  j01 = xh == 0.0 ? m.Bx : fma(m.cx, xh, m.Bx);
-  j11 = xh == 0.0 ? m.By : fma(m.cy, xh, m.By);
+  j00 = eh == 0.0 ? m.Ax : fma(m.cx, (T)eh, m.Ax);
+  j10 = eh == 0.0 ? m.Ay : fma(m.cy, (T)eh, m.Ay);
+  j01 = xh == 0.0 ? m.Bx : fma(m.cx, (T)xh, m.Bx);
+  j11 = xh == 0.0 ? m.By : fma(m.cy, (T)xh, m.By);
 }
 
 // Reference gradients (d/dxi, d/deta) of a Q2 field at the N x N Gauss
 // points, sum-factorised: row sums along xi, then columns along eta.
-template <int N>
-__device__ __forceinline__ void ref_grad_gauss(const double w[9], double gxi[N * N],
-                                               double geta[N * N]) {
-  double rd[3][N], r0[3][N];
+template <int N, typename T>
+__device__ __forceinline__ void ref_grad_gauss(const T w[9], T gxi[N * N], T geta[N * N]) {
+  T rd[3][N], r0[3][N];
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
     for (int gx = 0; gx < N; ++gx) {
-      double a1 = -0.0, a0 = -0.0;
+      T a1 = T(-0.0), a0 = T(-0.0);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double cd = dlq<N>(a, gx), c0 = lq<N>(a, gx);
@@ -116,7 +116,7 @@ __device__ __forceinline__ void ref_grad_gauss(const double w[9], double gxi[N *
   for (int gy = 0; gy < N; ++gy)
 #pragma unroll
     for (int gx = 0; gx < N; ++gx) {
-      double s1 = -0.0, s2 = -0.0;
+      T s1 = T(-0.0), s2 = T(-0.0);
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const double c0 = lq<N>(b, gy), cd = dlq<N>(b, gy);
@@ -130,16 +130,16 @@ __device__ __forceinline__ void ref_grad_gauss(const double w[9], double gxi[N *
 
 // Moments R_s = sum_g w_g psi_s(g) D_g of Gauss-point values D (no mass
 // scaling), sum-factorised.
-template <int NS>
-__device__ __forceinline__ void gauss_moments(const double D[DgSpace<NS>::NGP * DgSpace<NS>::NGP],
-                                              double R[NS]) {
+template <int NS, typename T>
+__device__ __forceinline__ void gauss_moments(const T D[DgSpace<NS>::NGP * DgSpace<NS>::NGP],
+                                              T R[NS]) {
   constexpr int N = DgSpace<NS>::NGP;
-  double t[3][N];
+  T t[3][N];
 #pragma unroll
   for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
     for (int gy = 0; gy < N; ++gy) {
-      double acc = -0.0;
+      T acc = T(-0.0);
       if (sidx<NS>(kx, 0) >= 0) {
 #pragma unroll
         for (int gx = 0; gx < N; ++gx) {
@@ -151,7 +151,7 @@ __device__ __forceinline__ void gauss_moments(const double D[DgSpace<NS>::NGP * 
     }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    double acc = -0.0;
+    T acc = T(-0.0);
 #pragma unroll
     for (int gy = 0; gy < N; ++gy) {
       const double c = Gauss<N>::w(gy) * pg<N>(dgy(s), gy);
@@ -164,29 +164,29 @@ __device__ __forceinline__ void gauss_moments(const double D[DgSpace<NS>::NGP * 
 // L D L^T factor of the local DG mass matrix of a bilinear element: the
 // strict lower triangle of L, row by row (L(i,k) at i(i-1)/2 + k; the unit
 // diagonal is implicit), and 1/D.
-template <int NS> struct MassFactor {
-  double L[NS * (NS - 1) / 2];
-  double Dinv[NS];
-  __device__ __forceinline__ double &at(int i, int k) { return L[i * (i - 1) / 2 + k]; }
-  __device__ __forceinline__ double at(int i, int k) const { return L[i * (i - 1) / 2 + k]; }
+template <int NS, typename T = double> struct MassFactor {
+  T L[NS * (NS - 1) / 2];
+  T Dinv[NS];
+  __device__ __forceinline__ T &at(int i, int k) { return L[i * (i - 1) / 2 + k]; }
+  __device__ __forceinline__ T at(int i, int k) const { return L[i * (i - 1) / 2 + k]; }
 };
 
-template <int NS>
-__device__ __forceinline__ void mass_factor(const QuadMap &m, MassFactor<NS> &F) {
-  const double d0 = m.d0(), d1 = m.d1(), d2 = m.d2();
-  double D[NS];
+template <int NS, typename T>
+__device__ __forceinline__ void mass_factor(const QuadMapT<T> &m, MassFactor<NS, T> &F) {
+  const T d0 = m.d0(), d1 = m.d1(), d2 = m.d2();
+  T D[NS];
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    double dj = d0 * dgmass(j);
+    T dj = d0 * (T)dgmass(j);
 #pragma unroll
     for (int k = 0; k < j; ++k) dj = fma(-F.at(j, k) * D[k], F.at(j, k), dj);
     D[j] = dj;
-    F.Dinv[j] = 1.0 / dj;
+    F.Dinv[j] = T(1) / dj;
 #pragma unroll
     for (int i = j + 1; i < NS; ++i) {
-      double a = 0.0;
-      if (mx(i, j) != 0.0) a = d1 * mx(i, j);
-      if (my(i, j) != 0.0) a = fma(d2, my(i, j), a);
+      T a = T(0);
+      if (mx(i, j) != 0.0) a = d1 * (T)mx(i, j);
+      if (my(i, j) != 0.0) a = fma(d2, (T)my(i, j), a);
 #pragma unroll
       for (int k = 0; k < j; ++k) a = fma(-F.at(i, k) * D[k], F.at(j, k), a);
       F.at(i, j) = a * F.Dinv[j];
@@ -195,8 +195,8 @@ __device__ __forceinline__ void mass_factor(const QuadMap &m, MassFactor<NS> &F)
 }
 
 // x <- M^-1 x with the factor above.
-template <int NS>
-__device__ __forceinline__ void mass_solve(const MassFactor<NS> &F, double x[NS]) {
+template <int NS, typename T>
+__device__ __forceinline__ void mass_solve(const MassFactor<NS, T> &F, T x[NS]) {
 #pragma unroll
   for (int i = 1; i < NS; ++i)
 #pragma unroll
@@ -214,14 +214,14 @@ __device__ __forceinline__ void mass_solve(const MassFactor<NS> &F, double x[NS]
 // Strain of the nodal velocities u, v as DG coefficients:
 // E11 = M^-1 int psi du/dx, E22 = M^-1 int psi dv/dy,
 // Esh = M^-1 int psi (du/dy + dv/dx)  (= 2 E12).
-template <int NS>
-__device__ __forceinline__ void strain_general(const QuadMap &m, const MassFactor<NS> &F,
-                                               const double u[9], const double v[9],
-                                               double E11[NS], double E22[NS], double Esh[NS]) {
+template <int NS, typename T>
+__device__ __forceinline__ void strain_general(const QuadMapT<T> &m, const MassFactor<NS, T> &F,
+                                               const T u[9], const T v[9], T E11[NS], T E22[NS],
+                                               T Esh[NS]) {
   constexpr int N = DgSpace<NS>::NGP, NG = N * N;
-  double D11[NG], D22[NG], Dsh[NG];
+  T D11[NG], D22[NG], Dsh[NG];
   {
-    double uxi[NG], ueta[NG], vxi[NG], veta[NG];
+    T uxi[NG], ueta[NG], vxi[NG], veta[NG];
     ref_grad_gauss<N>(u, uxi, ueta);
     ref_grad_gauss<N>(v, vxi, veta);
 #pragma unroll
@@ -229,12 +229,12 @@ __device__ __forceinline__ void strain_general(const QuadMap &m, const MassFacto
 #pragma unroll
       for (int gx = 0; gx < N; ++gx) {
         const int g = gx + N * gy;
-        double j00, j01, j10, j11;
+        T j00, j01, j10, j11;
         jac_at<N>(m, gx, gy, j00, j01, j10, j11);
         D11[g] = fma(j11, uxi[g], -(j10 * ueta[g]));  // detJ du/dx
         D22[g] = fma(j00, veta[g], -(j01 * vxi[g]));  // detJ dv/dy
-        const double duy = fma(j00, ueta[g], -(j01 * uxi[g]));
-        const double dvx = fma(j11, vxi[g], -(j10 * veta[g]));
+        const T duy = fma(j00, ueta[g], -(j01 * uxi[g]));
+        const T dvx = fma(j11, vxi[g], -(j10 * veta[g]));
         Dsh[g] = duy + dvx;
       }
   }
@@ -251,17 +251,15 @@ __device__ __forceinline__ void strain_general(const QuadMap &m, const MassFacto
 // X = Ph / sqrt(Delta^2), Ph = P/(2 alpha) (invariant form of Listing 1).
 // VAR: per-Gauss-point strength Phg (DG1/DG2 H, A), whose -P/2 term is
 // projected with the rest; otherwise the element constant Ph.
-template <int NS, bool VAR = false>
-__device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor<NS> &F,
-                                              double S11[NS], double S12[NS], double S22[NS],
-                                              const double Pc[NS], const double Qc[NS],
-                                              const double Gc[NS], double Ph, double dmin2,
-                                              double fac, double ie,
-                                              const double *Phg = nullptr) {
+template <int NS, bool VAR = false, typename T = double>
+__device__ __forceinline__ void relax_general(const QuadMapT<T> &m, const MassFactor<NS, T> &F,
+                                              T S11[NS], T S12[NS], T S22[NS], const T Pc[NS],
+                                              const T Qc[NS], const T Gc[NS], T Ph, T dmin2,
+                                              T fac, T ie, const T *Phg = nullptr) {
   constexpr int N = DgSpace<NS>::NGP, NG = N * N;
-  double RP[NS], RQ[NS], RG[NS];
+  T RP[NS], RQ[NS], RG[NS];
   {
-    double pgv[NG], qgv[NG], ggv[NG];
+    T pgv[NG], qgv[NG], ggv[NG];
     gauss_eval<NS>(Pc, pgv);
     gauss_eval<NS>(Qc, qgv);
     gauss_eval<NS>(Gc, ggv);
@@ -270,12 +268,12 @@ __device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor
 #pragma unroll
       for (int gx = 0; gx < N; ++gx) {
         const int g = gx + N * gy;
-        double j00, j01, j10, j11;
+        T j00, j01, j10, j11;
         jac_at<N>(m, gx, gy, j00, j01, j10, j11);
-        const double det = fma(j00, j11, -(j01 * j10));
-        const double d2 = fma(ggv[g], ggv[g], fma(qgv[g], qgv[g], fma(pgv[g], pgv[g], dmin2)));
-        const double Pg = VAR ? Phg[g] : Ph;
-        const double Xd = Pg * rsqrt(d2) * det;
+        const T det = fma(j00, j11, -(j01 * j10));
+        const T d2 = fma(ggv[g], ggv[g], fma(qgv[g], qgv[g], fma(pgv[g], pgv[g], dmin2)));
+        const T Pg = VAR ? Phg[g] : Ph;
+        const T Xd = Pg * rsqrt_t(d2) * det;
         pgv[g] = VAR ? fma(Xd, pgv[g], -(Pg * det)) : pgv[g] * Xd;
         qgv[g] *= Xd;
         ggv[g] *= Xd;
@@ -289,8 +287,8 @@ __device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor
   mass_solve<NS>(F, RG);
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const double base = (!VAR && s == 0) ? RP[s] - Ph : RP[s];
-    const double q = ie * RQ[s];
+    const T base = (!VAR && s == 0) ? RP[s] - Ph : RP[s];
+    const T q = ie * RQ[s];
     S11[s] = fma(fac, S11[s], base + q);
     S22[s] = fma(fac, S22[s], base - q);
     S12[s] = fma(fac, S12[s], ie * RG[s]);
@@ -299,14 +297,14 @@ __device__ __forceinline__ void relax_general(const QuadMap &m, const MassFactor
 
 // Element forces f_j = -int sigma : grad phi_j of a DG stress on a general
 // element (fx[j], fy[j] for the 9 local Q2 nodes, j = a + 3b).
-template <int NS>
-__device__ __forceinline__ void forces_general(const QuadMap &m, const double S11[NS],
-                                               const double S12[NS], const double S22[NS],
-                                               double fx[9], double fy[9]) {
+template <int NS, typename T>
+__device__ __forceinline__ void forces_general(const QuadMapT<T> &m, const T S11[NS],
+                                               const T S12[NS], const T S22[NS], T fx[9],
+                                               T fy[9]) {
   constexpr int N = DgSpace<NS>::NGP, NG = N * N;
-  double ax[NG], bx[NG], ay[NG], by[NG];
+  T ax[NG], bx[NG], ay[NG], by[NG];
   {
-    double s11[NG], s12[NG], s22[NG];
+    T s11[NG], s12[NG], s22[NG];
     gauss_eval<NS>(S11, s11);
     gauss_eval<NS>(S12, s12);
     gauss_eval<NS>(S22, s22);
@@ -315,9 +313,9 @@ __device__ __forceinline__ void forces_general(const QuadMap &m, const double S1
 #pragma unroll
       for (int gx = 0; gx < N; ++gx) {
         const int g = gx + N * gy;
-        double j00, j01, j10, j11;
+        T j00, j01, j10, j11;
         jac_at<N>(m, gx, gy, j00, j01, j10, j11);
-        const double w = Gauss<N>::w(gx) * Gauss<N>::w(gy);
+        const T w = (T)(Gauss<N>::w(gx) * Gauss<N>::w(gy));
         ax[g] = w * fma(s11[g], j11, -(s12[g] * j01));
         bx[g] = w * fma(s12[g], j00, -(s11[g] * j10));
         ay[g] = w * fma(s12[g], j11, -(s22[g] * j01));
@@ -327,10 +325,10 @@ __device__ __forceinline__ void forces_general(const QuadMap &m, const double S1
   // f_ab = -sum_gx [dL_a(gx) sum_gy L_b(gy) a_g + L_a(gx) sum_gy dL_b(gy) b_g]
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    double tax[N], tbx[N], tay[N], tby[N];
+    T tax[N], tbx[N], tay[N], tby[N];
 #pragma unroll
     for (int gx = 0; gx < N; ++gx) {
-      double p = -0.0, q = -0.0, r = -0.0, t = -0.0;
+      T p = T(-0.0), q = T(-0.0), r = T(-0.0), t = T(-0.0);
 #pragma unroll
       for (int gy = 0; gy < N; ++gy) {
         const double c0 = lq<N>(b, gy), cd = dlq<N>(b, gy);
@@ -351,7 +349,7 @@ __device__ __forceinline__ void forces_general(const QuadMap &m, const double S1
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double x = -0.0, y = -0.0;
+      T x = T(-0.0), y = T(-0.0);
 #pragma unroll
       for (int gx = 0; gx < N; ++gx) {
         const double cd = dlq<N>(a, gx), c0 = lq<N>(a, gx);

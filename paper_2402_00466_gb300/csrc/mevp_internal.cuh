@@ -92,6 +92,8 @@ struct DevState {
   float4 *vel4[2];     // [nn] (u_hi, u_lo, v_hi, v_lo) records, ping-pong
   float *Pe32;         // [ne]
   float *Pg32;         // [NGP^2][ne] (DG1/DG2 H, A)
+  float4 *map32ab;     // general mesh: [ne] (Ax, Ay, Bx, By) of the element map
+  float2 *map32c;      // general mesh: [ne] (cx, cy)
   float4 *nodec4;      // [nn] (m/dt, qx, qy, l Cw rho_w) records
   float2 *vo2;         // [nn] ocean velocity
   float2 *lines32;     // [nx + ny] (h, 1/h) per mesh column, then per row

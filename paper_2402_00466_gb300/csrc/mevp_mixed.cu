@@ -26,6 +26,7 @@
 // two-kernel variant (k_element_mix + k_node_mix) does the same arithmetic
 // through a global force buffer.
 #include "mevp_elem.cuh"
+#include "mevp_geom.cuh"
 #include "mevp_internal.cuh"
 #include "mevp_ref.cuh"
 
@@ -87,6 +88,53 @@ __device__ __forceinline__ Strength<NS, VAR> load_strength(const DevState &d, co
   return p;
 }
 
+// The same element step on a general (bilinear) element: the map in FP32
+// from the per-element record (A, B, c) of the preparation, the local mass
+// matrix factored per element (the FP64 general path's arithmetic in FP32).
+template <int NS, bool VAR>
+__device__ __forceinline__ void element_core_general(const float4 pv[9], float S11[NS],
+                                                     float S12[NS], float S22[NS],
+                                                     const Strength<NS, VAR> &P,
+                                                     const QuadMapT<float> &m, const MixArgs &a,
+                                                     float fx[9], float fy[9]) {
+  float du[9], dv[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    du[j] = __fsub_rn(pv[j].x, pv[4].x) + __fsub_rn(pv[j].y, pv[4].y);
+    dv[j] = __fsub_rn(pv[j].z, pv[4].z) + __fsub_rn(pv[j].w, pv[4].w);
+  }
+  MassFactor<NS, float> F;
+  mass_factor<NS>(m, F);
+  float Pc[NS], Qc[NS], Gc[NS];
+  {
+    float E11[NS], E22[NS], Esh[NS];
+    strain_general<NS>(m, F, du, dv, E11, E22, Esh);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Pc[s] = E11[s] + E22[s];
+      Qc[s] = a.ie * (E11[s] - E22[s]);
+      Gc[s] = a.ie * Esh[s];
+    }
+  }
+  relax_general<NS, VAR, float>(m, F, S11, S12, S22, Pc, Qc, Gc, P.Ph, a.dmin2, a.fac, a.ie,
+                                P.Phg);
+  forces_general<NS>(m, S11, S12, S22, fx, fy);
+}
+
+// FP32 map record of a general element: (Ax, Ay, Bx, By) and (cx, cy).
+__device__ __forceinline__ QuadMapT<float> map_record(const DevState &d, size_t K) {
+  const float4 ab = ck_ldg(d.flags, (const float4 *)d.map32ab, (long long)K, d.ne, 162);
+  const float2 c = ck_ldg(d.flags, (const float2 *)d.map32c, (long long)K, d.ne, 162);
+  QuadMapT<float> m;
+  m.Ax = ab.x;
+  m.Ay = ab.y;
+  m.Bx = ab.z;
+  m.By = ab.w;
+  m.cx = c.x;
+  m.cy = c.y;
+  return m;
+}
+
 template <int NS, bool VAR>
 __device__ __forceinline__ void element_core(const float4 pv[9], float S11[NS], float S12[NS],
                                              float S22[NS], const Strength<NS, VAR> &P, float hx,
@@ -142,7 +190,7 @@ __device__ __forceinline__ void line_geometry(const DevState &d, int kx, int ky,
   ihy = gy.y;
 }
 
-template <int NS, bool VAR>
+template <int NS, bool VAR, bool GEN>
 __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs a, int cur) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
@@ -157,11 +205,16 @@ __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs 
       pv[c + 3 * b] = ck_ldg(d.flags, vel, (long long)(base + (size_t)b * d.nw + c), d.nn, 151);
   float S11[NS], S12[NS], S22[NS];
   load_stress<NS>(d, cur, K, S11, S12, S22);
-  float hx, ihx, hy, ihy;
-  line_geometry(d, kx, ky, hx, ihx, hy, ihy);
   float fx[9], fy[9];
-  element_core<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K), hx, ihx, hy, ihy, a,
-                        fx, fy);
+  if constexpr (GEN) {
+    element_core_general<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K),
+                                  map_record(d, K), a, fx, fy);
+  } else {
+    float hx, ihx, hy, ihy;
+    line_geometry(d, kx, ky, hx, ihx, hy, ihy);
+    element_core<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K), hx, ihx, hy, ihy,
+                          a, fx, fy);
+  }
   store_stress<NS>(d, cur, K, S11, S12, S22);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
@@ -296,7 +349,7 @@ template <int TX, int TY> struct Tile {
   static constexpr size_t smem = sizeof(float4) * 2 * NW * NH + sizeof(float2) * 9 * TX * TY;
 };
 
-template <int NS, int TX, int TY, bool VAR = false>
+template <int NS, int TX, int TY, bool VAR = false, bool GEN = false>
 __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, int cur, int bx,
                                          int by, float4 *smem) {
   constexpr int TNW = Tile<TX, TY>::NW, TNH = Tile<TX, TY>::NH;
@@ -334,10 +387,14 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         pv[c + 3 * b] = ck_ldg(d.flags, vel, (long long)(base + (size_t)b * d.nw + c), d.nn, 151);
-    float hx, ihx, hy, ihy;
-    line_geometry(d, kx, ky, hx, ihx, hy, ihy);
     float fx[9], fy[9];
-    element_core<NS, VAR>(pv, S11, S12, S22, P, hx, ihx, hy, ihy, ma, fx, fy);
+    if constexpr (GEN) {
+      element_core_general<NS, VAR>(pv, S11, S12, S22, P, map_record(d, K), ma, fx, fy);
+    } else {
+      float hx, ihx, hy, ihy;
+      line_geometry(d, kx, ky, hx, ihx, hy, ihy);
+      element_core<NS, VAR>(pv, S11, S12, S22, P, hx, ihx, hy, ihy, ma, fx, fy);
+    }
 #pragma unroll
     for (int j = 0; j < 9; ++j) f[j] = make_float2(fx[j], fy[j]);
     if (lx >= 1 && ly >= 1) store_stress<NS>(d, cur, K, S11, S12, S22);
@@ -408,24 +465,40 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY))
   mix_tile<NS, TX, TY, VAR>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
 }
 
+// General (bilinear) elements: the per-element mass factorisation needs more
+// registers, so half as many threads per SM (128 registers a thread).
+template <int NS, int TX, int TY, bool VAR>
+__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
+    k_subcycle_mix_gen(DevState d, MixArgs ma, int cur) {
+  extern __shared__ float4 smem[];
+  mix_tile<NS, TX, TY, VAR, true>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+}
+
 template <int NS, int TX, int TY>
 cudaError_t launch_fused(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {
   const dim3 grid((d.nx + TX - 2) / (TX - 1), (d.ny + TY - 2) / (TY - 1));
-  if (d.na > 1)
-    k_subcycle_mix<NS, TX, TY, true><<<grid, dim3(TX, TY), Tile<TX, TY>::smem, st>>>(d, a, cur);
-  else
-    k_subcycle_mix<NS, TX, TY, false><<<grid, dim3(TX, TY), Tile<TX, TY>::smem, st>>>(d, a, cur);
+  const size_t sm = Tile<TX, TY>::smem;
+  if (d.xy) {
+    if (d.na > 1)
+      k_subcycle_mix_gen<NS, TX, TY, true><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+    else
+      k_subcycle_mix_gen<NS, TX, TY, false><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+  } else if (d.na > 1) {
+    k_subcycle_mix<NS, TX, TY, true><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+  } else {
+    k_subcycle_mix<NS, TX, TY, false><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+  }
   return cudaGetLastError();
 }
 
 template <int NS, int TX, int TY>
 cudaError_t fused_attribute() {
-  cudaError_t e = cudaFuncSetAttribute(k_subcycle_mix<NS, TX, TY, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Tile<TX, TY>::smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_subcycle_mix<NS, TX, TY, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile<TX, TY>::smem);
+  const int sm = (int)Tile<TX, TY>::smem;
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_subcycle_mix<NS, TX, TY, false>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix<NS, TX, TY, true>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix_gen<NS, TX, TY, false>, at, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix_gen<NS, TX, TY, true>, at, sm);
   return e;
 }
 
@@ -509,6 +582,13 @@ __global__ void k_consts_to_f32(DevState d, double dt, int has_vo) {
       for (int g = 0; g < ng; ++g)
         d.Pg32[(size_t)g * d.ne + i] = __double2float_rn(d.Pg[(size_t)g * d.ne + i]);
     }
+  }
+  if (d.xy && i < (size_t)d.ne) {  // general mesh: FP32 map record per element
+    const int ky = (int)(i / d.nx), kx = (int)(i - (size_t)ky * d.nx);
+    const QuadMap m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
+    d.map32ab[i] = make_float4(__double2float_rn(m.Ax), __double2float_rn(m.Ay),
+                               __double2float_rn(m.Bx), __double2float_rn(m.By));
+    d.map32c[i] = make_float2(__double2float_rn(m.cx), __double2float_rn(m.cy));
   }
   if (i < (size_t)d.nx)
     d.lines32[i] = make_float2(__double2float_rn(d.lines[i]), __double2float_rn(d.lines[d.nx + i]));
@@ -622,6 +702,25 @@ MixArgs make_mixargs(const Rheo &r, const mevp_params &p, bool has_vo) {
   return a;
 }
 
+template <int NS, bool VAR>
+void launch_element_mix_ns(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {
+  const int eg = blocks(d.ne, kElemBlock);
+  if (d.xy)
+    k_element_mix<NS, VAR, true><<<eg, kElemBlock, 0, st>>>(d, a, cur);
+  else
+    k_element_mix<NS, VAR, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
+}
+
+void launch_element_mix(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {
+  const bool var = d.na > 1;
+  if (d.ns == 3)
+    var ? launch_element_mix_ns<3, true>(d, a, cur, st) : launch_element_mix_ns<3, false>(d, a, cur, st);
+  else if (d.ns == 6)
+    var ? launch_element_mix_ns<6, true>(d, a, cur, st) : launch_element_mix_ns<6, false>(d, a, cur, st);
+  else
+    var ? launch_element_mix_ns<8, true>(d, a, cur, st) : launch_element_mix_ns<8, false>(d, a, cur, st);
+}
+
 cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
                                   bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
                                   bool fused) {
@@ -642,17 +741,7 @@ cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_p
     if (ev) cudaEventRecord(ev[2], st);
     return e;
   }
-  const int eg = blocks(d.ne, kElemBlock);
-  const bool var = d.na > 1;
-  if (d.ns == 3)
-    var ? k_element_mix<3, true><<<eg, kElemBlock, 0, st>>>(d, a, cur)
-        : k_element_mix<3, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
-  else if (d.ns == 6)
-    var ? k_element_mix<6, true><<<eg, kElemBlock, 0, st>>>(d, a, cur)
-        : k_element_mix<6, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
-  else
-    var ? k_element_mix<8, true><<<eg, kElemBlock, 0, st>>>(d, a, cur)
-        : k_element_mix<8, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
+  launch_element_mix(d, a, cur, st);
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
   k_node_mix<<<blocks(slots, kNodeBlock), kNodeBlock, 0, st>>>(d, a, cur);
