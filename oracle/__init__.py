@@ -72,17 +72,17 @@ def _lib(openmp: bool = False):
             lib.orc_ngp.argtypes = [i]
             lib.orc_dg_basis.argtypes = [i, ctypes.c_double, ctypes.c_double, dp]
             lib.orc_q2_basis.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp, dp]
-            lib.orc_subcycles.argtypes = [i, i, dp, i, i, pp, dp, dp, dp, dp, dp, dp, dp, i,
+            lib.orc_subcycles.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp, dp, dp, dp, dp, i,
                                           dp, dp, dp, dp]
-            lib.orc_strain.argtypes = [i, i, dp, i, dp, dp]
-            lib.orc_stress.argtypes = [i, i, dp, i, i, pp, dp, dp, dp, dp]
-            lib.orc_divergence.argtypes = [i, i, dp, i, dp, dp, dp]
-            lib.orc_lumped.argtypes = [i, i, dp, i, i, pp, dp, dp, dp]
+            lib.orc_strain.argtypes = [i, i, dp, i, i, dp, dp]
+            lib.orc_stress.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp, dp]
+            lib.orc_divergence.argtypes = [i, i, dp, i, i, dp, dp, dp]
+            lib.orc_lumped.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp]
             lib.orc_velocity.argtypes = [i, i, pp, dp, dp, dp, dp, dp, dp, dp, dp]
-            lib.orc_element_map.argtypes = [i, i, dp, i, i, dp, dp]
+            lib.orc_element_map.argtypes = [i, i, dp, i, i, i, dp, dp]
             lib.orc_max_threads.argtypes = []
-            lib.orc_advect.argtypes = [i, i, dp, i, dp, ctypes.c_double, i, dp, dp]
-            lib.orc_advect_operator.argtypes = [i, i, dp, i, dp, dp, dp, dp, dp]
+            lib.orc_advect.argtypes = [i, i, dp, i, i, dp, ctypes.c_double, i, dp, dp]
+            lib.orc_advect_operator.argtypes = [i, i, dp, i, i, dp, dp, dp, dp, dp]
             _handles[openmp] = lib
         return _handles[openmp]
 
@@ -105,6 +105,18 @@ def _check(rc, what):
 
 def sizes(nx, ny):
     return nx * ny, (2 * nx + 1) * (2 * ny + 1)
+
+
+def _geo(nx, ny, xy):
+    """(array, mode) of a mesh's geometry: vertices [(nx+1)(ny+1)][2] give
+    bilinear element maps (mode 0), CG2 node positions [(2nx+1)(2ny+1)][2]
+    give isoparametric Q2 element maps (mode 1)."""
+    a = _c(xy).reshape(-1, 2)
+    if a.shape[0] == (nx + 1) * (ny + 1):
+        return a, 0
+    if a.shape[0] == (2 * nx + 1) * (2 * ny + 1):
+        return a, 1
+    raise ValueError(f"geometry of {a.shape[0]} points fits neither the vertices nor the nodes")
 
 
 def uniform_vertices(nx, ny, Lx, Ly):
@@ -153,14 +165,16 @@ def _adv_in(H, n_a, ne):
 def element_map(nx, ny, xy, n_s, K):
     ng = ngp(n_s) ** 2
     det = np.zeros(ng); m = np.zeros(n_s * ng)
-    _check(_lib().orc_element_map(nx, ny, _p(_c(xy)), n_s, K, _p(det), _p(m)), "element_map")
+    g, mode = _geo(nx, ny, xy)
+    _check(_lib().orc_element_map(nx, ny, _p(g), mode, n_s, K, _p(det), _p(m)), "element_map")
     return det, m.reshape(n_s, ng)
 
 
 def strain(nx, ny, xy, n_s, vel):
     ne, nn = sizes(nx, ny)
     E = np.zeros(3 * ne * n_s)
-    _check(_lib().orc_strain(nx, ny, _p(_c(xy)), n_s, _p(_c(vel).reshape(-1)), _p(E)), "strain")
+    g, mode = _geo(nx, ny, xy)
+    _check(_lib().orc_strain(nx, ny, _p(g), mode, n_s, _p(_c(vel).reshape(-1)), _p(E)), "strain")
     return _dg_out(E, n_s, ne)
 
 
@@ -168,7 +182,8 @@ def stress(nx, ny, xy, n_s, n_a, params, E, H, A, S):
     ne, nn = sizes(nx, ny)
     Sc = _dg_in(S, n_s, ne)
     prm = Params.from_dict(params)
-    _check(_lib().orc_stress(nx, ny, _p(_c(xy)), n_s, n_a, ctypes.byref(prm),
+    g, mode = _geo(nx, ny, xy)
+    _check(_lib().orc_stress(nx, ny, _p(g), mode, n_s, n_a, ctypes.byref(prm),
                              _p(_dg_in(E, n_s, ne)), _p(_adv_in(H, n_a, ne)),
                              _p(_adv_in(A, n_a, ne)), _p(Sc)), "stress")
     return _dg_out(Sc, n_s, ne)
@@ -178,7 +193,8 @@ def divergence(nx, ny, xy, n_s, S, return_element_forces=False):
     ne, nn = sizes(nx, ny)
     F = np.zeros(2 * nn)
     fel = np.zeros(18 * ne)
-    _check(_lib().orc_divergence(nx, ny, _p(_c(xy)), n_s, _p(_dg_in(S, n_s, ne)), _p(F), _p(fel)),
+    g, mode = _geo(nx, ny, xy)
+    _check(_lib().orc_divergence(nx, ny, _p(g), mode, n_s, _p(_dg_in(S, n_s, ne)), _p(F), _p(fel)),
            "divergence")
     if return_element_forces:
         return F.reshape(2, nn), fel.reshape(ne, 18)
@@ -189,7 +205,8 @@ def lumped(nx, ny, xy, n_s, n_a, params, H):
     ne, nn = sizes(nx, ny)
     m = np.zeros(nn); l = np.zeros(nn)
     prm = Params.from_dict(params)
-    _check(_lib().orc_lumped(nx, ny, _p(_c(xy)), n_s, n_a, ctypes.byref(prm),
+    g, mode = _geo(nx, ny, xy)
+    _check(_lib().orc_lumped(nx, ny, _p(g), mode, n_s, n_a, ctypes.byref(prm),
                              _p(_adv_in(H, n_a, ne)), _p(m), _p(l)), "lumped")
     return m, l
 
@@ -220,8 +237,9 @@ def subcycles(nx, ny, xy, n_s, n_a, params, H, A, tau, vel0, S0, n_sub, vn=None,
     F = np.zeros(2 * nn) if want_last else None
     fel = np.zeros(18 * ne) if want_last else None
     ph = np.zeros(4)
+    g, mode = _geo(nx, ny, xy)
     rc = _lib(openmp).orc_subcycles(
-        nx, ny, _p(_c(xy)), n_s, n_a, ctypes.byref(prm), _p(_adv_in(H, n_a, ne)),
+        nx, ny, _p(g), mode, n_s, n_a, ctypes.byref(prm), _p(_adv_in(H, n_a, ne)),
         _p(_adv_in(A, n_a, ne)), _p(_c(tau).reshape(-1)),
         None if vo is None else _p(_c(vo).reshape(-1)), _p(vn_), _p(vel), _p(Sc), int(n_sub),
         _p(E), _p(F), _p(fel), _p(ph))
@@ -243,7 +261,8 @@ def advect(nx, ny, xy, n_a, vel, dt, n_steps, H, A, openmp=False):
     velocity vel (2, N_n) held fixed; returns (H, A)."""
     ne, nn = sizes(nx, ny)
     Hc, Ac = _adv_in(H, n_a, ne).copy(), _adv_in(A, n_a, ne).copy()
-    _check(_lib(openmp).orc_advect(nx, ny, _p(_c(xy)), n_a, _p(_c(vel).reshape(-1)), float(dt),
+    g, mode = _geo(nx, ny, xy)
+    _check(_lib(openmp).orc_advect(nx, ny, _p(g), mode, n_a, _p(_c(vel).reshape(-1)), float(dt),
                                    int(n_steps), _p(Hc), _p(Ac)), "advect")
     return np.ascontiguousarray(Hc.T), np.ascontiguousarray(Ac.T)
 
@@ -252,7 +271,8 @@ def advect_operator(nx, ny, xy, n_a, vel, H, A):
     """The semi-discrete operator L = M^-1 R applied to (H, A); (n_a, N_e) each."""
     ne, nn = sizes(nx, ny)
     LH = np.zeros(ne * n_a); LA = np.zeros(ne * n_a)
-    _check(_lib().orc_advect_operator(nx, ny, _p(_c(xy)), n_a, _p(_c(vel).reshape(-1)),
+    g, mode = _geo(nx, ny, xy)
+    _check(_lib().orc_advect_operator(nx, ny, _p(g), mode, n_a, _p(_c(vel).reshape(-1)),
                                       _p(_adv_in(H, n_a, ne)), _p(_adv_in(A, n_a, ne)),
                                       _p(LH), _p(LA)), "advect_operator")
     return (np.ascontiguousarray(LH.reshape(ne, n_a).T),

@@ -181,7 +181,9 @@ int orc_q2_basis(double xi, double eta, double *phi, double *dxi, double *deta) 
  * ---------------------------------------------------------------------- */
 typedef struct {
   int nx, ny, n_s, n_a, ngp, ng;
-  const double *xy;  /* vertices */
+  int geo;           /* 0: xy holds the vertices (bilinear Q1 element maps);
+                        1: xy holds the CG2 node positions (isoparametric Q2 maps) */
+  const double *xy;  /* vertices [N_v][2] or CG2 nodes [N_n][2] */
   double gx[4], gw[4];
   double psi_s[MAXS][MAXG]; /* DG stress basis at the Gauss points */
   double psi_a[MAXS][MAXG]; /* DG advection basis at the Gauss points */
@@ -230,13 +232,14 @@ static int invert_spd(int n, double *m /* n*n, overwritten by inverse */) {
   return ORC_OK;
 }
 
-static int mesh_init(mesh_t *M, int nx, int ny, const double *xy, int n_s, int n_a) {
+static int mesh_init(mesh_t *M, int nx, int ny, const double *xy, int geo, int n_s, int n_a) {
   if (nx < 1 || ny < 1 || !xy) return ORC_ERR_ARG;
   int ngp = orc_ngp(n_s);
   if (ngp < 0) return ORC_ERR_ARG;
   if (!(n_a == 1 || n_a == 3 || n_a == 6)) return ORC_ERR_ARG;
   M->nx = nx; M->ny = ny; M->n_s = n_s; M->n_a = n_a; M->ngp = ngp; M->ng = ngp * ngp;
   M->xy = xy;
+  M->geo = geo;
   orc_gauss(ngp, M->gx, M->gw);
   for (int gy = 0; gy < ngp; ++gy)
     for (int gx = 0; gx < ngp; ++gx) {
@@ -254,7 +257,7 @@ static int mesh_init(mesh_t *M, int nx, int ny, const double *xy, int n_s, int n
 
 static int elem_geometry(const mesh_t *M, int K, elem_t *E) {
   int kx = K % M->nx, ky = K / M->nx;
-  int vw = M->nx + 1;
+  int vw = M->nx + 1, nw = 2 * M->nx + 1;
   const double *x00 = M->xy + 2 * (ky * vw + kx);
   const double *x10 = M->xy + 2 * (ky * vw + kx + 1);
   const double *x01 = M->xy + 2 * ((ky + 1) * vw + kx);
@@ -264,13 +267,29 @@ static int elem_geometry(const mesh_t *M, int K, elem_t *E) {
     for (int gx = 0; gx < ngp; ++gx) {
       int g = gx + ngp * gy;
       double xi = M->gx[gx], eta = M->gx[gy];
-      /* derivatives of the bilinear shape functions */
-      double d00x = -(1.0 - eta), d10x = (1.0 - eta), d01x = -eta, d11x = eta;
-      double d00e = -(1.0 - xi), d10e = -xi, d01e = (1.0 - xi), d11e = xi;
-      double J00 = d00x * x00[0] + d10x * x10[0] + d01x * x01[0] + d11x * x11[0]; /* dx/dxi  */
-      double J01 = d00e * x00[0] + d10e * x10[0] + d01e * x01[0] + d11e * x11[0]; /* dx/deta */
-      double J10 = d00x * x00[1] + d10x * x10[1] + d01x * x01[1] + d11x * x11[1]; /* dy/dxi  */
-      double J11 = d00e * x00[1] + d10e * x10[1] + d01e * x01[1] + d11e * x11[1]; /* dy/deta */
+      double J00, J01, J10, J11;
+      if (M->geo) {
+        /* isoparametric map: x = sum_j x_j phi_j over the 9 CG2 nodes of the
+           element (Sec. 2.1: the element map from the velocity's space) */
+        J00 = J01 = J10 = J11 = 0.0;
+        for (int b = 0; b < 3; ++b)
+          for (int a = 0; a < 3; ++a) {
+            int j = a + 3 * b;
+            const double *xn = M->xy + 2 * ((2 * ky + b) * nw + 2 * kx + a);
+            J00 += xn[0] * M->q2x[g][j];
+            J01 += xn[0] * M->q2e[g][j];
+            J10 += xn[1] * M->q2x[g][j];
+            J11 += xn[1] * M->q2e[g][j];
+          }
+      } else {
+        /* derivatives of the bilinear shape functions */
+        double d00x = -(1.0 - eta), d10x = (1.0 - eta), d01x = -eta, d11x = eta;
+        double d00e = -(1.0 - xi), d10e = -xi, d01e = (1.0 - xi), d11e = xi;
+        J00 = d00x * x00[0] + d10x * x10[0] + d01x * x01[0] + d11x * x11[0]; /* dx/dxi  */
+        J01 = d00e * x00[0] + d10e * x10[0] + d01e * x01[0] + d11e * x11[0]; /* dx/deta */
+        J10 = d00x * x00[1] + d10x * x10[1] + d01x * x01[1] + d11x * x11[1]; /* dy/dxi  */
+        J11 = d00e * x00[1] + d10e * x10[1] + d01e * x01[1] + d11e * x11[1]; /* dy/deta */
+      }
       double det = J00 * J11 - J01 * J10;
       if (!(det > 0.0)) return ORC_ERR_ARG;
       E->detJ[g] = det;
@@ -295,7 +314,6 @@ static int elem_geometry(const mesh_t *M, int K, elem_t *E) {
       for (int t = 0; t < n_s; ++t) acc += mass[s * n_s + t] * E->wdet[g] * M->psi_s[t][g];
       E->iMJwPSI[s][g] = acc;
     }
-  int nw = 2 * M->nx + 1;
   for (int b = 0; b < 3; ++b)
     for (int a = 0; a < 3; ++a) E->node[a + 3 * b] = (2 * ky + b) * nw + 2 * kx + a;
   return ORC_OK;
@@ -555,13 +573,13 @@ static double now_s(void) {
  *   E_last [3][N_e][n_s], F_last [2][N_n], fel_last [N_e][18]: optional
  *   outputs of the last subcycle; phase_sec[4] (optional) accumulates the
  *   time of strain / stress / divergence / velocity.                        */
-int orc_subcycles(int nx, int ny, const double *xy, int n_s, int n_a, const orc_params *p,
+int orc_subcycles(int nx, int ny, const double *xy, int geo, int n_s, int n_a, const orc_params *p,
                   const double *H, const double *A, const double *tau, const double *vo,
                   const double *vn, double *vel, double *S, int n_sub, double *E_last,
                   double *F_last, double *fel_last, double *phase_sec) {
   mesh_t M;
   if (!p || !H || !A || !tau || !vn || !vel || !S || n_sub < 0) return ORC_ERR_ARG;
-  int rc = mesh_init(&M, nx, ny, xy, n_s, n_a);
+  int rc = mesh_init(&M, nx, ny, xy, geo, n_s, n_a);
   if (rc) return rc;
   size_t ne = (size_t)nx * ny, nn = (size_t)(2 * nx + 1) * (2 * ny + 1);
   double *E = (double *)malloc(sizeof(double) * 3 * ne * n_s);
@@ -600,33 +618,33 @@ int orc_subcycles(int nx, int ny, const double *xy, int n_s, int n_a, const orc_
 }
 
 /* Single stages, for the pins. */
-int orc_strain(int nx, int ny, const double *xy, int n_s, const double *vel, double *E) {
+int orc_strain(int nx, int ny, const double *xy, int geo, int n_s, const double *vel, double *E) {
   mesh_t M;
-  int rc = mesh_init(&M, nx, ny, xy, n_s, 1);
+  int rc = mesh_init(&M, nx, ny, xy, geo, n_s, 1);
   if (rc) return rc;
   return stage_strain(&M, vel, E);
 }
 
-int orc_stress(int nx, int ny, const double *xy, int n_s, int n_a, const orc_params *p,
+int orc_stress(int nx, int ny, const double *xy, int geo, int n_s, int n_a, const orc_params *p,
                const double *E, const double *H, const double *A, double *S) {
   mesh_t M;
-  int rc = mesh_init(&M, nx, ny, xy, n_s, n_a);
+  int rc = mesh_init(&M, nx, ny, xy, geo, n_s, n_a);
   if (rc) return rc;
   return stage_stress(&M, p, E, H, A, S);
 }
 
-int orc_divergence(int nx, int ny, const double *xy, int n_s, const double *S, double *F,
+int orc_divergence(int nx, int ny, const double *xy, int geo, int n_s, const double *S, double *F,
                    double *fel) {
   mesh_t M;
-  int rc = mesh_init(&M, nx, ny, xy, n_s, 1);
+  int rc = mesh_init(&M, nx, ny, xy, geo, n_s, 1);
   if (rc) return rc;
   return stage_divergence(&M, S, F, fel);
 }
 
-int orc_lumped(int nx, int ny, const double *xy, int n_s, int n_a, const orc_params *p,
+int orc_lumped(int nx, int ny, const double *xy, int geo, int n_s, int n_a, const orc_params *p,
                const double *H, double *m, double *l) {
   mesh_t M;
-  int rc = mesh_init(&M, nx, ny, xy, n_s, n_a);
+  int rc = mesh_init(&M, nx, ny, xy, geo, n_s, n_a);
   if (rc) return rc;
   return lumped(&M, p, H, m, l);
 }
@@ -642,11 +660,11 @@ int orc_velocity(int nx, int ny, const orc_params *p, const double *F, const dou
 }
 
 /* Geometry of one element for the pins: detJ and iMJwPSI at the Gauss points. */
-int orc_element_map(int nx, int ny, const double *xy, int n_s, int K, double *detJ,
+int orc_element_map(int nx, int ny, const double *xy, int geo, int n_s, int K, double *detJ,
                     double *iMJwPSI /* n_s x n_g */) {
   mesh_t M;
   elem_t G;
-  int rc = mesh_init(&M, nx, ny, xy, n_s, 1);
+  int rc = mesh_init(&M, nx, ny, xy, geo, n_s, 1);
   if (rc) return rc;
   if (K < 0 || K >= nx * ny) return ORC_ERR_ARG;
   rc = elem_geometry(&M, K, &G);
@@ -699,6 +717,7 @@ static int adv_nq(int n_a) { return n_a == 6 ? 4 : 3; }
 
 typedef struct {
   int nx, ny, n_a, nq;
+  int geo;            /* as in mesh_t: vertices (0) or CG2 nodes (1) */
   const double *xy;
   double qx[4], qw[4];
 } adv_t;
@@ -706,6 +725,22 @@ typedef struct {
 /* Jacobian of element K at reference point (xi, eta). */
 static void adv_jac(const adv_t *P, int K, double xi, double eta, double J[4]) {
   int kx = K % P->nx, ky = K / P->nx, vw = P->nx + 1;
+  if (P->geo) { /* isoparametric Q2 map of the 9 CG2 nodes */
+    int nw = 2 * P->nx + 1;
+    double dxi[9], deta[9];
+    orc_q2_basis(xi, eta, NULL, dxi, deta);
+    J[0] = J[1] = J[2] = J[3] = 0.0;
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) {
+        int j = a + 3 * b;
+        const double *xn = P->xy + 2 * ((2 * ky + b) * nw + 2 * kx + a);
+        for (int c = 0; c < 2; ++c) {
+          J[2 * c + 0] += xn[c] * dxi[j];
+          J[2 * c + 1] += xn[c] * deta[j];
+        }
+      }
+    return;
+  }
   const double *x00 = P->xy + 2 * (ky * vw + kx);
   const double *x10 = P->xy + 2 * (ky * vw + kx + 1);
   const double *x01 = P->xy + 2 * ((ky + 1) * vw + kx);
@@ -843,12 +878,12 @@ static int adv_operator(const adv_t *P, const double *vel, const double *H, cons
 
 /* n_steps advection steps of length dt (SSP Runge-Kutta of order n_a's
  * degree + 1), H and A [N_e][n_a] in/out, vel [2][N_n] fixed. */
-int orc_advect(int nx, int ny, const double *xy, int n_a, const double *vel, double dt,
+int orc_advect(int nx, int ny, const double *xy, int geo, int n_a, const double *vel, double dt,
                int n_steps, double *H, double *A) {
   if (nx < 1 || ny < 1 || !xy || !vel || !H || !A || n_steps < 0) return ORC_ERR_ARG;
   if (!(n_a == 1 || n_a == 3 || n_a == 6)) return ORC_ERR_ARG;
   adv_t P;
-  P.nx = nx; P.ny = ny; P.n_a = n_a; P.nq = adv_nq(n_a); P.xy = xy;
+  P.nx = nx; P.ny = ny; P.n_a = n_a; P.nq = adv_nq(n_a); P.xy = xy; P.geo = geo;
   orc_gauss(P.nq, P.qx, P.qw);
   size_t n = (size_t)nx * ny * n_a;
   double *LH = (double *)malloc(sizeof(double) * n), *LA = (double *)malloc(sizeof(double) * n);
@@ -892,12 +927,12 @@ int orc_advect(int nx, int ny, const double *xy, int n_a, const double *vel, dou
 }
 
 /* The semi-discrete operator alone, L(H) = M^-1 R(H) (for the pins). */
-int orc_advect_operator(int nx, int ny, const double *xy, int n_a, const double *vel,
+int orc_advect_operator(int nx, int ny, const double *xy, int geo, int n_a, const double *vel,
                         const double *H, const double *A, double *LH, double *LA) {
   if (nx < 1 || ny < 1 || !xy || !vel || !H || !A || !LH || !LA) return ORC_ERR_ARG;
   if (!(n_a == 1 || n_a == 3 || n_a == 6)) return ORC_ERR_ARG;
   adv_t P;
-  P.nx = nx; P.ny = ny; P.n_a = n_a; P.nq = adv_nq(n_a); P.xy = xy;
+  P.nx = nx; P.ny = ny; P.n_a = n_a; P.nq = adv_nq(n_a); P.xy = xy; P.geo = geo;
   orc_gauss(P.nq, P.qx, P.qw);
   return adv_operator(&P, vel, H, A, LH, LA);
 }

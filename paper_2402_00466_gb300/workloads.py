@@ -202,7 +202,10 @@ def small_case(nx: int, ny: int, n_s: int, seed: int, L: float = DOMAIN_M, movin
     """A small seeded case of any size (iid ice, cyclone wind, optional smooth
     initial velocity and random initial stress) for parity tests.  geometry:
     "uniform", "perturbed" (random interior vertex moves, seed + 4000) or
-    "wavy" (smooth curvilinear map)."""
+    "wavy" (smooth curvilinear map, bilinear elements), "wavy_iso" (the same
+    map at every CG2 node: isoparametric curved elements) or "curved"
+    (randomly curved isoparametric elements).  xy holds the vertices, or
+    for the isoparametric geometries the CG2 node positions."""
     ne, nn, nv = sizes(nx, ny)
     H, A = ice_iid(nx, ny, seed)
     rng = np.random.Generator(np.random.PCG64(seed + 1000))
@@ -212,9 +215,14 @@ def small_case(nx: int, ny: int, n_s: int, seed: int, L: float = DOMAIN_M, movin
         xy = perturbed_vertices(nx, ny, seed + 4000, L=L)
     elif geometry == "wavy":
         xy = wavy_vertices(nx, ny, L=L)
+    elif geometry == "wavy_iso":
+        xy = wavy_nodes(nx, ny, L=L)
+    elif geometry == "curved":
+        xy = curved_nodes(nx, ny, seed + 4000, L=L)
     else:
         raise ValueError(f"unknown geometry {geometry!r}")
-    tau = cyclone_wind_stress(node_coords(nx, ny, xy), cyclone_params(seed + 2000, L))
+    ncoord = xy.T if xy.shape[0] == nn else node_coords(nx, ny, xy)
+    tau = cyclone_wind_stress(ncoord, cyclone_params(seed + 2000, L))
     vel0 = smooth_velocity(nx, ny, seed + 3000, L=L) if moving else np.zeros((2, nn))
     S0 = rng.uniform(-5e3, 5e3, (3, n_s, ne)) if moving else np.zeros((3, n_s, ne))
     return dict(name=f"small{nx}x{ny}_dg{n_s}", nx=nx, ny=ny, n_s=n_s, n_a=1, n_sub=10, L=L,
@@ -280,3 +288,36 @@ def node_coords(nx: int, ny: int, xy):
     out[1::2, 0::2] = 0.5 * (v[:-1, :] + v[1:, :])
     out[1::2, 1::2] = 0.25 * (v[:-1, :-1] + v[:-1, 1:] + v[1:, :-1] + v[1:, 1:])
     return out.reshape(-1, 2).T.copy()
+
+
+def wavy_nodes(nx: int, ny: int, amp: float = 0.3, L: float = DOMAIN_M):
+    """CG2 node positions (N_n, 2) of a curved mesh: the smooth map of
+    wavy_vertices evaluated at every CG2 node of the uniform mesh, so that
+    the isoparametric (Q2) elements follow the curved map."""
+    nc = node_coords_uniform(nx, ny, L, L)
+    x, y = nc[0] / L, nc[1] / L
+    h = L / max(nx, ny)
+    out = nc.T.copy()
+    out[:, 0] += amp * h * np.sin(2 * math.pi * y) * np.sin(math.pi * x)
+    out[:, 1] += amp * h * np.sin(2 * math.pi * x) * np.sin(math.pi * y)
+    return out
+
+
+def curved_nodes(nx: int, ny: int, seed: int, amp: float = 0.08, L: float = DOMAIN_M):
+    """CG2 node positions (N_n, 2) of a randomly curved mesh: the nodes of a
+    perturbed-vertex mesh, with every edge-midpoint and element-centre node
+    moved by U[-amp h, amp h] per coordinate (PCG64(seed)); boundary nodes
+    stay on the boundary."""
+    xy = perturbed_vertices(nx, ny, seed, L=L)
+    nodes = node_coords(nx, ny, xy).T.reshape(2 * ny + 1, 2 * nx + 1, 2).copy()
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    h = L / max(nx, ny)
+    d = rng.uniform(-amp * h, amp * h, nodes.shape)
+    iy, ix = np.meshgrid(np.arange(2 * ny + 1), np.arange(2 * nx + 1), indexing="ij")
+    mid = (ix % 2 == 1) | (iy % 2 == 1)  # not a vertex
+    d[~mid] = 0.0
+    d[0, :, 1] = d[-1, :, 1] = 0.0  # south / north boundary nodes move along x only
+    d[:, 0, 0] = d[:, -1, 0] = 0.0  # west / east boundary nodes move along y only
+    d[0, 0] = d[0, -1] = d[-1, 0] = d[-1, -1] = 0.0
+    nodes += d
+    return nodes.reshape(-1, 2).copy()

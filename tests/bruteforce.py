@@ -79,18 +79,27 @@ def dg_documented(n_s, xi, eta):
 
 class Mesh:
     def __init__(self, nx, ny, xy, n_s):
+        """xy: the vertices [(nx+1)(ny+1)][2] (bilinear element maps), or the
+        CG2 node positions [(2nx+1)(2ny+1)][2] (isoparametric Q2 maps; the
+        "exact" rule is then the method's own, since curved elements make the
+        integrands rational)."""
         self.nx, self.ny, self.n_s = nx, ny, n_s
         self.ne = nx * ny
         self.nw, self.nh = 2 * nx + 1, 2 * ny + 1
         self.nn = self.nw * self.nh
-        xy = np.asarray(xy, dtype=np.float64).reshape(ny + 1, nx + 1, 2)
         kx, ky = np.meshgrid(np.arange(nx), np.arange(ny))
         kx, ky = kx.ravel(), ky.ravel()
-        self.X00, self.X10 = xy[ky, kx], xy[ky, kx + 1]
-        self.X01, self.X11 = xy[ky + 1, kx], xy[ky + 1, kx + 1]
         self.nodes = np.stack([(2 * ky + b) * self.nw + 2 * kx + a
                                for b in range(3) for a in range(3)], -1)  # (ne, 9)
-        self.rule_exact = self._rule(*self._tensor(gauss01(10)))
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        self.iso = xy.shape[0] == self.nn
+        if self.iso:
+            self.XN = xy[self.nodes]  # (ne, 9, 2)
+        else:
+            xy = xy.reshape(ny + 1, nx + 1, 2)
+            self.X00, self.X10 = xy[ky, kx], xy[ky, kx + 1]
+            self.X01, self.X11 = xy[ky + 1, kx], xy[ky + 1, kx + 1]
+        self.rule_exact = self._rule(*self._tensor(gauss01(NGP[n_s] if self.iso else 10)))
         self.rule_method = self._rule(*self._tensor(gauss01(NGP[n_s])))
         sp = np.array([0.1, 0.35, 0.6, 0.9])
         XI, ET = np.meshgrid(sp, sp)
@@ -104,7 +113,12 @@ class Mesh:
         return XI.ravel(), ET.ravel(), W.ravel()
 
     def _map(self, xi, eta):
-        """Jacobian entries (ne, nq) of the bilinear map."""
+        """Jacobian entries (ne, nq) of the bilinear or isoparametric map."""
+        if self.iso:
+            _, gxi, geta = q2(xi, eta)  # (nq, 9)
+            dxi = np.einsum("qj,kjc->kqc", gxi, self.XN)
+            deta = np.einsum("qj,kjc->kqc", geta, self.XN)
+            return dxi[..., 0], deta[..., 0], dxi[..., 1], deta[..., 1]
         X00, X10, X01, X11 = (v[:, None, :] for v in (self.X00, self.X10, self.X01, self.X11))
         e = eta[None, :, None]
         x = xi[None, :, None]
@@ -239,12 +253,22 @@ def _q2_at(xi, eta):
 
 
 class Advection:
-    def __init__(self, nx, ny, xy, n_a, nq=10):
+    def __init__(self, nx, ny, xy, n_a, nq=None):
+        """xy: vertices (bilinear maps; default rule 10 points) or CG2 node
+        positions (isoparametric maps; default rule the method's own, 3 or 4
+        points, since curved elements make the integrands rational)."""
         self.nx, self.ny, self.n_a = nx, ny, n_a
         self.ne = nx * ny
         self.nw = 2 * nx + 1
         self.nn = self.nw * (2 * ny + 1)
-        self.xy = np.asarray(xy, dtype=np.float64).reshape(ny + 1, nx + 1, 2)
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        self.iso = xy.shape[0] == self.nn
+        if nq is None:
+            nq = ({1: 3, 3: 3, 6: 4}[n_a]) if self.iso else 10
+        if self.iso:
+            self.nxy = xy
+        else:
+            self.xy = xy.reshape(ny + 1, nx + 1, 2)
         self.x1, self.w1 = gauss01(nq)
         XI, ET = np.meshgrid(self.x1, self.x1)
         self.vxi, self.veta, self.vw = XI.ravel(), ET.ravel(), np.outer(self.w1, self.w1).ravel()
@@ -254,13 +278,25 @@ class Advection:
         v = self.xy
         return v[ky, kx], v[ky, kx + 1], v[ky + 1, kx], v[ky + 1, kx + 1]
 
+    def elem_nodes(self, K):
+        kx, ky = K % self.nx, K // self.nx
+        idx = [(2 * ky + b) * self.nw + 2 * kx + a for b in range(3) for a in range(3)]
+        return self.nxy[idx]  # (9, 2)
+
     def xmap(self, K, xi, eta):
+        if self.iso:
+            phi, _, _ = q2(np.atleast_1d(xi), np.atleast_1d(eta))
+            return phi @ self.elem_nodes(K)
         x00, x10, x01, x11 = self.corners(K)
         xi, eta = np.asarray(xi)[..., None], np.asarray(eta)[..., None]
         return (x00 * (1 - xi) * (1 - eta) + x10 * xi * (1 - eta) + x01 * (1 - xi) * eta
                 + x11 * xi * eta)
 
     def jac(self, K, xi, eta):
+        if self.iso:
+            _, gxi, geta = q2(np.atleast_1d(xi), np.atleast_1d(eta))
+            X = self.elem_nodes(K)
+            return gxi @ X, geta @ X  # columns d x/d xi, d x/d eta
         x00, x10, x01, x11 = self.corners(K)
         xi, eta = np.asarray(xi)[..., None], np.asarray(eta)[..., None]
         dxi = (x10 - x00) * (1 - eta) + (x11 - x01) * eta

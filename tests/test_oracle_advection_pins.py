@@ -186,3 +186,21 @@ def test_advect_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.advect(2, 2, W.uniform_vertices(2, 2), 2, np.zeros((2, 25)), 1.0, 1,
                       np.zeros((2, 4)), np.zeros((2, 4)))
+
+
+@pytest.mark.parametrize("n_a", [1, 3, 6])
+def test_iso_advection_preserves_a_constant_and_matches_bruteforce(n_a):
+    """Curved (isoparametric) elements: a constant under a rigid rotation stays
+    put, and the operator agrees with the brute force at the method's rule."""
+    nx, ny, L = 4, 4, 3e3
+    nodes = W.curved_nodes(nx, ny, 23, amp=0.08, L=L)
+    vel = np.stack([-(nodes[:, 1] - 0.4 * L), nodes[:, 0] - 0.55 * L]) * 1e-4
+    ne = nx * ny
+    H = np.zeros((n_a, ne)); H[0] = 1.3
+    LH, _ = oracle.advect_operator(nx, ny, nodes, n_a, vel, H, H)
+    assert np.abs(LH).max() <= 1e-12 * 1.3 * np.abs(vel).max() / (L / nx)
+    rng = np.random.default_rng(29)
+    H = rng.uniform(0.5, 1.5, (n_a, ne))
+    LH, _ = oracle.advect_operator(nx, ny, nodes, n_a, vel, H, H)
+    ref = BF.Advection(nx, ny, nodes, n_a).operator(vel, H)
+    assert np.abs(LH - ref).max() <= 1e-11 * np.abs(ref).max()

@@ -42,6 +42,10 @@ MUTANTS = [
      "double dvx = ox - vn[j], dvy = oy - vn[nn + j];"),
     ("stress 12 coefficient", "s12[g] = alphaInv * (PD * c_s * e12);",
      "s12[g] = alphaInv * (PD * c_a * e12);"),
+    ("isoparametric dx/deta from the xi-derivative", "J01 += xn[0] * M->q2e[g][j];",
+     "J01 += xn[0] * M->q2x[g][j];"),
+    ("isoparametric map reads y for x", "J00 += xn[0] * M->q2x[g][j];",
+     "J00 += xn[1] * M->q2x[g][j];"),
 ]
 
 
@@ -68,6 +72,8 @@ ADVECTION_MUTANTS = [
     ("DG2 rule too low", "static int adv_nq(int n_a) { return n_a == 6 ? 4 : 3; }",
      "static int adv_nq(int n_a) { return n_a == 6 ? 3 : 3; }"),
     ("Euler step sign", "H1[k] = H[k] + dt * LH[k];", "H1[k] = H[k] - dt * LH[k];"),
+    ("isoparametric transport Jacobian transposed", "J[2 * c + 1] += xn[c] * deta[j];",
+     "J[2 * c + 1] += xn[c] * dxi[j];"),
 ]
 
 

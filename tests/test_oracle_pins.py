@@ -448,3 +448,87 @@ def test_bad_arguments_rejected():
     bad[1, 1] = bad[2, 2] + 10.0  # folded element: det J <= 0
     with pytest.raises(ValueError):
         oracle.strain(2, 2, bad.reshape(-1, 2), 3, np.zeros((2, 25)))
+
+
+# --------------------------------------------------------------------------
+# Isoparametric (Q2) element maps: the geometry given by the CG2 node
+# positions (Sec. 2.1: the element map comes from the velocity's space)
+# --------------------------------------------------------------------------
+def curved(nx, ny, seed, L=3e3):
+    return W.curved_nodes(nx, ny, seed, amp=0.08, L=L)
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+def test_iso_with_bilinear_nodes_reproduces_bilinear_maps(n_s):
+    """Node positions that are the bilinear images of the vertices make the
+    Q2 map equal the Q1 map: every stage agrees with the vertex geometry."""
+    nx, ny, L = 5, 4, 4e3
+    xy = perturbed_vertices(nx, ny, L, 7)
+    nodes = W.node_coords(nx, ny, xy).T.copy()
+    case = W.small_case(nx, ny, n_s, seed=3, L=L)
+    args = (case["params"], case["H"], case["A"], case["tau"], case["vel0"], case["S0"], 3)
+    va, Sa = oracle.subcycles(nx, ny, xy, n_s, 1, *args)
+    vb, Sb = oracle.subcycles(nx, ny, nodes, n_s, 1, *args)
+    assert rel(vb, va) < 1e-14 and rel(Sb, Sa) < 1e-14
+    ma, _ = oracle.lumped(nx, ny, xy, n_s, 1, case["params"], case["H"])
+    mb, _ = oracle.lumped(nx, ny, nodes, n_s, 1, case["params"], case["H"])
+    assert rel(mb, ma) < 1e-14
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+def test_iso_strain_of_a_linear_field_is_exact(n_s):
+    """On curved elements a physical linear velocity lies in the isoparametric
+    space, so its projected strain is the exact constant (higher DG
+    coefficients zero)."""
+    nx, ny = 4, 3
+    nodes = curved(nx, ny, 11)
+    a, b, c, d = 2e-6, -1e-6, 3e-6, 0.5e-6
+    vel = np.stack([a * nodes[:, 0] + b * nodes[:, 1], c * nodes[:, 0] + d * nodes[:, 1]])
+    E = oracle.strain(nx, ny, nodes, n_s, vel)
+    for comp, val in ((0, a), (1, 0.5 * (b + c)), (2, d)):
+        assert np.allclose(E[comp, 0], val, rtol=1e-12, atol=0)
+        assert np.abs(E[comp, 1:]).max() < 1e-12 * abs(val)
+
+
+def test_iso_rigid_rotation_has_no_strain():
+    nx, ny = 4, 4
+    nodes = curved(nx, ny, 13)
+    w = 1e-5
+    vel = np.stack([-w * nodes[:, 1], w * nodes[:, 0]])
+    E = oracle.strain(nx, ny, nodes, 6, vel)
+    assert np.abs(E).max() < 1e-12 * w
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+def test_iso_forces_sum_to_zero(n_s):
+    """sum_j phi_j = 1 gives sum_j grad phi_j = 0 at every quadrature point,
+    so the nodal forces of any stress sum to zero on curved elements too."""
+    nx, ny = 4, 3
+    nodes = curved(nx, ny, 17)
+    S = np.random.default_rng(2).uniform(-5e3, 5e3, (3, n_s, nx * ny))
+    F = oracle.divergence(nx, ny, nodes, n_s, S)
+    scale = np.abs(S).max() * 3e3 / nx
+    assert np.abs(F.sum(axis=1)).max() < 1e-12 * scale * nx * ny
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+def test_iso_matches_bruteforce(n_s):
+    """Curved elements against the independent numpy restatement (global
+    assembly, shifted-Legendre basis) with the method's Gauss rule."""
+    nx, ny = 3, 3
+    L = 3e3
+    nodes = curved(nx, ny, 19, L=L)
+    case = W.small_case(nx, ny, n_s, seed=5, L=L)
+    bf = BF.Mesh(nx, ny, nodes, n_s)
+    vel = case["vel0"]
+    E = oracle.strain(nx, ny, nodes, n_s, vel)
+    Ebf = bf.strain(vel)
+    assert rel(bf.values_documented(E), bf.values(Ebf)) < 1e-12
+    F = oracle.divergence(nx, ny, nodes, n_s, case["S0"])
+    Fbf = bf.divergence(bf.from_documented(case["S0"]))
+    assert rel(F, Fbf) < 1e-12
+    vo, So = oracle.subcycles(nx, ny, nodes, n_s, 1, case["params"], case["H"], case["A"],
+                              case["tau"], vel, case["S0"], 3)
+    vb, Sb, _ = bf.subcycles(vel, case["S0"], case["H"], case["A"], case["tau"], case["params"], 3)
+    assert rel(vo, vb) < 1e-11
+    assert rel(bf.values_documented(So), bf.values(Sb)) < 1e-11
