@@ -127,6 +127,15 @@ enum mevp_field {
  * nx, ny >= 1 and (2nx+1)(2ny+1) < 2^31. */
 MEVP_API int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_xy,
                      mevp_mesh **out);
+/* Create a structured nx x ny mesh of curved (isoparametric) quadrilaterals:
+ * node_xy [N_n][2] host memory (copied) holds the positions of all CG2 nodes,
+ * node id = iy*(2nx+1) + ix, and each element is the image of the reference
+ * square under the Q2 interpolant of its 9 nodes -- the element map from the
+ * velocity's finite element space (Sec. 2.1).  The local mass matrices use
+ * the Gauss rule of App. A (det J is then a higher-degree polynomial).
+ * MEVP_ERR_ARG for non-finite positions or an element whose det J is not
+ * positive at its 5 x 5 reference sample points.  FP64 states only. */
+MEVP_API int mevp_mesh_create_nodes(int nx, int ny, const double *node_xy, mevp_mesh **out);
 MEVP_API void mevp_mesh_destroy(mevp_mesh *mesh);
 
 /* Device workspace a state needs, in bytes (all internal buffers). */

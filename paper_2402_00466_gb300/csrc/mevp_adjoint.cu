@@ -375,7 +375,7 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
   if (rc) return rc;
   if (s->prec != MEVP_FP64) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: FP64 states only");
   if (s->ns == 8) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: 3 or 6 stress dofs only");
-  if (s->d.xy) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: rectilinear meshes only");
+  if (s->d.xy || s->d.nxy) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: rectilinear meshes only");
   if (s->na != 1) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: DG0 ice fields only");
   if (n < 1) return afail(MEVP_ERR_ARG, "adjoint: n=%d < 1", n);
   if (checkpoint_every < 1) return afail(MEVP_ERR_ARG, "adjoint: checkpoint_every < 1");

@@ -57,6 +57,28 @@ __host__ __device__ constexpr double dleg(int k, double x) {
 __host__ __device__ constexpr double lag2(int a, double x) {
   return a == 0 ? 2.0 * x * x - x : a == 1 ? 1.0 - 4.0 * x * x : 2.0 * x * x + x;
 }
+// and its derivative: 4x - 1, -8x, 4x + 1
+__host__ __device__ constexpr double dlag2(int a, double x) {
+  return a == 0 ? 4.0 * x - 1.0 : a == 1 ? -8.0 * x : 4.0 * x + 1.0;
+}
+
+// Jacobian of an isoparametric element at centred reference point (xh, eh)
+// from its 9 node positions X, Y (local node a + 3b).
+__device__ __forceinline__ void iso_jac(const double X[9], const double Y[9], double xh,
+                                        double eh, double &j00, double &j01, double &j10,
+                                        double &j11) {
+  j00 = j01 = j10 = j11 = 0.0;
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double gx = dlag2(a, xh) * lag2(b, eh), ge = lag2(a, xh) * dlag2(b, eh);
+      j00 = fma(X[a + 3 * b], gx, j00);
+      j01 = fma(X[a + 3 * b], ge, j01);
+      j10 = fma(Y[a + 3 * b], gx, j10);
+      j11 = fma(Y[a + 3 * b], ge, j11);
+    }
+}
 
 // Element geometry: the bilinear map from the vertices on a general mesh, or
 // the rectangle hx x hy of the mesh lines; and the four edge vectors, each
@@ -102,12 +124,29 @@ struct AdvArgs {
   double a, b, dt;          // U_out = a U0 + b (U_in + dt L(U_in))
 };
 
-template <int NA, int NQ>
+template <int NA, int NQ, bool ISO>
 __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
   const size_t ne = d.ne, nn = d.nn;
-  const AdvGeom G = adv_geom(d, kx, ky);
+  // geometry: the bilinear map and edge vectors, or (ISO) the 9 node
+  // positions of the isoparametric element
+  AdvGeom G{};
+  double X[9], Y[9];
+  if constexpr (ISO) {
+    const long long base = (long long)(2 * ky) * d.nw + 2 * kx;
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+        const double2 p = ck_ldg(d.flags, d.nxy, base + (long long)bb * d.nw + aa, d.nn, 176);
+        X[aa + 3 * bb] = p.x;
+        Y[aa + 3 * bb] = p.y;
+      }
+  } else {
+    G = adv_geom(d, kx, ky);
+  }
   const QuadMap &m = G.m;
+  double wdet[NQ * NQ];  // ISO: w det J at the volume points (mass matrix)
   const long long nf = (long long)d.na * d.ne;
   double h[NA], a[NA];
 #pragma unroll
@@ -122,6 +161,16 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
 #pragma unroll
   for (int i = 0; i < NA; ++i) RH[i] = RA[i] = 0.0;
 
+  if constexpr (ISO) {
+#pragma unroll
+    for (int qy = 0; qy < NQ; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < NQ; ++qx) {
+        double j00, j01, j10, j11;
+        iso_jac(X, Y, Rule<NQ>::xh(qx), Rule<NQ>::xh(qy), j00, j01, j10, j11);
+        wdet[qx + NQ * qy] = Rule<NQ>::w(qx) * Rule<NQ>::w(qy) * fma(j00, j11, -(j01 * j10));
+      }
+  }
   // volume terms
   if (NA > 1) {
 #pragma unroll
@@ -142,8 +191,15 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
           ux = fma(lag2(bb, eh), rx, ux);
           uy = fma(lag2(bb, eh), ry, uy);
         }
-        const double j00 = fma(m.cx, eh, m.Ax), j10 = fma(m.cy, eh, m.Ay);
-        const double j01 = fma(m.cx, xh, m.Bx), j11 = fma(m.cy, xh, m.By);
+        double j00, j01, j10, j11;
+        if constexpr (ISO) {
+          iso_jac(X, Y, xh, eh, j00, j01, j10, j11);
+        } else {
+          j00 = fma(m.cx, eh, m.Ax);
+          j10 = fma(m.cy, eh, m.Ay);
+          j01 = fma(m.cx, xh, m.Bx);
+          j11 = fma(m.cy, xh, m.By);
+        }
         const double vtx = w * fma(j11, ux, -(j01 * uy));
         const double vte = w * fma(j00, uy, -(j10 * ux));
         double hq = 0.0, aq = 0.0;
@@ -185,13 +241,24 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
     // +vt_eta on the north edge.
     const bool vert = e < 2;
     const double side = (e == 1 || e == 3) ? 0.5 : -0.5;
-    const double tx = G.ex[e], ty = G.ey[e];
     const double sgn = (e == 1 || e == 2) ? 1.0 : -1.0;
     const int n0 = vert ? (e == 0 ? 0 : 2) : (e == 2 ? 0 : 6);
     const int step = vert ? 3 : 1;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const double t = Rule<NQ>::xh(q), w = Rule<NQ>::w(q);
+      // the edge tangent (ISO: the derivative of the edge's quadratic through
+      // its three nodes, the same seen from both elements)
+      double tx = G.ex[e], ty = G.ey[e];
+      if constexpr (ISO) {
+        tx = 0.0;
+        ty = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          tx = fma(dlag2(k, t), X[n0 + step * k], tx);
+          ty = fma(dlag2(k, t), Y[n0 + step * k], ty);
+        }
+      }
       double ux = 0.0, uy = 0.0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -232,7 +299,35 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
 
   // L = M^-1 R
   bool done = false;
-  if constexpr (NA > 1) {
+  if constexpr (ISO) {
+    if constexpr (NA > 1) {
+      MassFactor<NA> F;
+      ldl_factor<NA, double>(
+          [&](int i, int j) -> double {
+            double acc = 0.0;
+#pragma unroll
+            for (int qy = 0; qy < NQ; ++qy)
+#pragma unroll
+              for (int qx = 0; qx < NQ; ++qx) {
+                const double xh = Rule<NQ>::xh(qx), eh = Rule<NQ>::xh(qy);
+                const double pp = leg(dgx(i), xh) * leg(dgy(i), eh) * leg(dgx(j), xh) *
+                                  leg(dgy(j), eh);
+                acc = fma(wdet[qx + NQ * qy], pp, acc);
+              }
+            return acc;
+          },
+          F);
+      mass_solve<NA>(F, RH);
+      mass_solve<NA>(F, RA);
+    } else {
+      double area = 0.0;
+#pragma unroll
+      for (int q = 0; q < NQ * NQ; ++q) area += wdet[q];
+      RH[0] /= area;
+      RA[0] /= area;
+    }
+    done = true;
+  } else if constexpr (NA > 1) {
     if (d.xy) {
       MassFactor<NA> F;
       mass_factor<NA>(m, F);
@@ -261,20 +356,28 @@ __device__ __forceinline__ void adv_element(const DevState &d, const AdvArgs &g,
   }
 }
 
-template <int NA, int NQ>
+template <int NA, int NQ, bool ISO>
 __global__ void __launch_bounds__(kAdvBlock) k_advect(DevState d, AdvArgs g) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K < d.ne) adv_element<NA, NQ>(d, g, K);
+  if (K < d.ne) adv_element<NA, NQ, ISO>(d, g, K);
 }
 
 inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
 cudaError_t stage(const DevState &d, const AdvArgs &g, cudaStream_t st) {
   const int gr = blocks(d.ne, kAdvBlock);
-  switch (d.na) {
-    case 1: k_advect<1, 3><<<gr, kAdvBlock, 0, st>>>(d, g); break;
-    case 3: k_advect<3, 3><<<gr, kAdvBlock, 0, st>>>(d, g); break;
-    default: k_advect<6, 4><<<gr, kAdvBlock, 0, st>>>(d, g); break;
+  if (d.nxy) {
+    switch (d.na) {
+      case 1: k_advect<1, 3, true><<<gr, kAdvBlock, 0, st>>>(d, g); break;
+      case 3: k_advect<3, 3, true><<<gr, kAdvBlock, 0, st>>>(d, g); break;
+      default: k_advect<6, 4, true><<<gr, kAdvBlock, 0, st>>>(d, g); break;
+    }
+  } else {
+    switch (d.na) {
+      case 1: k_advect<1, 3, false><<<gr, kAdvBlock, 0, st>>>(d, g); break;
+      case 3: k_advect<3, 3, false><<<gr, kAdvBlock, 0, st>>>(d, g); break;
+      default: k_advect<6, 4, false><<<gr, kAdvBlock, 0, st>>>(d, g); break;
+    }
   }
   return cudaGetLastError();
 }

@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, xy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -77,6 +77,7 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.xline = take(sizeof(double) * (m->nx + 1));
   L.yline = take(sizeof(double) * (m->ny + 1));
   L.xy = take(m->general ? m->xy.size() * sizeof(double) : 0);
+  L.nxy = take(m->iso ? m->nxy.size() * sizeof(double) : 0);
   L.lines = take(sizeof(double) * 2 * (m->nx + m->ny));
   L.pstar = take(sizeof(double) * ne);
   L.flags = take(sizeof(int) * 4);
@@ -277,6 +278,57 @@ int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double *vertex_
   return MEVP_OK;
 }
 
+int mevp_mesh_create_nodes(int nx, int ny, const double *node_xy, mevp_mesh **out) {
+  if (!out) return fail(MEVP_ERR_ARG, "mesh_create_nodes: out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1)
+    return fail(MEVP_ERR_ARG, "mesh_create_nodes: nx=%d ny=%d must be >= 1", nx, ny);
+  if (!node_xy) return fail(MEVP_ERR_ARG, "mesh_create_nodes: node_xy is NULL");
+  const long long nw = 2LL * nx + 1, nh = 2LL * ny + 1, nn = nw * nh;
+  if (nn >= (1LL << 31) - 1)
+    return fail(MEVP_ERR_ARG, "mesh_create_nodes: too many nodes (%lld)", nn);
+  for (long long i = 0; i < 2 * nn; ++i)
+    if (!std::isfinite(node_xy[i]))
+      return fail(MEVP_ERR_ARG, "mesh_create_nodes: non-finite node %lld", i / 2);
+  // det J of every element's Q2 map must be positive: checked at a 5 x 5
+  // grid of reference points (corners, edge and interior points)
+  auto lag = [](int a, double t) {
+    return a == 0 ? (1 - t) * (1 - 2 * t) : a == 1 ? 4 * t * (1 - t) : t * (2 * t - 1);
+  };
+  auto dlag = [](int a, double t) { return a == 0 ? 4 * t - 3 : a == 1 ? 4 - 8 * t : 4 * t - 1; };
+  for (int ky = 0; ky < ny; ++ky)
+    for (int kx = 0; kx < nx; ++kx)
+      for (int qy = 0; qy <= 4; ++qy)
+        for (int qx = 0; qx <= 4; ++qx) {
+          const double xi = 0.25 * qx, eta = 0.25 * qy;
+          double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+          for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) {
+              const double *p = node_xy + 2 * ((2LL * ky + b) * nw + 2LL * kx + a);
+              const double gx = dlag(a, xi) * lag(b, eta), ge = lag(a, xi) * dlag(b, eta);
+              j00 += p[0] * gx;
+              j01 += p[0] * ge;
+              j10 += p[1] * gx;
+              j11 += p[1] * ge;
+            }
+          if (!(j00 * j11 - j01 * j10 > 0))
+            return fail(MEVP_ERR_ARG,
+                        "mesh_create_nodes: element (%d,%d) folds or is clockwise (det J <= 0 "
+                        "at reference point (%g,%g))",
+                        kx, ky, xi, eta);
+        }
+  mevp_mesh *m = new (std::nothrow) mevp_mesh;
+  if (!m) return fail(MEVP_ERR_OOM, "mesh_create_nodes: host allocation failed");
+  m->nx = nx;
+  m->ny = ny;
+  m->iso = true;
+  m->nxy.assign(node_xy, node_xy + 2 * nn);
+  m->xline.assign(nx + 1, 0.0);
+  m->yline.assign(ny + 1, 0.0);
+  *out = m;
+  return MEVP_OK;
+}
+
 void mevp_mesh_destroy(mevp_mesh *mesh) { delete mesh; }
 
 int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, int precision,
@@ -288,6 +340,9 @@ int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, i
     return fail(MEVP_ERR_ARG, "n_adv=%d: H, A need 1, 3 or 6 dofs (DG0, DG1, DG2)", n_adv);
   if (precision != MEVP_FP64 && precision != MEVP_MIXED)
     return fail(MEVP_ERR_ARG, "precision=%d unknown", precision);
+  if (mesh->iso && precision != MEVP_FP64)
+    return fail(MEVP_ERR_UNSUPPORTED,
+                "precision=%d: isoparametric (curved) meshes run in FP64 only", precision);
   *bytes = make_layout(mesh, n_stress, n_adv, precision).total;
   return MEVP_OK;
 }
@@ -351,6 +406,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.xline = (const double *)(b + L.xline);
   d.yline = (const double *)(b + L.yline);
   d.xy = mesh->general ? (const double2 *)(b + L.xy) : nullptr;
+  d.nxy = mesh->iso ? (const double2 *)(b + L.nxy) : nullptr;
   d.lines = (double *)(b + L.lines);
   s->pstar_buf = (double *)(b + L.pstar);
   s->adv1 = (double *)(b + L.adv1);
@@ -401,6 +457,10 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   if (e == cudaSuccess && mesh->general)
     e = cudaMemcpyAsync((void *)d.xy, mesh->xy.data(), sizeof(double) * mesh->xy.size(),
                         cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && mesh->iso)
+    e = cudaMemcpyAsync((void *)d.nxy, mesh->nxy.data(), sizeof(double) * mesh->nxy.size(),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && mesh->iso) e = mevp::setup_iso_kernels();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) r2 = cuda_fail(e, "state_create: initialise workspace");
   if (r2) {

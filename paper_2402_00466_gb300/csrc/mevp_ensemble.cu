@@ -258,7 +258,7 @@ int mevp_ensemble_create(mevp_state *const *members, int n, mevp_ensemble **out)
     for (int j = 0; j < i; ++j)
       if (members[j] == members[i])
         return efail(MEVP_ERR_ARG, "ensemble_create: member %d repeats member %d", i, j);
-    if (members[i]->d.xy)
+    if (members[i]->d.xy || members[i]->d.nxy)
       return efail(MEVP_ERR_UNSUPPORTED,
                    "ensemble_create: member %d has a general mesh; ensembles take rectilinear "
                    "meshes", i);

@@ -316,11 +316,52 @@ __global__ void k_strength_gauss(DevState d, double Pstar, double C) {
     }
 }
 
+// det J at the N x N Gauss points of an isoparametric element (reference
+// gradients of its 9 node positions).
+template <int N>
+__device__ __forceinline__ void iso_det_gauss(const DevState &d, int kx, int ky,
+                                              double det[N * N]) {
+  double X[9], Y[9];
+  const long long base = (long long)(2 * ky) * d.nw + 2 * kx;
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      const double2 p = ck_ldg(d.flags, d.nxy, base + (long long)b * d.nw + a, d.nn, 143);
+      X[a + 3 * b] = p.x;
+      Y[a + 3 * b] = p.y;
+    }
+  double xxi[N * N], xeta[N * N], yxi[N * N], yeta[N * N];
+  ref_grad_gauss<N>(X, xxi, xeta);
+  ref_grad_gauss<N>(Y, yxi, yeta);
+  for (int g = 0; g < N * N; ++g) det[g] = fma(xxi[g], yeta[g], -(xeta[g] * yxi[g]));
+}
+
+// int_K w phi_j (w = 1, or max(0, H) with DG1/DG2 H) on an isoparametric
+// element with the N-point rule of the stress space.
+template <int N>
+__device__ __forceinline__ double iso_integral(const DevState &d, int kx, int ky, int a, int b,
+                                               bool with_h) {
+  double det[N * N];
+  iso_det_gauss<N>(d, kx, ky, det);
+  const int K = ky * d.nx + kx;
+  double acc = 0.0;
+  for (int gy = 0; gy < N; ++gy)
+    for (int gx = 0; gx < N; ++gx) {
+      double w = Gauss<N>::w(gx) * Gauss<N>::w(gy) * det[gx + N * gy];
+      if (with_h) {
+        const double hv = d.na == 1 ? d.H[K] : dg_at_gauss<N>(d.H, d.na, d.ne, K, gx, gy);
+        w *= fmax(0.0, hv);
+      }
+      acc = fma(w, lq<N>(a, gx) * lq<N>(b, gy), acc);
+    }
+  return acc;
+}
+
 // int_K max(0, H) phi_j for DG1/DG2 H with the N-point rule of the stress
 // space, phi_j the Q2 function of local node (a, b).
 template <int N>
 __device__ __forceinline__ double mass_integral_gauss(const DevState &d, int kx, int ky, int a,
                                                       int b) {
+  if (d.nxy) return iso_integral<N>(d, kx, ky, a, b, true);
   const int K = ky * d.nx + kx;
   QuadMap m;
   if (d.xy) {
@@ -358,15 +399,21 @@ __global__ void k_node_constants(DevState d, int cur, mevp_params p, int has_vo)
     for (int kx = kx1; kx <= kx2; ++kx) {
       if (kx < 0 || kx >= d.nx) continue;
       double w;
-      if (d.xy) {
+      if (d.nxy) {
+        w = d.ns == 3 ? iso_integral<2>(d, kx, ky, ix - 2 * kx, iy - 2 * ky, false)
+                      : iso_integral<3>(d, kx, ky, ix - 2 * kx, iy - 2 * ky, false);
+      } else if (d.xy) {
         w = node_area_general(quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1)), ix - 2 * kx, iy - 2 * ky);
       } else {
         const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
         w = area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
       }
       l += w;
-      if (d.na == 1)
+      if (d.na == 1 && !d.nxy)
         mh += fmax(0.0, d.H[ky * d.nx + kx]) * w;
+      else if (d.na == 1)
+        mh += d.ns == 3 ? iso_integral<2>(d, kx, ky, ix - 2 * kx, iy - 2 * ky, true)
+                        : iso_integral<3>(d, kx, ky, ix - 2 * kx, iy - 2 * ky, true);
       else if (d.ns == 3)
         mh += mass_integral_gauss<2>(d, kx, ky, ix - 2 * kx, iy - 2 * ky);
       else
@@ -470,7 +517,7 @@ cudaError_t launch_nan_check(const DevState &d, int cur, cudaStream_t st) {
 
 cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                            cudaStream_t st) {
-  if (!d.xy) k_mesh_lines<<<blocks(d.nx + d.ny, 256), 256, 0, st>>>(d);
+  if (!d.xy && !d.nxy) k_mesh_lines<<<blocks(d.nx + d.ny, 256), 256, 0, st>>>(d);
   if (d.na == 1)
     k_strength<<<blocks(d.ne, 256), 256, 0, st>>>(d, p.Pstar, p.C);
   else if (d.ns == 3)
@@ -485,7 +532,9 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
                                 cudaStream_t st, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[0], st);
   const int eg = d.nsm;  // persistent: one block per SM
-  if (d.xy)
+  if (d.nxy)
+    launch_element_iso(d, r, cur, st);
+  else if (d.xy)
     launch_element_general(d, r, cur, st);
   else if (d.na == 1) {
     if (d.ns == 3)
@@ -548,6 +597,7 @@ int f64_node_ctas_per_sm() {
 }
 
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st) {
+  if (d.nxy) return launch_strain_diag_iso(d, cur, st);
   if (d.xy) return launch_strain_diag_general(d, cur, st);
   if (d.ns == 3)
     k_strain_diag<3><<<blocks(d.ne, 128), 128, 0, st>>>(d, cur);
@@ -559,7 +609,9 @@ cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st) {
 }
 
 cudaError_t launch_force_diag(const DevState &d, cudaStream_t st) {
-  if (d.xy)
+  if (d.nxy)
+    launch_force_elem_iso(d, st);
+  else if (d.xy)
     launch_force_elem_general(d, st);
   else if (d.ns == 3)
     k_force_elem<3><<<blocks(d.ne, 128), 128, 0, st>>>(d);

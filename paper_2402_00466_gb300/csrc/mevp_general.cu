@@ -119,9 +119,219 @@ __global__ void k_force_elem_gen(DevState d) {
   }
 }
 
+// ---- isoparametric (Q2) elements ------------------------------------------
+constexpr int kIsoBlock = 128;
+
+// The 9 CG2 node positions of element (kx, ky).
+__device__ __forceinline__ void gather_nodes9(const DevState &d, int kx, int ky, double X[9],
+                                              double Y[9]) {
+  const long long base = (long long)(2 * ky) * d.nw + 2 * kx;
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double2 p = ck_ldg(d.flags, d.nxy, base + (long long)b * d.nw + a, d.nn, 143);
+      X[a + 3 * b] = p.x;
+      Y[a + 3 * b] = p.y;
+    }
+}
+
+// Jacobian of the isoparametric map at the N x N Gauss points (reference
+// gradients of the node positions), into this thread's shared-memory column.
+template <int N>
+__device__ __forceinline__ IsoGeo<N, double> iso_geometry(const DevState &d, int kx, int ky,
+                                                          double *sm) {
+  constexpr int NG = N * N;
+  double X[9], Y[9];
+  gather_nodes9(d, kx, ky, X, Y);
+  double xxi[NG], xeta[NG], yxi[NG], yeta[NG];
+  ref_grad_gauss<N>(X, xxi, xeta);
+  ref_grad_gauss<N>(Y, yxi, yeta);
+  const int stride = blockDim.x;
+  double *col = sm + threadIdx.x;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    col[(0 * NG + g) * stride] = xxi[g];   // dx/dxi
+    col[(1 * NG + g) * stride] = xeta[g];  // dx/deta
+    col[(2 * NG + g) * stride] = yxi[g];   // dy/dxi
+    col[(3 * NG + g) * stride] = yeta[g];  // dy/deta
+  }
+  return IsoGeo<N, double>{col, stride};
+}
+
+template <int NS, bool VAR>
+__device__ __forceinline__ void elem_iso(const DevState &d, const Rheo &r, int cur, int K,
+                                         double *sm) {
+  constexpr int N = DgSpace<NS>::NGP;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const IsoGeo<N, double> m = iso_geometry<N>(d, kx, ky, sm);
+  MassFactor<NS> F;
+  mass_factor<NS>(m, F);
+  double Pc[NS], Qc[NS], Gc[NS];
+  {
+    double u[9], v[9];
+    gather9(d.vel[cur], d.nw, kx, ky, u, d.flags, d.nn);
+    gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v, d.flags, d.nn);
+    double E11[NS], E22[NS], Esh[NS];
+    strain_general<NS>(m, F, u, v, E11, E22, Esh);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Pc[s] = E11[s] + E22[s];
+      Qc[s] = r.ie * (E11[s] - E22[s]);
+      Gc[s] = r.ie * Esh[s];
+    }
+  }
+  double S11[NS], S12[NS], S22[NS];
+  const long long nsd = 3LL * d.ns * d.ne;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    S11[s] = ck_ld(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, nsd, 103);
+    S12[s] = ck_ld(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, nsd, 103);
+    S22[s] = ck_ld(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, nsd, 103);
+  }
+  if constexpr (VAR) {
+    constexpr int NG = N * N;
+    double Phg[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      Phg[g] = ck_ldg(d.flags, d.Pg, (long long)g * d.ne + K, (long long)NG * d.ne, 104) * r.hainv;
+    relax_general<NS, true>(m, F, S11, S12, S22, Pc, Qc, Gc, 0.0, r.dmin2, r.fac, r.ie, Phg);
+  } else {
+    const double Ph = ck_ldg(d.flags, d.Pe, (long long)K, (long long)d.ne, 104) * r.hainv;
+    relax_general<NS>(m, F, S11, S12, S22, Pc, Qc, Gc, Ph, r.dmin2, r.fac, r.ie);
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    ck_st(d.flags, d.S, (long long)(0 * NS + s) * d.ne + K, nsd, 105, S11[s]);
+    ck_st(d.flags, d.S, (long long)(1 * NS + s) * d.ne + K, nsd, 105, S12[s]);
+    ck_st(d.flags, d.S, (long long)(2 * NS + s) * d.ne + K, nsd, 105, S22[s]);
+  }
+  double fx[9], fy[9];
+  forces_general<NS>(m, S11, S12, S22, fx, fy);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    ck_st(d.flags, d.fbuf, (long long)j * d.ne + K, 18LL * d.ne, 106, fx[j]);
+    ck_st(d.flags, d.fbuf, (long long)(9 + j) * d.ne + K, 18LL * d.ne, 106, fy[j]);
+  }
+}
+
+template <int NS>
+constexpr size_t iso_smem() {
+  return sizeof(double) * 4 * DgSpace<NS>::NGP * DgSpace<NS>::NGP * kIsoBlock;
+}
+
+template <int NS, bool VAR>
+__global__ void __launch_bounds__(kIsoBlock) k_element_iso(DevState d, Rheo r, int cur) {
+  extern __shared__ double iso_sm[];
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K < d.ne) elem_iso<NS, VAR>(d, r, cur, K, iso_sm);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kIsoBlock) k_strain_diag_iso(DevState d, int cur) {
+  extern __shared__ double iso_sm[];
+  constexpr int N = DgSpace<NS>::NGP;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const IsoGeo<N, double> m = iso_geometry<N>(d, kx, ky, iso_sm);
+  MassFactor<NS> F;
+  mass_factor<NS>(m, F);
+  double u[9], v[9];
+  gather9(d.vel[cur], d.nw, kx, ky, u, d.flags, d.nn);
+  gather9(d.vel[cur] + d.nn, d.nw, kx, ky, v, d.flags, d.nn);
+  double E11[NS], E22[NS], Esh[NS];
+  strain_general<NS>(m, F, u, v, E11, E22, Esh);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    d.diag[(size_t)(0 * NS + s) * d.ne + K] = E11[s];
+    d.diag[(size_t)(1 * NS + s) * d.ne + K] = 0.5 * Esh[s];
+    d.diag[(size_t)(2 * NS + s) * d.ne + K] = E22[s];
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kIsoBlock) k_force_elem_iso(DevState d) {
+  extern __shared__ double iso_sm[];
+  constexpr int N = DgSpace<NS>::NGP;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const IsoGeo<N, double> m = iso_geometry<N>(d, kx, ky, iso_sm);
+  double S11[NS], S12[NS], S22[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    S11[s] = d.S[(size_t)(0 * NS + s) * d.ne + K];
+    S12[s] = d.S[(size_t)(1 * NS + s) * d.ne + K];
+    S22[s] = d.S[(size_t)(2 * NS + s) * d.ne + K];
+  }
+  double fx[9], fy[9];
+  forces_general<NS>(m, S11, S12, S22, fx, fy);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    d.fbuf[(size_t)j * d.ne + K] = fx[j];
+    d.fbuf[(size_t)(9 + j) * d.ne + K] = fy[j];
+  }
+}
+
 inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
+template <int NS, bool VAR>
+void launch_iso_ns(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
+  k_element_iso<NS, VAR><<<blocks(d.ne, kIsoBlock), kIsoBlock, iso_smem<NS>(), st>>>(d, r, cur);
+}
+
 }  // namespace
+
+cudaError_t setup_iso_kernels() {
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_element_iso<3, false>, at, (int)iso_smem<3>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<3, true>, at, (int)iso_smem<3>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<6, false>, at, (int)iso_smem<6>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<6, true>, at, (int)iso_smem<6>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<8, false>, at, (int)iso_smem<8>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<8, true>, at, (int)iso_smem<8>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strain_diag_iso<3>, at, (int)iso_smem<3>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strain_diag_iso<6>, at, (int)iso_smem<6>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strain_diag_iso<8>, at, (int)iso_smem<8>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_force_elem_iso<3>, at, (int)iso_smem<3>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_force_elem_iso<6>, at, (int)iso_smem<6>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_force_elem_iso<8>, at, (int)iso_smem<8>());
+  return e;
+}
+
+cudaError_t launch_element_iso(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
+  const bool var = d.na > 1;
+  if (d.ns == 3)
+    var ? launch_iso_ns<3, true>(d, r, cur, st) : launch_iso_ns<3, false>(d, r, cur, st);
+  else if (d.ns == 6)
+    var ? launch_iso_ns<6, true>(d, r, cur, st) : launch_iso_ns<6, false>(d, r, cur, st);
+  else
+    var ? launch_iso_ns<8, true>(d, r, cur, st) : launch_iso_ns<8, false>(d, r, cur, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_strain_diag_iso(const DevState &d, int cur, cudaStream_t st) {
+  const int g = blocks(d.ne, kIsoBlock);
+  if (d.ns == 3)
+    k_strain_diag_iso<3><<<g, kIsoBlock, iso_smem<3>(), st>>>(d, cur);
+  else if (d.ns == 6)
+    k_strain_diag_iso<6><<<g, kIsoBlock, iso_smem<6>(), st>>>(d, cur);
+  else
+    k_strain_diag_iso<8><<<g, kIsoBlock, iso_smem<8>(), st>>>(d, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_elem_iso(const DevState &d, cudaStream_t st) {
+  const int g = blocks(d.ne, kIsoBlock);
+  if (d.ns == 3)
+    k_force_elem_iso<3><<<g, kIsoBlock, iso_smem<3>(), st>>>(d);
+  else if (d.ns == 6)
+    k_force_elem_iso<6><<<g, kIsoBlock, iso_smem<6>(), st>>>(d);
+  else
+    k_force_elem_iso<8><<<g, kIsoBlock, iso_smem<8>(), st>>>(d);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
   const int g = blocks(d.ne, kGenBlock);

@@ -93,6 +93,26 @@ __device__ __forceinline__ void jac_at(const QuadMapT<T> &m, int gx, int gy, T &
   j11 = xh == 0.0 ? m.By : fma(m.cy, (T)xh, m.By);
 }
 
+// Isoparametric (Q2) element: the element map is the CG2 interpolant of the
+// element's 9 node positions (Sec. 2.1: the map from the velocity's space).
+// Its Jacobian at the N x N Gauss points is formed once per element and kept
+// in shared memory, one column per thread: entry q (J00, J01, J10, J11) of
+// point g at sJ[(q * N * N + g) * stride].
+template <int N, typename T> struct IsoGeo {
+  const T *sJ;
+  int stride;
+};
+
+template <int N, typename T>
+__device__ __forceinline__ void jac_at(const IsoGeo<N, T> &m, int gx, int gy, T &j00, T &j01,
+                                       T &j10, T &j11) {
+  const int g = gx + N * gy, NG = N * N;
+  j00 = m.sJ[(0 * NG + g) * m.stride];
+  j01 = m.sJ[(1 * NG + g) * m.stride];
+  j10 = m.sJ[(2 * NG + g) * m.stride];
+  j11 = m.sJ[(3 * NG + g) * m.stride];
+}
+
 // Reference gradients (d/dxi, d/deta) of a Q2 field at the N x N Gauss
 // points, sum-factorised: row sums along xi, then columns along eta.
 template <int N, typename T>
@@ -171,27 +191,70 @@ template <int NS, typename T = double> struct MassFactor {
   __device__ __forceinline__ T at(int i, int k) const { return L[i * (i - 1) / 2 + k]; }
 };
 
-template <int NS, typename T>
-__device__ __forceinline__ void mass_factor(const QuadMapT<T> &m, MassFactor<NS, T> &F) {
-  const T d0 = m.d0(), d1 = m.d1(), d2 = m.d2();
+// L D L^T of a symmetric positive definite NS x NS matrix given by the
+// functor Mij(i, j) (i >= j).
+template <int NS, typename T, typename MF>
+__device__ __forceinline__ void ldl_factor(const MF &Mij, MassFactor<NS, T> &F) {
   T D[NS];
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    T dj = d0 * (T)dgmass(j);
+    T dj = Mij(j, j);
 #pragma unroll
     for (int k = 0; k < j; ++k) dj = fma(-F.at(j, k) * D[k], F.at(j, k), dj);
     D[j] = dj;
     F.Dinv[j] = T(1) / dj;
 #pragma unroll
     for (int i = j + 1; i < NS; ++i) {
-      T a = T(0);
-      if (mx(i, j) != 0.0) a = d1 * (T)mx(i, j);
-      if (my(i, j) != 0.0) a = fma(d2, (T)my(i, j), a);
+      T a = Mij(i, j);
 #pragma unroll
       for (int k = 0; k < j; ++k) a = fma(-F.at(i, k) * D[k], F.at(j, k), a);
       F.at(i, j) = a * F.Dinv[j];
     }
   }
+}
+
+// Bilinear element: M = d0 diag(mass) + d1 MX + d2 MY with the exact moments.
+template <int NS, typename T>
+__device__ __forceinline__ void mass_factor(const QuadMapT<T> &m, MassFactor<NS, T> &F) {
+  const T d0 = m.d0(), d1 = m.d1(), d2 = m.d2();
+  ldl_factor<NS, T>(
+      [&](int i, int j) -> T {
+        if (i == j) return d0 * (T)dgmass(j);
+        T a = T(0);
+        if (mx(i, j) != 0.0) a = d1 * (T)mx(i, j);
+        if (my(i, j) != 0.0) a = fma(d2, (T)my(i, j), a);
+        return a;
+      },
+      F);
+}
+
+// Isoparametric element: M = sum_g w_g det J_g psi psi^T with the Gauss rule
+// of the stress space (the map makes det J rational-free but of higher
+// degree, so the rule is the method's own, as in the paper's iMJwPSI).
+template <int NS, typename T>
+__device__ __forceinline__ void mass_factor(const IsoGeo<DgSpace<NS>::NGP, T> &m,
+                                            MassFactor<NS, T> &F) {
+  constexpr int N = DgSpace<NS>::NGP, NG = N * N;
+  T wd[NG];
+#pragma unroll
+  for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) {
+      T j00, j01, j10, j11;
+      jac_at<N>(m, gx, gy, j00, j01, j10, j11);
+      wd[gx + N * gy] = (T)(Gauss<N>::w(gx) * Gauss<N>::w(gy)) * fma(j00, j11, -(j01 * j10));
+    }
+  ldl_factor<NS, T>(
+      [&](int i, int j) -> T {
+        T a = T(-0.0);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const double c = psi<NS>(i, g) * psi<NS>(j, g);
+          if (c != 0.0) a = cmul_acc(c, wd[g], a);
+        }
+        return a;
+      },
+      F);
 }
 
 // x <- M^-1 x with the factor above.
@@ -214,8 +277,8 @@ __device__ __forceinline__ void mass_solve(const MassFactor<NS, T> &F, T x[NS]) 
 // Strain of the nodal velocities u, v as DG coefficients:
 // E11 = M^-1 int psi du/dx, E22 = M^-1 int psi dv/dy,
 // Esh = M^-1 int psi (du/dy + dv/dx)  (= 2 E12).
-template <int NS, typename T>
-__device__ __forceinline__ void strain_general(const QuadMapT<T> &m, const MassFactor<NS, T> &F,
+template <int NS, typename G, typename T>
+__device__ __forceinline__ void strain_general(const G &m, const MassFactor<NS, T> &F,
                                                const T u[9], const T v[9], T E11[NS], T E22[NS],
                                                T Esh[NS]) {
   constexpr int N = DgSpace<NS>::NGP, NG = N * N;
@@ -251,8 +314,8 @@ __device__ __forceinline__ void strain_general(const QuadMapT<T> &m, const MassF
 // X = Ph / sqrt(Delta^2), Ph = P/(2 alpha) (invariant form of Listing 1).
 // VAR: per-Gauss-point strength Phg (DG1/DG2 H, A), whose -P/2 term is
 // projected with the rest; otherwise the element constant Ph.
-template <int NS, bool VAR = false, typename T = double>
-__device__ __forceinline__ void relax_general(const QuadMapT<T> &m, const MassFactor<NS, T> &F,
+template <int NS, bool VAR = false, typename T = double, typename G>
+__device__ __forceinline__ void relax_general(const G &m, const MassFactor<NS, T> &F,
                                               T S11[NS], T S12[NS], T S22[NS], const T Pc[NS],
                                               const T Qc[NS], const T Gc[NS], T Ph, T dmin2,
                                               T fac, T ie, const T *Phg = nullptr) {
@@ -297,8 +360,8 @@ __device__ __forceinline__ void relax_general(const QuadMapT<T> &m, const MassFa
 
 // Element forces f_j = -int sigma : grad phi_j of a DG stress on a general
 // element (fx[j], fy[j] for the 9 local Q2 nodes, j = a + 3b).
-template <int NS, typename T>
-__device__ __forceinline__ void forces_general(const QuadMapT<T> &m, const T S11[NS],
+template <int NS, typename G, typename T>
+__device__ __forceinline__ void forces_general(const G &m, const T S11[NS],
                                                const T S12[NS], const T S22[NS], T fx[9],
                                                T fy[9]) {
   constexpr int N = DgSpace<NS>::NGP, NG = N * N;

@@ -28,6 +28,8 @@ struct mevp_mesh {
   std::vector<double> yline;  // ny+1 vertex y coordinates
   bool general = false;       // vertices not on a rectilinear grid
   std::vector<double> xy;     // general mesh: [(nx+1)(ny+1)][2] vertex coordinates
+  bool iso = false;           // isoparametric: geometry from the CG2 node positions
+  std::vector<double> nxy;    // isoparametric mesh: [(2nx+1)(2ny+1)][2] node positions
 };
 
 namespace mevp {
@@ -72,6 +74,7 @@ struct DevState {
   int nsm;             // SMs of the device (grid of the persistent kernels)
   const double *xline, *yline;
   const double2 *xy;   // general mesh: [(nx+1)(ny+1)] vertices; NULL on rectilinear meshes
+  const double2 *nxy;  // isoparametric mesh: [nn] CG2 node positions; NULL otherwise
   double *lines;       // [hx: nx][1/hx: nx][hy: ny][1/hy: ny], from the mesh lines
   double *vel[2];      // [2][nn] ping-pong
   double *S;           // FP64: [3][ns][ne]
@@ -160,6 +163,11 @@ cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
 cudaError_t launch_strain_diag_general(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_elem_general(const DevState &d, cudaStream_t st);
+// isoparametric (Q2) meshes
+cudaError_t setup_iso_kernels();  // once per device, before any capture
+cudaError_t launch_element_iso(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
+cudaError_t launch_strain_diag_iso(const DevState &d, int cur, cudaStream_t st);
+cudaError_t launch_force_elem_iso(const DevState &d, cudaStream_t st);
 
 // FP64 ensemble: persistent element kernel (block size chosen from
 // kF64Blocks) + persistent node kernel (256 threads), over their work lists

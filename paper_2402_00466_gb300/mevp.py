@@ -65,6 +65,7 @@ def load(build_if_stale: bool = True):
         sig = {
             "mevp_mesh_create": (i, [i, i, d, d, vp, pvp]),
             "mevp_mesh_destroy": (None, [vp]),
+            "mevp_mesh_create_nodes": (i, [i, i, vp, pvp]),
             "mevp_state_workspace_bytes": (i, [vp, i, i, i, ctypes.POINTER(sz)]),
             "mevp_state_create": (i, [vp, i, i, i, vp, vp, sz, pvp]),
             "mevp_state_destroy": (None, [vp]),
@@ -139,6 +140,15 @@ def mevp_mesh_create(nx: int, ny: int, Lx: float = 0.0, Ly: float = 0.0, vertex_
     _check(load().mevp_mesh_create(int(nx), int(ny), float(Lx), float(Ly),
                                    None if xy is None else ctypes.c_void_p(xy.ctypes.data),
                                    ctypes.byref(out)))
+    return out
+
+
+def mevp_mesh_create_nodes(nx: int, ny: int, node_xy):
+    """Isoparametric mesh from the CG2 node positions [(2nx+1)(2ny+1)][2]."""
+    out = ctypes.c_void_p()
+    xy = np.ascontiguousarray(node_xy, dtype=np.float64)
+    _check(load().mevp_mesh_create_nodes(int(nx), int(ny), ctypes.c_void_p(xy.ctypes.data),
+                                         ctypes.byref(out)))
     return out
 
 
@@ -300,7 +310,11 @@ class State:
         self.nn = (2 * nx + 1) * (2 * ny + 1)
         self.precision = {"fp64": MEVP_FP64, "mixed": MEVP_MIXED}[precision]
         Lx = Ly = float(L if L is not None else 0.0)
-        self.mesh = mevp_mesh_create(nx, ny, Lx, Ly, vertex_xy)
+        if vertex_xy is not None and np.asarray(vertex_xy).reshape(-1, 2).shape[0] == self.nn:
+            # the positions of every CG2 node: an isoparametric (curved) mesh
+            self.mesh = mevp_mesh_create_nodes(nx, ny, vertex_xy)
+        else:
+            self.mesh = mevp_mesh_create(nx, ny, Lx, Ly, vertex_xy)
         self.state = None
         nbytes = mevp_state_workspace_bytes(self.mesh, n_stress, n_adv, self.precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()

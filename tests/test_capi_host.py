@@ -123,6 +123,32 @@ def test_general_mesh_workspace():
         mevp.mevp_mesh_destroy(r)
 
 
+def test_isoparametric_mesh_validation():
+    """mesh_create_nodes: the CG2 node positions of curved elements; an
+    element whose map folds (det J <= 0 somewhere) is rejected; curved meshes
+    run in FP64 only."""
+    nx, ny = 3, 2
+    nodes = W.curved_nodes(nx, ny, 5, amp=0.08, L=3e3)
+    m = mevp.mevp_mesh_create_nodes(nx, ny, nodes)
+    try:
+        assert mevp.mevp_state_workspace_bytes(m, 6, 1, 0) > 0
+        with pytest.raises(mevp.MevpError) as e:
+            mevp.mevp_state_workspace_bytes(m, 6, 1, 1)
+        assert e.value.code == -7
+    finally:
+        mevp.mevp_mesh_destroy(m)
+    bad = nodes.copy()
+    nw = 2 * nx + 1
+    bad[1 * nw + 1] = bad[2 * nw + 2] + (400.0, 300.0)  # centre of element 0 pulled past a corner
+    with pytest.raises(mevp.MevpError) as e:
+        mevp.mevp_mesh_create_nodes(nx, ny, bad)
+    assert e.value.code == -1 and "det J" in str(e.value)
+    nan = nodes.copy()
+    nan[4, 0] = np.nan
+    with pytest.raises(mevp.MevpError):
+        mevp.mevp_mesh_create_nodes(nx, ny, nan)
+
+
 def test_null_state_calls_fail_cleanly():
     lib = mevp.load()
     assert lib.mevp_run_subcycles(None, 1) == -1

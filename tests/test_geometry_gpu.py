@@ -263,3 +263,102 @@ def test_general_mesh_refusals():
         with pytest.raises(mevp.MevpError) as e:
             mevp.Ensemble([st])
         assert e.value.code == -7
+
+
+# ---------------------------------------------------------------- isoparametric
+ISO_GEOMS = ["wavy_iso", "curved"]
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+@pytest.mark.parametrize("geometry", ISO_GEOMS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_iso_stages(n_s, geometry, shape):
+    """Curved (isoparametric Q2) elements: strain, forces and lumped mass
+    against the oracle."""
+    nx, ny = shape
+    case = W.small_case(nx, ny, n_s, seed=500 + nx, geometry=geometry)
+    rng = np.random.default_rng(nx * 13 + ny)
+    vel = case["vel0"] + rng.normal(0, 1e-3, case["vel0"].shape)
+    with make_state(case) as st:
+        st.set_velocity(vel)
+        E = st.strain()
+        st.set_velocity(case["vel0"])
+        F = st.force()
+        st.begin_step()
+        m = st.read("NODAL_MASS")
+    assert_close(E, oracle.strain(nx, ny, case["xy"], n_s, vel), "strain")
+    Fo = oracle.divergence(nx, ny, case["xy"], n_s, case["S0"])
+    scale = np.abs(case["S0"]).max() * (case["L"] / nx)
+    assert np.abs(F - Fo).max() <= 1e-13 * scale and errors(F, Fo)[0] <= 1e-11
+    mo, _ = oracle.lumped(nx, ny, case["xy"], n_s, 1, case["params"], case["H"])
+    assert_close(m, mo, "mass", 1e-13, 1e-13)
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+@pytest.mark.parametrize("geometry", ISO_GEOMS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_iso_subcycles(n_s, geometry, shape):
+    nx, ny = shape
+    case = W.small_case(nx, ny, n_s, seed=520 + nx + ny, geometry=geometry)
+    vg, Sg = gpu_run(case, 7)
+    vo, So = oracle_run(case, 7)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_iso_mesh_100_subcycles_from_rest():
+    """64 x 64 randomly curved isoparametric mesh, DG2, 100 subcycles."""
+    nx = ny = 64
+    case = W.small_case(nx, ny, 6, seed=531, geometry="curved", moving=False)
+    vg, Sg = gpu_run(case, 100)
+    vo, So = oracle_run(case, 100, openmp=True)
+    assert np.abs(vo).max() > 1e-3
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+
+
+def test_iso_with_bilinear_nodes_matches_the_vertex_mesh():
+    """Node positions that are the bilinear images of the vertices describe
+    the same elements as the vertex mesh: the two GPU paths agree."""
+    nx, ny = 17, 11
+    case = W.small_case(nx, ny, 6, seed=533, geometry="perturbed")
+    iso = dict(case, xy=W.node_coords(nx, ny, case["xy"]).T.copy())
+    va, Sa = gpu_run(case, 9)
+    vb, Sb = gpu_run(iso, 9)
+    assert_close(vb, va, "velocity", 1e-12, 1e-11)
+    assert_close(Sb, Sa, "stress", 1e-12, 1e-11)
+
+
+@pytest.mark.parametrize("n_a", [1, 3, 6])
+def test_iso_advection(n_a):
+    nx, ny = 19, 13
+    case = W.small_case(nx, ny, 6, seed=540 + n_a, geometry="curved")
+    ne = nx * ny
+    rng = np.random.default_rng(n_a)
+    H = np.vstack([rng.uniform(0.5, 1.5, ne)] + [rng.uniform(-0.2, 0.2, ne)] * (n_a - 1))
+    A = np.vstack([rng.uniform(0.8, 0.95, ne)] + [rng.uniform(-0.05, 0.05, ne)] * (n_a - 1))
+    vel = 3.0 * case["vel0"]
+    with mevp.State(nx, ny, 6, vertex_xy=case["xy"], n_adv=n_a, params=case["params"]) as st:
+        st.set_ice(H, A)
+        st.set_forcing(case["tau"])
+        st.set_velocity(vel)
+        st.advect(4)
+        Hg, Ag = st.read("H").reshape(n_a, ne), st.read("A").reshape(n_a, ne)
+    Ho, Ao = oracle.advect(nx, ny, case["xy"], n_a, vel, case["params"]["dt"], 4, H, A)
+    assert_close(Hg, Ho, "H")
+    assert_close(Ag, Ao, "A")
+
+
+def test_iso_refusals():
+    case = W.small_case(6, 5, 6, seed=545, geometry="curved")
+    with pytest.raises(mevp.MevpError) as e:
+        mevp.State(6, 5, 6, vertex_xy=case["xy"], params=case["params"], precision="mixed")
+    assert e.value.code == -7
+    with make_state(case) as st:
+        st.begin_step()
+        with pytest.raises(mevp.MevpError) as e:
+            st.adjoint_kinetic_energy(2, 1)
+        assert e.value.code == -7
+        with pytest.raises(mevp.MevpError) as e:
+            mevp.Ensemble([st])
+        assert e.value.code == -7
