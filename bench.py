@@ -48,6 +48,11 @@ ELEM_FLOPS = {3: 474, 6: 1055}
 # solves 198 + 198, invariants 24, Gauss evaluation 132 + 132, rheology 183,
 # update 61, force integrands 192, force sums 270.
 GEN_ELEM_FLOPS = {3: 1051, 6: 2362, 8: 2990}
+# Isoparametric (curved Q2) elements, k_element_iso: the same stages with the
+# Jacobians at the Gauss points formed once per element from the 9 node
+# positions (reference gradients 252, det J 27, weights 18) and the local
+# mass matrix by the Gauss rule instead of the exact moments.
+ISO_ELEM_FLOPS = {3: 1199, 6: 2724, 8: 3491}
 # Transport step (k_advect, rectilinear mesh), per element and Runge-Kutta
 # stage: volume terms at NQ x NQ points (velocity, contravariant flux,
 # traces, basis gradients), NQ points on each of the 4 edges (velocity,
@@ -346,12 +351,16 @@ def _roofline_for(precision, case, kt, total_ms, steps):
     common = {"element_kernel_ms_mean": el_s * 1e3, "node_kernel_ms_mean": nd_s * 1e3,
               "element_share_of_subcycle": el_ms / max(el_ms + nd_ms, 1e-12)}
     if precision == "fp64":
-        general = case.get("geometry", "uniform") != "uniform"
-        ach = (GEN_ELEM_FLOPS if general else ELEM_FLOPS)[ns] * ne / el_s / 1e12
+        geo = case.get("geometry", "uniform")
+        general = geo != "uniform"
+        iso = geo in ("wavy_iso", "curved")
+        table = ISO_ELEM_FLOPS if iso else (GEN_ELEM_FLOPS if general else ELEM_FLOPS)
+        ach = table[ns] * ne / el_s / 1e12
         bytes_sub = HBM_BYTES.get(("fp64", ns), 0) * ne
         return dict({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": f"k_element_gen<{ns}>" if general else f"k_element_f64<{ns}>",
+                     "kernel": (f"k_element_iso<{ns}>" if iso else f"k_element_gen<{ns}>")
+                               if general else f"k_element_f64<{ns}>",
                      "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
                      "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
                      "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak}, **common)
@@ -731,7 +740,8 @@ def _run_ours(a, torch, dist, ws, rank):
 
     variants = None
     general = case.get("geometry", "uniform") != "uniform"
-    if not a.no_variants and ws == 1:
+    iso = case.get("geometry", "uniform") in ("wavy_iso", "curved")
+    if not a.no_variants and ws == 1 and not iso:
         variants = {}
         other = "mixed" if a.precision == "fp64" else "fp64"
         mv = measure(mevp, torch, barrier, 1, case, other, a.steps, a.warmup, flush)

@@ -47,6 +47,10 @@ CONFIGS = {
     # stress after 100 subcycles on the 256x256 DG1 mesh, checkpoint every 10
     "adjoint256_dg1": dict(nx=256, ny=256, n_s=3, n_a=1, n_sub=100, ice="grf", seeds=(7, 8),
                            wind_seed=14, adjoint_every=10, vel_seed=16),
+    # the same curvilinear map at every CG2 node: 256x256 curved
+    # (isoparametric Q2) elements, DG2, 500 subcycles
+    "mesh256_dg2_iso": dict(nx=256, ny=256, n_s=6, n_a=1, n_sub=500, ice="grf", seeds=(2, 3),
+                            wind_seed=12, geometry="wavy_iso"),
     # transport of DG2 H and A on 1024x1024 quads with a smooth velocity held
     # fixed (the step before the subcycles); one advection step per bench step
     "advect1024_dg2": dict(nx=1024, ny=1024, n_s=6, n_a=6, n_sub=0, ice="grf", seeds=(4, 5),
@@ -178,7 +182,12 @@ def make_case(name: str, L: float = DOMAIN_M, params: dict | None = None):
     else:
         H, A = ice_grf(nx, ny, cfg["seeds"], L)
     geometry = cfg.get("geometry", "uniform")
-    xy = wavy_vertices(nx, ny, L=L) if geometry == "wavy" else uniform_vertices(nx, ny, L, L)
+    if geometry == "wavy":
+        xy = wavy_vertices(nx, ny, L=L)
+    elif geometry == "wavy_iso":
+        xy = wavy_nodes(nx, ny, L=L)  # the CG2 node positions
+    else:
+        xy = uniform_vertices(nx, ny, L, L)
     n_a = cfg["n_a"]
     if n_a > 1:
         # DG1/DG2 ice: the random-field means plus seeded slopes and curvatures
@@ -188,7 +197,8 @@ def make_case(name: str, L: float = DOMAIN_M, params: dict | None = None):
         Hd[1:] = rng.uniform(-0.1, 0.1, (n_a - 1, ne))
         Ad[1:] = rng.uniform(-0.02, 0.02, (n_a - 1, ne))
         H, A = Hd, Ad
-    tau = cyclone_wind_stress(node_coords(nx, ny, xy), cyclone_params(cfg["wind_seed"], L))
+    ncoord = xy.T if xy.shape[0] == nn else node_coords(nx, ny, xy)
+    tau = cyclone_wind_stress(ncoord, cyclone_params(cfg["wind_seed"], L))
     vel0 = (smooth_velocity(nx, ny, cfg["vel_seed"], amp=0.3, L=L) if "vel_seed" in cfg
             else np.zeros((2, nn)))
     return dict(name=name, nx=nx, ny=ny, n_s=cfg["n_s"], n_a=n_a, n_sub=cfg["n_sub"],
@@ -303,12 +313,18 @@ def wavy_nodes(nx: int, ny: int, amp: float = 0.3, L: float = DOMAIN_M):
     return out
 
 
-def curved_nodes(nx: int, ny: int, seed: int, amp: float = 0.08, L: float = DOMAIN_M):
+def curved_nodes(nx: int, ny: int, seed: int, amp: float = 0.05, vamp: float = 0.1,
+                 L: float = DOMAIN_M):
     """CG2 node positions (N_n, 2) of a randomly curved mesh: the nodes of a
-    perturbed-vertex mesh, with every edge-midpoint and element-centre node
-    moved by U[-amp h, amp h] per coordinate (PCG64(seed)); boundary nodes
-    stay on the boundary."""
-    xy = perturbed_vertices(nx, ny, seed, L=L)
+    perturbed-vertex mesh (vertices moved by U[-vamp h, vamp h]), with every
+    edge-midpoint and element-centre node moved by U[-amp h, amp h] per
+    coordinate (PCG64(seed)); boundary nodes stay on the boundary.
+
+    At a corner the Q2 map's edge derivative is the edge vector plus 4 times
+    the midpoint's offset from the chord, and the centre node does not enter,
+    so det J there is at least h^2 (1 - 4 vamp - 8 amp) / 4 in the unit
+    square's coordinates: positive for the defaults, on any mesh size."""
+    xy = perturbed_vertices(nx, ny, seed, amp=vamp, L=L)
     nodes = node_coords(nx, ny, xy).T.reshape(2 * ny + 1, 2 * nx + 1, 2).copy()
     rng = np.random.Generator(np.random.PCG64(seed + 1))
     h = L / max(nx, ny)
