@@ -461,6 +461,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
     e = cudaMemcpyAsync((void *)d.nxy, mesh->nxy.data(), sizeof(double) * mesh->nxy.size(),
                         cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && mesh->iso) e = mevp::setup_iso_kernels();
+  if (e == cudaSuccess && mesh->general && !mesh->iso) e = mevp::setup_general_kernels();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) r2 = cuda_fail(e, "state_create: initialise workspace");
   if (r2) {

@@ -16,6 +16,17 @@ namespace {
 
 constexpr int kGenBlock = 128;
 
+// The element kernels of this file are persistent: the grid is the number of
+// blocks that fit on the chip at once (queried at state creation), and each
+// block takes an equal contiguous share of the element warps, which its warps
+// walk in turn.  A grid of one block per 128 elements ends in a partial wave
+// that leaves part of the chip idle (256x256: 512 blocks on 304 slots).
+__device__ __forceinline__ void warp_share(int ne, int &w0, int &w1) {
+  const int nwarps = (ne + 31) >> 5;
+  w0 = (int)((long long)nwarps * blockIdx.x / gridDim.x);
+  w1 = (int)((long long)nwarps * (blockIdx.x + 1) / gridDim.x);
+}
+
 template <int NS, bool VAR>
 __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int cur, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
@@ -70,8 +81,13 @@ __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int c
 
 template <int NS, bool VAR>
 __global__ void __launch_bounds__(kGenBlock) k_element_gen(DevState d, Rheo r, int cur) {
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K < d.ne) elem_gen<NS, VAR>(d, r, cur, K);
+  int w0, w1;
+  warp_share(d.ne, w0, w1);
+  const int lane = threadIdx.x & 31;
+  for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += kGenBlock / 32) {
+    const int K = (w << 5) + lane;
+    if (K < d.ne) elem_gen<NS, VAR>(d, r, cur, K);
+  }
 }
 
 // Strain coefficients E11, E12, E22 of the current velocity (read-back).
@@ -223,8 +239,13 @@ constexpr size_t iso_smem() {
 template <int NS, bool VAR>
 __global__ void __launch_bounds__(kIsoBlock) k_element_iso(DevState d, Rheo r, int cur) {
   extern __shared__ double iso_sm[];
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K < d.ne) elem_iso<NS, VAR>(d, r, cur, K, iso_sm);
+  int w0, w1;
+  warp_share(d.ne, w0, w1);
+  const int lane = threadIdx.x & 31;
+  for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += kIsoBlock / 32) {
+    const int K = (w << 5) + lane;
+    if (K < d.ne) elem_iso<NS, VAR>(d, r, cur, K, iso_sm);
+  }
 }
 
 template <int NS>
@@ -276,21 +297,65 @@ __global__ void __launch_bounds__(kIsoBlock) k_force_elem_iso(DevState d) {
 
 inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
+// Resident blocks per SM of the persistent element kernels, [NS index][VAR];
+// filled at state creation, 2 until then (the grid size only affects speed).
+int g_gen_resident[3][2] = {{2, 2}, {2, 2}, {2, 2}};
+int g_iso_resident[3][2] = {{2, 2}, {2, 2}, {2, 2}};
+
+constexpr int ns_index(int ns) { return ns == 3 ? 0 : ns == 6 ? 1 : 2; }
+
+inline int persistent_grid(const DevState &d, int resident, int block) {
+  const int need = blocks(d.ne, block);
+  const int fit = (resident > 0 ? resident : 1) * d.nsm;
+  return need < fit ? need : fit;
+}
+
+template <class Kernel>
+cudaError_t resident_blocks(Kernel k, int block, size_t smem, int &out) {
+  int n = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem);
+  if (e == cudaSuccess && n > 0) out = n;
+  return e;
+}
+
 template <int NS, bool VAR>
 void launch_iso_ns(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
-  k_element_iso<NS, VAR><<<blocks(d.ne, kIsoBlock), kIsoBlock, iso_smem<NS>(), st>>>(d, r, cur);
+  const int g = persistent_grid(d, g_iso_resident[ns_index(NS)][VAR], kIsoBlock);
+  k_element_iso<NS, VAR><<<g, kIsoBlock, iso_smem<NS>(), st>>>(d, r, cur);
+}
+
+template <int NS, bool VAR>
+void launch_gen_ns(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
+  const int g = persistent_grid(d, g_gen_resident[ns_index(NS)][VAR], kGenBlock);
+  k_element_gen<NS, VAR><<<g, kGenBlock, 0, st>>>(d, r, cur);
+}
+
+template <int NS, bool VAR>
+cudaError_t setup_iso_ns() {
+  cudaError_t e = cudaFuncSetAttribute(k_element_iso<NS, VAR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)iso_smem<NS>());
+  if (e == cudaSuccess)
+    e = resident_blocks(k_element_iso<NS, VAR>, kIsoBlock, iso_smem<NS>(),
+                        g_iso_resident[ns_index(NS)][VAR]);
+  return e;
+}
+
+template <int NS, bool VAR>
+cudaError_t setup_gen_ns() {
+  return resident_blocks(k_element_gen<NS, VAR>, kGenBlock, 0, g_gen_resident[ns_index(NS)][VAR]);
 }
 
 }  // namespace
 
 cudaError_t setup_iso_kernels() {
   const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_element_iso<3, false>, at, (int)iso_smem<3>());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<3, true>, at, (int)iso_smem<3>());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<6, false>, at, (int)iso_smem<6>());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<6, true>, at, (int)iso_smem<6>());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<8, false>, at, (int)iso_smem<8>());
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_element_iso<8, true>, at, (int)iso_smem<8>());
+  cudaError_t e = setup_iso_ns<3, false>();
+  if (e == cudaSuccess) e = setup_iso_ns<3, true>();
+  if (e == cudaSuccess) e = setup_iso_ns<6, false>();
+  if (e == cudaSuccess) e = setup_iso_ns<6, true>();
+  if (e == cudaSuccess) e = setup_iso_ns<8, false>();
+  if (e == cudaSuccess) e = setup_iso_ns<8, true>();
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strain_diag_iso<3>, at, (int)iso_smem<3>());
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strain_diag_iso<6>, at, (int)iso_smem<6>());
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strain_diag_iso<8>, at, (int)iso_smem<8>());
@@ -333,18 +398,24 @@ cudaError_t launch_force_elem_iso(const DevState &d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t setup_general_kernels() {
+  cudaError_t e = setup_gen_ns<3, false>();
+  if (e == cudaSuccess) e = setup_gen_ns<3, true>();
+  if (e == cudaSuccess) e = setup_gen_ns<6, false>();
+  if (e == cudaSuccess) e = setup_gen_ns<6, true>();
+  if (e == cudaSuccess) e = setup_gen_ns<8, false>();
+  if (e == cudaSuccess) e = setup_gen_ns<8, true>();
+  return e;
+}
+
 cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
-  const int g = blocks(d.ne, kGenBlock);
   const bool var = d.na > 1;
   if (d.ns == 3)
-    var ? k_element_gen<3, true><<<g, kGenBlock, 0, st>>>(d, r, cur)
-        : k_element_gen<3, false><<<g, kGenBlock, 0, st>>>(d, r, cur);
+    var ? launch_gen_ns<3, true>(d, r, cur, st) : launch_gen_ns<3, false>(d, r, cur, st);
   else if (d.ns == 6)
-    var ? k_element_gen<6, true><<<g, kGenBlock, 0, st>>>(d, r, cur)
-        : k_element_gen<6, false><<<g, kGenBlock, 0, st>>>(d, r, cur);
+    var ? launch_gen_ns<6, true>(d, r, cur, st) : launch_gen_ns<6, false>(d, r, cur, st);
   else
-    var ? k_element_gen<8, true><<<g, kGenBlock, 0, st>>>(d, r, cur)
-        : k_element_gen<8, false><<<g, kGenBlock, 0, st>>>(d, r, cur);
+    var ? launch_gen_ns<8, true>(d, r, cur, st) : launch_gen_ns<8, false>(d, r, cur, st);
   return cudaGetLastError();
 }
 

@@ -164,7 +164,8 @@ cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cu
 cudaError_t launch_strain_diag_general(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_elem_general(const DevState &d, cudaStream_t st);
 // isoparametric (Q2) meshes
-cudaError_t setup_iso_kernels();  // once per device, before any capture
+cudaError_t setup_iso_kernels();
+cudaError_t setup_general_kernels();  // once per device, before any capture
 cudaError_t launch_element_iso(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
 cudaError_t launch_strain_diag_iso(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_elem_iso(const DevState &d, cudaStream_t st);
