@@ -369,13 +369,18 @@ def _roofline_for(precision, case, kt, total_ms, steps):
     import torch
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     big = ((case["nx"] + 29) // 31) * ((case["ny"] + 5) // 7) >= 16 * nsm
-    general = case.get("geometry", "uniform") != "uniform"
-    extra = 24 if general else 0  # FP32 map record (A, B, c) per element
+    geo = case.get("geometry", "uniform")
+    general = geo != "uniform"
+    iso = geo in ("wavy_iso", "curved")
+    # FP32 map record (A, B, c) per bilinear element; 8 FP32 node offsets per
+    # isoparametric element
+    extra = 64 if iso else 24 if general else 0
     ach = (MIXED_SINGLE_PASS_BYTES[ns] + extra) * ne / el_s / 1e9
     own = (MIXED_OWN_BYTES[ns] + extra) * ne / el_s / 1e9
     return dict({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                  "frac": ach / hbm_peak, "traffic": None,
-                 "kernel": f"k_subcycle_mix{'_gen' if general else ''}<{ns},32,{8 if big else 4}>",
+                 "kernel": f"k_subcycle_mix{'_iso' if iso else '_gen' if general else ''}"
+                           f"<{ns},32,{8 if big else 4}>",
                  "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
                  "bytes_per_element": MIXED_SINGLE_PASS_BYTES[ns] + extra,
                  "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x (v R+W, v^n, tau, m)",
@@ -740,8 +745,7 @@ def _run_ours(a, torch, dist, ws, rank):
 
     variants = None
     general = case.get("geometry", "uniform") != "uniform"
-    iso = case.get("geometry", "uniform") in ("wavy_iso", "curved")
-    if not a.no_variants and ws == 1 and not iso:
+    if not a.no_variants and ws == 1:
         variants = {}
         other = "mixed" if a.precision == "fp64" else "fp64"
         mv = measure(mevp, torch, barrier, 1, case, other, a.steps, a.warmup, flush)

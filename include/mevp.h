@@ -134,7 +134,8 @@ MEVP_API int mevp_mesh_create(int nx, int ny, double Lx, double Ly, const double
  * velocity's finite element space (Sec. 2.1).  The local mass matrices use
  * the Gauss rule of App. A (det J is then a higher-degree polynomial).
  * MEVP_ERR_ARG for non-finite positions or an element whose det J is not
- * positive at its 5 x 5 reference sample points.  FP64 states only. */
+ * positive at its 5 x 5 reference sample points.  FP64 and mixed states
+ * (the mixed path keeps FP32 node offsets from each element's centre node). */
 MEVP_API int mevp_mesh_create_nodes(int nx, int ny, const double *node_xy, mevp_mesh **out);
 MEVP_API void mevp_mesh_destroy(mevp_mesh *mesh);
 

@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, iso32, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -87,6 +87,7 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.Pg32 = take(na > 1 && prec == MEVP_MIXED ? sizeof(float) * (ns == 3 ? 4 : 9) * ne : 0);
   L.map32ab = take(m->general && prec == MEVP_MIXED ? sizeof(float4) * ne : 0);
   L.map32c = take(m->general && prec == MEVP_MIXED ? sizeof(float2) * ne : 0);
+  L.iso32 = take(m->iso && prec == MEVP_MIXED ? 4 * sizeof(float4) * ne : 0);
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(sizeof(double) * 3 * ns * ne);
@@ -340,9 +341,6 @@ int mevp_state_workspace_bytes(const mevp_mesh *mesh, int n_stress, int n_adv, i
     return fail(MEVP_ERR_ARG, "n_adv=%d: H, A need 1, 3 or 6 dofs (DG0, DG1, DG2)", n_adv);
   if (precision != MEVP_FP64 && precision != MEVP_MIXED)
     return fail(MEVP_ERR_ARG, "precision=%d unknown", precision);
-  if (mesh->iso && precision != MEVP_FP64)
-    return fail(MEVP_ERR_UNSUPPORTED,
-                "precision=%d: isoparametric (curved) meshes run in FP64 only", precision);
   *bytes = make_layout(mesh, n_stress, n_adv, precision).total;
   return MEVP_OK;
 }
@@ -442,6 +440,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
     d.Pg32 = (float *)(b + L.Pg32);
     d.map32ab = (float4 *)(b + L.map32ab);
     d.map32c = (float2 *)(b + L.map32c);
+    d.iso32 = mesh->iso ? (float4 *)(b + L.iso32) : nullptr;
     d.nodec4 = (float4 *)(b + L.nodec32);
     d.vo2 = (float2 *)(b + L.vo2);
     d.lines32 = (float2 *)(b + L.lines32);

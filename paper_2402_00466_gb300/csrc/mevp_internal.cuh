@@ -97,6 +97,7 @@ struct DevState {
   float *Pg32;         // [NGP^2][ne] (DG1/DG2 H, A)
   float4 *map32ab;     // general mesh: [ne] (Ax, Ay, Bx, By) of the element map
   float2 *map32c;      // general mesh: [ne] (cx, cy)
+  float4 *iso32;       // curved mesh: [4][ne] node offsets from the centre node
   float4 *nodec4;      // [nn] (m/dt, qx, qy, l Cw rho_w) records
   float2 *vo2;         // [nn] ocean velocity
   float2 *lines32;     // [nx + ny] (h, 1/h) per mesh column, then per row

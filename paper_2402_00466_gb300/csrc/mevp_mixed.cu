@@ -88,15 +88,19 @@ __device__ __forceinline__ Strength<NS, VAR> load_strength(const DevState &d, co
   return p;
 }
 
-// The same element step on a general (bilinear) element: the map in FP32
-// from the per-element record (A, B, c) of the preparation, the local mass
+// Element geometry of the mixed kernels: mesh lines (rectangles), bilinear
+// map records, or isoparametric node records.
+constexpr int kGeoRect = 0, kGeoQuad = 1, kGeoIso = 2;
+
+// The same element step on a general element: the map in FP32 from the
+// per-element record of the preparation (bilinear QuadMapT, or the Jacobians
+// at the Gauss points of an isoparametric element, IsoGeo), the local mass
 // matrix factored per element (the FP64 general path's arithmetic in FP32).
-template <int NS, bool VAR>
+template <int NS, bool VAR, typename G>
 __device__ __forceinline__ void element_core_general(const float4 pv[9], float S11[NS],
                                                      float S12[NS], float S22[NS],
-                                                     const Strength<NS, VAR> &P,
-                                                     const QuadMapT<float> &m, const MixArgs &a,
-                                                     float fx[9], float fy[9]) {
+                                                     const Strength<NS, VAR> &P, const G &m,
+                                                     const MixArgs &a, float fx[9], float fy[9]) {
   float du[9], dv[9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
@@ -133,6 +137,53 @@ __device__ __forceinline__ QuadMapT<float> map_record(const DevState &d, size_t 
   m.cx = c.x;
   m.cy = c.y;
   return m;
+}
+
+// FP32 node record of an isoparametric element: its 8 non-centre node
+// positions minus the centre node's, as four float4 planes holding the node
+// pairs (0,1), (2,3), (5,6), (7,8).  The centre node drops out of J because
+// the Q2 reference gradients sum to zero, and the offsets (about h) keep FP32's
+// relative precision where absolute coordinates (~5e5 m) would lose it.  The
+// Jacobian at the N x N Gauss points goes to this thread's shared-memory
+// column col[(q * N * N + g) * stride], as in the FP64 isoparametric kernel.
+template <int N>
+__device__ __forceinline__ IsoGeo<N, float> iso_record(const DevState &d, size_t K, float *col,
+                                                       int stride) {
+  constexpr int NG = N * N;
+  float X[9], Y[9];
+  const long long ne = d.ne, n4 = 4LL * d.ne;
+  const float4 r0 = ck_ldg(d.flags, (const float4 *)d.iso32, (long long)K, n4, 163);
+  const float4 r1 = ck_ldg(d.flags, (const float4 *)d.iso32, ne + (long long)K, n4, 163);
+  const float4 r2 = ck_ldg(d.flags, (const float4 *)d.iso32, 2 * ne + (long long)K, n4, 163);
+  const float4 r3 = ck_ldg(d.flags, (const float4 *)d.iso32, 3 * ne + (long long)K, n4, 163);
+  X[0] = r0.x; Y[0] = r0.y; X[1] = r0.z; Y[1] = r0.w;
+  X[2] = r1.x; Y[2] = r1.y; X[3] = r1.z; Y[3] = r1.w;
+  X[4] = 0.f;  Y[4] = 0.f;
+  X[5] = r2.x; Y[5] = r2.y; X[6] = r2.z; Y[6] = r2.w;
+  X[7] = r3.x; Y[7] = r3.y; X[8] = r3.z; Y[8] = r3.w;
+  {  // one coordinate at a time, to keep the live registers down
+    float gxi[NG], geta[NG];
+    ref_grad_gauss<N>(X, gxi, geta);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      col[(0 * NG + g) * stride] = gxi[g];
+      col[(1 * NG + g) * stride] = geta[g];
+    }
+  }
+  float gxi[NG], geta[NG];
+  ref_grad_gauss<N>(Y, gxi, geta);
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    col[(2 * NG + g) * stride] = gxi[g];
+    col[(3 * NG + g) * stride] = geta[g];
+  }
+  return IsoGeo<N, float>{col, stride};
+}
+
+// Shared memory of the isoparametric Jacobian columns: 4 N^2 floats a thread.
+template <int NS>
+constexpr size_t iso_cols_bytes(int threads) {
+  return sizeof(float) * 4 * DgSpace<NS>::NGP * DgSpace<NS>::NGP * threads;
 }
 
 template <int NS, bool VAR>
@@ -190,8 +241,9 @@ __device__ __forceinline__ void line_geometry(const DevState &d, int kx, int ky,
   ihy = gy.y;
 }
 
-template <int NS, bool VAR, bool GEN>
+template <int NS, bool VAR, int GEO>
 __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs a, int cur) {
+  extern __shared__ float jcols[];  // isoparametric elements only
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= d.ne) return;
   const int ky = K / d.nx, kx = K - ky * d.nx;
@@ -206,7 +258,11 @@ __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs 
   float S11[NS], S12[NS], S22[NS];
   load_stress<NS>(d, cur, K, S11, S12, S22);
   float fx[9], fy[9];
-  if constexpr (GEN) {
+  if constexpr (GEO == kGeoIso) {
+    const auto m = iso_record<DgSpace<NS>::NGP>(d, K, jcols + threadIdx.x, blockDim.x);
+    element_core_general<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K), m, a, fx,
+                                  fy);
+  } else if constexpr (GEO == kGeoQuad) {
     element_core_general<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K),
                                   map_record(d, K), a, fx, fy);
   } else {
@@ -349,7 +405,7 @@ template <int TX, int TY> struct Tile {
   static constexpr size_t smem = sizeof(float4) * 2 * NW * NH + sizeof(float2) * 9 * TX * TY;
 };
 
-template <int NS, int TX, int TY, bool VAR = false, bool GEN = false>
+template <int NS, int TX, int TY, bool VAR = false, int GEO = kGeoRect>
 __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, int cur, int bx,
                                          int by, float4 *smem) {
   constexpr int TNW = Tile<TX, TY>::NW, TNH = Tile<TX, TY>::NH;
@@ -388,7 +444,12 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
       for (int c = 0; c < 3; ++c)
         pv[c + 3 * b] = ck_ldg(d.flags, vel, (long long)(base + (size_t)b * d.nw + c), d.nn, 151);
     float fx[9], fy[9];
-    if constexpr (GEN) {
+    if constexpr (GEO == kGeoIso) {
+      // Jacobian columns after the tile's own shared memory
+      float *jc = (float *)((char *)smem + Tile<TX, TY>::smem) + tid;
+      const auto m = iso_record<DgSpace<NS>::NGP>(d, K, jc, TX * TY);
+      element_core_general<NS, VAR>(pv, S11, S12, S22, P, m, ma, fx, fy);
+    } else if constexpr (GEO == kGeoQuad) {
       element_core_general<NS, VAR>(pv, S11, S12, S22, P, map_record(d, K), ma, fx, fy);
     } else {
       float hx, ihx, hy, ihy;
@@ -471,14 +532,29 @@ template <int NS, int TX, int TY, bool VAR>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
     k_subcycle_mix_gen(DevState d, MixArgs ma, int cur) {
   extern __shared__ float4 smem[];
-  mix_tile<NS, TX, TY, VAR, true>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+  mix_tile<NS, TX, TY, VAR, kGeoQuad>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+}
+
+// Isoparametric elements: as the bilinear kernel, with the Jacobians at the
+// Gauss points in shared memory after the tile's buffers.
+template <int NS, int TX, int TY, bool VAR>
+__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
+    k_subcycle_mix_iso(DevState d, MixArgs ma, int cur) {
+  extern __shared__ float4 smem[];
+  mix_tile<NS, TX, TY, VAR, kGeoIso>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
 }
 
 template <int NS, int TX, int TY>
 cudaError_t launch_fused(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {
   const dim3 grid((d.nx + TX - 2) / (TX - 1), (d.ny + TY - 2) / (TY - 1));
   const size_t sm = Tile<TX, TY>::smem;
-  if (d.xy) {
+  if (d.nxy) {
+    const size_t smi = sm + iso_cols_bytes<NS>(TX * TY);
+    if (d.na > 1)
+      k_subcycle_mix_iso<NS, TX, TY, true><<<grid, dim3(TX, TY), smi, st>>>(d, a, cur);
+    else
+      k_subcycle_mix_iso<NS, TX, TY, false><<<grid, dim3(TX, TY), smi, st>>>(d, a, cur);
+  } else if (d.xy) {
     if (d.na > 1)
       k_subcycle_mix_gen<NS, TX, TY, true><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
     else
@@ -499,6 +575,9 @@ cudaError_t fused_attribute() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix<NS, TX, TY, true>, at, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix_gen<NS, TX, TY, false>, at, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix_gen<NS, TX, TY, true>, at, sm);
+  const int smi = sm + (int)iso_cols_bytes<NS>(TX * TY);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix_iso<NS, TX, TY, false>, at, smi);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subcycle_mix_iso<NS, TX, TY, true>, at, smi);
   return e;
 }
 
@@ -582,6 +661,26 @@ __global__ void k_consts_to_f32(DevState d, double dt, int has_vo) {
       for (int g = 0; g < ng; ++g)
         d.Pg32[(size_t)g * d.ne + i] = __double2float_rn(d.Pg[(size_t)g * d.ne + i]);
     }
+  }
+  if (d.nxy && d.iso32 && i < (size_t)d.ne) {  // curved mesh: FP32 node offsets
+    const int ky = (int)(i / d.nx), kx = (int)(i - (size_t)ky * d.nx);
+    const long long base = (long long)(2 * ky) * d.nw + 2 * kx;
+    double2 p[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        p[a + 3 * b] = ck_ldg(d.flags, d.nxy, base + (long long)b * d.nw + a, d.nn, 164);
+    float o[18];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      o[2 * q] = __double2float_rn(p[q].x - p[4].x);
+      o[2 * q + 1] = __double2float_rn(p[q].y - p[4].y);
+    }
+    d.iso32[i] = make_float4(o[0], o[1], o[2], o[3]);
+    d.iso32[(size_t)d.ne + i] = make_float4(o[4], o[5], o[6], o[7]);
+    d.iso32[2 * (size_t)d.ne + i] = make_float4(o[10], o[11], o[12], o[13]);
+    d.iso32[3 * (size_t)d.ne + i] = make_float4(o[14], o[15], o[16], o[17]);
   }
   if (d.xy && i < (size_t)d.ne) {  // general mesh: FP32 map record per element
     const int ky = (int)(i / d.nx), kx = (int)(i - (size_t)ky * d.nx);
@@ -705,10 +804,13 @@ MixArgs make_mixargs(const Rheo &r, const mevp_params &p, bool has_vo) {
 template <int NS, bool VAR>
 void launch_element_mix_ns(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {
   const int eg = blocks(d.ne, kElemBlock);
-  if (d.xy)
-    k_element_mix<NS, VAR, true><<<eg, kElemBlock, 0, st>>>(d, a, cur);
+  if (d.nxy)
+    k_element_mix<NS, VAR, kGeoIso>
+        <<<eg, kElemBlock, iso_cols_bytes<NS>(kElemBlock), st>>>(d, a, cur);
+  else if (d.xy)
+    k_element_mix<NS, VAR, kGeoQuad><<<eg, kElemBlock, 0, st>>>(d, a, cur);
   else
-    k_element_mix<NS, VAR, false><<<eg, kElemBlock, 0, st>>>(d, a, cur);
+    k_element_mix<NS, VAR, kGeoRect><<<eg, kElemBlock, 0, st>>>(d, a, cur);
 }
 
 void launch_element_mix(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {

@@ -48,6 +48,26 @@ def run_all():
                     st.sync()
                     out[f"mixed_{n_s}_{fused}_v"], out[f"mixed_{n_s}_{fused}_S"] = (
                         st.velocity(), st.stress())
+        for n_s in (3, 6, 8):  # curved meshes, FP64 and mixed (fused and two-kernel)
+            case = W.small_case(37, 23, n_s, seed=350 + n_s, geometry="curved")
+            for prec, fused in (("fp64", 1), ("mixed", 1), ("mixed", 0)):
+                with state(case, prec) as st:
+                    st.set_option(mevp.MEVP_OPT_FUSED, fused)
+                    st.begin_step()
+                    st.run_subcycles(5)
+                    st.sync()
+                    key = f"iso_{prec}_{n_s}_{fused}"
+                    out[key + "_v"], out[key + "_S"] = st.velocity(), st.stress()
+                    out[key + "_E"], out[key + "_F"] = st.strain(), st.force()
+        for n_s in (3, 6, 8):  # bilinear general meshes, mixed
+            case = W.small_case(37, 23, n_s, seed=355 + n_s, geometry="wavy")
+            for fused in (1, 0):
+                with state(case, "mixed") as st:
+                    st.set_option(mevp.MEVP_OPT_FUSED, fused)
+                    st.begin_step()
+                    st.run_subcycles(5)
+                    st.sync()
+                    out[f"gen_mixed_{n_s}_{fused}_v"] = st.velocity()
         for n_a in (1, 3, 6):
             case = W.small_case(21, 13, 6, seed=320 + n_a, geometry="perturbed")
             ne = 21 * 13

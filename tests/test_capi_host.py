@@ -125,16 +125,19 @@ def test_general_mesh_workspace():
 
 def test_isoparametric_mesh_validation():
     """mesh_create_nodes: the CG2 node positions of curved elements; an
-    element whose map folds (det J <= 0 somewhere) is rejected; curved meshes
-    run in FP64 only."""
+    element whose map folds (det J <= 0 somewhere) is rejected; the mixed
+    workspace adds the FP32 node-offset records (4 float4 per element)."""
     nx, ny = 3, 2
     nodes = W.curved_nodes(nx, ny, 5, amp=0.08, L=3e3)
     m = mevp.mevp_mesh_create_nodes(nx, ny, nodes)
     try:
         assert mevp.mevp_state_workspace_bytes(m, 6, 1, 0) > 0
-        with pytest.raises(mevp.MevpError) as e:
-            mevp.mevp_state_workspace_bytes(m, 6, 1, 1)
-        assert e.value.code == -7
+        mixed = mevp.mevp_state_workspace_bytes(m, 6, 1, 1)
+        r = mevp.mevp_mesh_create(nx, ny, 3e3, 3e3)
+        try:
+            assert mixed >= mevp.mevp_state_workspace_bytes(r, 6, 1, 1) + 64 * nx * ny
+        finally:
+            mevp.mevp_mesh_destroy(r)
     finally:
         mevp.mevp_mesh_destroy(m)
     bad = nodes.copy()

@@ -351,9 +351,6 @@ def test_iso_advection(n_a):
 
 def test_iso_refusals():
     case = W.small_case(6, 5, 6, seed=545, geometry="curved")
-    with pytest.raises(mevp.MevpError) as e:
-        mevp.State(6, 5, 6, vertex_xy=case["xy"], params=case["params"], precision="mixed")
-    assert e.value.code == -7
     with make_state(case) as st:
         st.begin_step()
         with pytest.raises(mevp.MevpError) as e:
@@ -362,3 +359,73 @@ def test_iso_refusals():
         with pytest.raises(mevp.MevpError) as e:
             mevp.Ensemble([st])
         assert e.value.code == -7
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+@pytest.mark.parametrize("geometry", ISO_GEOMS)
+@pytest.mark.parametrize("shape", [(1, 1), (37, 23), (130, 5)])
+def test_mixed_iso_mesh(n_s, geometry, shape):
+    """The mixed path on curved (isoparametric) meshes: FP32 node offsets from
+    the centre node, Jacobians at the Gauss points in shared memory; fused
+    and two-kernel launches bitwise equal, and within the mixed path's stated
+    tolerances of the FP64 oracle (velocity 5e-6 / 3e-5, stress 5e-5 / 2e-4)."""
+    nx, ny = shape
+    case = W.small_case(nx, ny, n_s, seed=560 + n_s + nx, geometry=geometry)
+    got = []
+    for fused in (1, 0):
+        with mevp.State(nx, ny, n_s, vertex_xy=case["xy"], params=case["params"],
+                        precision="mixed") as st:
+            st.set_option(mevp.MEVP_OPT_FUSED, fused)
+            st.set_ice(case["H"], case["A"])
+            st.set_forcing(case["tau"])
+            st.set_velocity(case["vel0"])
+            st.set_stress(case["S0"])
+            st.begin_step()
+            st.run_subcycles(7)
+            got.append((st.velocity(), st.stress()))
+    assert np.array_equal(got[0][0], got[1][0]) and np.array_equal(got[0][1], got[1][1])
+    vo, So = oracle_run(case, 7)
+    assert_close(got[0][0], vo, "velocity", 5e-6, 3e-5)
+    assert_close(got[0][1], So, "stress", 5e-5, 2e-4)
+
+
+@pytest.mark.parametrize("n_a", [3, 6])
+def test_mixed_iso_with_dg_ice(n_a):
+    """Mixed path, curved mesh, DG1/DG2 H and A (FP32 strength per Gauss
+    point)."""
+    nx, ny = 23, 17
+    case = W.small_case(nx, ny, 6, seed=570 + n_a, geometry="curved")
+    ne = nx * ny
+    rng = np.random.default_rng(571 + n_a)
+    H = np.vstack([rng.uniform(0.5, 1.8, ne)] + [rng.uniform(-0.3, 0.3, ne)] * (n_a - 1))
+    A = np.vstack([rng.uniform(0.75, 0.97, ne)] + [rng.uniform(-0.08, 0.08, ne)] * (n_a - 1))
+    with mevp.State(nx, ny, 6, vertex_xy=case["xy"], n_adv=n_a, params=case["params"],
+                    precision="mixed") as st:
+        st.set_ice(H, A)
+        st.set_forcing(case["tau"])
+        st.set_velocity(case["vel0"])
+        st.set_stress(case["S0"])
+        st.begin_step()
+        st.run_subcycles(7)
+        vg, Sg = st.velocity(), st.stress()
+    vo, So = oracle.subcycles(nx, ny, case["xy"], 6, n_a, case["params"], H, A, case["tau"],
+                              case["vel0"], case["S0"], 7)
+    assert_close(vg, vo, "velocity", 5e-6, 3e-5)
+    assert_close(Sg, So, "stress", 5e-5, 2e-4)
+
+
+def test_mixed_iso_mesh_100_subcycles_from_rest():
+    """64 x 64 curved mesh, DG2, mixed path, 100 subcycles from rest."""
+    nx = ny = 64
+    case = W.small_case(nx, ny, 6, seed=575, geometry="wavy_iso", moving=False)
+    with mevp.State(nx, ny, 6, vertex_xy=case["xy"], params=case["params"],
+                    precision="mixed") as st:
+        st.set_ice(case["H"], case["A"])
+        st.set_forcing(case["tau"])
+        st.begin_step()
+        st.run_subcycles(100)
+        vg, Sg = st.velocity(), st.stress()
+    vo, So = oracle_run(case, 100, openmp=True)
+    assert np.abs(vo).max() > 1e-3
+    assert_close(vg, vo, "velocity", 5e-6, 3e-5)
+    assert_close(Sg, So, "stress", 5e-5, 2e-4)
