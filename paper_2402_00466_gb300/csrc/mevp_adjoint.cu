@@ -157,12 +157,10 @@ __global__ void k_adj_node(DevState d, AdjBuf b, const double *__restrict__ vpre
 
 // ---- element stage ---------------------------------------------------------------
 template <int NS>
-__global__ void __launch_bounds__(128) k_adj_elem(DevState d, Rheo r, AdjBuf b,
-                                                  const double *__restrict__ vprev) {
+__device__ __forceinline__ void adj_elem(const DevState &d, const Rheo &r, const AdjBuf &b,
+                                         const double *__restrict__ vprev, int K) {
   constexpr int NGP = DgSpace<NS>::NGP;
   constexpr int NG = NGP * NGP;
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K >= d.ne) return;
   const int ky = K / d.nx, kx = K - ky * d.nx;
   const double hx = d.lines[kx], ihx = d.lines[d.nx + kx];
   const double hy = d.lines[2 * d.nx + ky], ihy = d.lines[2 * d.nx + d.ny + ky];
@@ -302,6 +300,45 @@ __global__ void __launch_bounds__(128) k_adj_elem(DevState d, Rheo r, AdjBuf b,
     b.ubar[(size_t)j * ne + K] = ub[j];
     b.ubar[(size_t)(9 + j) * ne + K] = vb[j];
   }
+}
+
+// Persistent: the grid is the number of blocks resident on the chip and each
+// block takes an equal contiguous share of the element warps (a grid of one
+// block per 128 elements ends in a partial wave: 256^2 gives 512 blocks for
+// 760 slots, 3 or 4 per SM).
+constexpr int kAdjElemBlock = 128;
+
+template <int NS>
+__global__ void __launch_bounds__(kAdjElemBlock) k_adj_elem(DevState d, Rheo r, AdjBuf b,
+                                                            const double *__restrict__ vprev) {
+  const int nwarps = (d.ne + 31) >> 5;
+  const int w0 = (int)((long long)nwarps * blockIdx.x / gridDim.x);
+  const int w1 = (int)((long long)nwarps * (blockIdx.x + 1) / gridDim.x);
+  const int lane = threadIdx.x & 31;
+  for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += kAdjElemBlock / 32) {
+    const int K = (w << 5) + lane;
+    if (K < d.ne) adj_elem<NS>(d, r, b, vprev, K);
+  }
+}
+
+// Grid of the persistent reverse element kernel: resident blocks x SMs, at
+// most one block per 128 elements.
+template <int NS>
+int adj_elem_grid(const DevState &d) {
+  static int resident = 0;
+  if (resident == 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adj_elem<NS>, kAdjElemBlock, 0) !=
+            cudaSuccess ||
+        n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    resident = n;
+  }
+  const long long need = (d.ne + kAdjElemBlock - 1) / kAdjElemBlock;
+  const long long fit = (long long)resident * d.nsm;
+  return (int)(need < fit ? need : fit);
 }
 
 // ---- gradients -------------------------------------------------------------------
@@ -474,15 +511,16 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
                                  cudaMemcpyDeviceToDevice, st),
                  "adjoint history");
       }
+      const int eg = ns == 3 ? adj_elem_grid<3>(d) : adj_elem_grid<6>(d);
       for (int i = len - 1; i >= 0; --i) {
         const double *vprev = hist + (size_t)i * 2 * nn;
         const double *vnext = hist + (size_t)(i + 1) * 2 * nn;
         k_adj_node<<<blocks(nn, kBlock), kBlock, 0, st>>>(d, b, vprev, vnext, s->has_vo ? 1 : 0,
                                                            first ? 0 : 1);
         if (ns == 3)
-          k_adj_elem<3><<<blocks(ne, 128), 128, 0, st>>>(d, s->rheo, b, vprev);
+          k_adj_elem<3><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev);
         else
-          k_adj_elem<6><<<blocks(ne, 128), 128, 0, st>>>(d, s->rheo, b, vprev);
+          k_adj_elem<6><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev);
         ADJ_CUDA(cudaGetLastError(), "adjoint reverse");
         first = false;
       }
