@@ -22,6 +22,11 @@
  *     H, A, E at the Gauss points, clamp h, a, ice strength
  *     P = P* h exp(-C(1-a)), Delta, P/Delta, then the relaxed update with the
  *     local inverse-mass-times-weights matrix (the paper's iMJwPSI).
+ *   - Element geometry (Sec. 2.1, Sec. 3.2): the bilinear map of an element's
+ *     4 vertices, or the isoparametric Q2 map of its 9 CG2 node positions;
+ *     J, det J and J^-1 at every quadrature point, M_K by the Gauss rule.
+ *   - The transport of H and A that precedes the subcycles in every outer
+ *     step (Sec. 2, Sec. 2.1): DG upwind fluxes and SSP Runge-Kutta steps.
  *
  * Everything is FP64, evaluated in the order the definitions are written,
  * compiled with -O2 -ffp-contract=off.  Per-element work is independent, so
