@@ -246,15 +246,18 @@ MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
 
 /* ---- Ensembles ------------------------------------------------------------
  * Many independent domains advanced together, for ensembles of uneven
- * domains (sizes, DG1/DG2, parameters may differ per member).  The members
- * are existing states that share one precision, one device and one stream;
- * the ensemble borrows them (they must outlive it) and they remain usable on
- * their own.  Per subcycle, MEVP_MIXED issues one persistent launch over the
- * (member, tile) work list of all members; MEVP_FP64 issues a persistent
- * element launch and a persistent node launch.  Results are bitwise those of
- * stepping each member alone.  The ensemble allocates small device tables
- * (cudaMalloc) for its member descriptors and work lists.  Members must have
- * rectilinear meshes and 3 or 6 stress dofs (else MEVP_ERR_UNSUPPORTED). */
+ * domains (sizes, stress dofs, ice degree, mesh kind and parameters may
+ * differ per member).  The members are existing states that share one
+ * precision, one device and one stream; the ensemble borrows them (they must
+ * outlive it) and they remain usable on their own.  Per subcycle, MEVP_MIXED
+ * issues one persistent launch over the (member, tile) work list of the
+ * members on rectilinear meshes with 3 or 6 stress dofs and DG0 ice; MEVP_FP64
+ * issues a persistent element launch over the members on rectilinear meshes
+ * and a persistent node launch over all members.  The remaining members run
+ * their single-state launches in the same stream (and CUDA graphs).  Results
+ * are bitwise those of stepping each member alone.  The ensemble allocates
+ * small device tables (cudaMalloc) for its member descriptors and work
+ * lists. */
 typedef struct mevp_ensemble mevp_ensemble; /* opaque, library-owned */
 
 MEVP_API int mevp_ensemble_create(mevp_state *const *members, int n, mevp_ensemble **out);

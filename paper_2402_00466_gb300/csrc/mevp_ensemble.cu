@@ -1,10 +1,15 @@
 // mevp_ensemble.cu -- the ensemble entry points of include/mevp.h.
 //
 // An ensemble advances many independent domains (existing states of uneven
-// sizes, DG1 and DG2 mixed, one precision, one stream) together: per subcycle
-// one persistent launch over the (member, tile) work list of all members in
-// the mixed precision, and one persistent element launch plus one persistent
-// node launch in FP64.  Runs of subcycles are replayed as CUDA graphs, and
+// sizes and kinds, one precision, one stream) together.  Per subcycle, the
+// members on rectilinear meshes with 3 or 6 stress dofs and DG0 ice are
+// batched: in the mixed precision one persistent launch covers their
+// (member, tile) work list, in FP64 one persistent element launch their
+// element blocks, and one persistent node launch the nodes of all members.
+// The other members (8 stress dofs, DG1/DG2 ice, general or curved meshes)
+// run their single-state launches (FP64: the element launch) within the same
+// stream and graphs: batching every variant into one kernel would make its
+// register allocation spill for all members.  Runs of subcycles are replayed as CUDA graphs, and
 // the tile shape (mixed) or element block size (FP64) is chosen by timing the
 // candidates on the ensemble itself.  Per element and per node the arithmetic
 // is that of the single-state kernels, so an ensemble step gives bitwise the
@@ -36,6 +41,7 @@ struct mevp_ensemble {
   int nwork = 0, nnwork = 0;
   size_t work_cap = 0, nwork_cap = 0;
   int grid = 0, grid_n = 0;
+  std::vector<int> solo;              // members stepped with their own launches
   bool use_graphs = true;
   struct Graph {
     int flip, len;
@@ -65,8 +71,13 @@ void drop_graphs(mevp_ensemble *e) {
 
 int shape_count(int prec) { return prec == MEVP_MIXED ? mevp::kMixTileCount : mevp::kF64BlockCount; }
 
+// Whether a member's element work goes into the batched launch.
+bool batched(const mevp_state *s) { return !s->d.xy && !s->d.nxy && s->na == 1 && s->ns != 8; }
+
+// Relative per-element cost (FP64 flop counts of the rectilinear element
+// kernel), for ordering the batched work largest first.
 long long member_cost(const mevp_state *s) {
-  return (long long)s->d.ne * (s->ns == 6 ? 2 : 1);
+  return (long long)s->d.ne * (s->ns == 3 ? 474 : 1055);
 }
 
 // Work lists for the current shape, members ordered by decreasing cost.
@@ -77,9 +88,12 @@ int build_work(mevp_ensemble *e) {
     return member_cost(e->members[a]) > member_cost(e->members[b]);
   });
   std::vector<EnsWork> w, nw;
+  e->solo.clear();
   for (int m : order) {
     const mevp_state *s = e->members[m];
-    if (e->prec == MEVP_MIXED) {
+    if (!batched(s)) {
+      e->solo.push_back(m);
+    } else if (e->prec == MEVP_MIXED) {
       int tx = 0, ty = 0;
       mevp::mixed_tile_count(e->shape, s->d.nx, s->d.ny, &tx, &ty);
       for (int y = 0; y < ty; ++y)
@@ -87,6 +101,8 @@ int build_work(mevp_ensemble *e) {
     } else {
       const int B = mevp::kF64Blocks[e->shape];
       for (int b = 0; b * B < s->d.ne; ++b) w.push_back({m, b, 0});
+    }
+    if (e->prec != MEVP_MIXED) {
       const int slots = (s->d.nx + 1) * (s->d.ny + 1);
       for (int b = 0; b * mevp::kNodeSlotBlock < slots; ++b) nw.push_back({m, b, 0});
     }
@@ -171,10 +187,30 @@ int sync_descriptors(mevp_ensemble *e, int *flip) {
   return MEVP_OK;
 }
 
+// One subcycle of every member.  Mixed: the batched tile launch, then each
+// other member's fused single-state launch.  FP64: each other member's own
+// element launch, the batched element launch, then the node launch over all
+// members.  Member m's current buffer is base_cur(m) ^ flip.
 cudaError_t launch_one(mevp_ensemble *e, int flip) {
-  if (e->prec == MEVP_MIXED)
-    return mevp::launch_ensemble_mixed(e->d_mem, e->d_work, e->nwork, e->shape, e->grid, flip,
-                                       e->stream);
+  cudaError_t err = cudaSuccess;
+  if (e->prec == MEVP_MIXED) {
+    if (e->nwork > 0)
+      err = mevp::launch_ensemble_mixed(e->d_mem, e->d_work, e->nwork, e->shape, e->grid, flip,
+                                        e->stream);
+    for (size_t i = 0; i < e->solo.size() && err == cudaSuccess; ++i) {
+      const mevp_state *s = e->members[e->solo[i]];
+      const int cur = e->host_mem[e->solo[i]].base_cur ^ flip;
+      err = mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, cur, e->stream,
+                                        nullptr, true);
+    }
+    return err;
+  }
+  for (size_t i = 0; i < e->solo.size() && err == cudaSuccess; ++i) {
+    const mevp_state *s = e->members[e->solo[i]];
+    const int cur = e->host_mem[e->solo[i]].base_cur ^ flip;
+    err = mevp::launch_element_f64(s->d, s->rheo, cur, e->stream);
+  }
+  if (err != cudaSuccess) return err;
   return mevp::launch_ensemble_f64(e->d_mem, e->d_work, e->nwork, e->d_nwork, e->nnwork, e->shape,
                                    e->grid, e->grid_n, flip, e->stream);
 }
@@ -258,16 +294,6 @@ int mevp_ensemble_create(mevp_state *const *members, int n, mevp_ensemble **out)
     for (int j = 0; j < i; ++j)
       if (members[j] == members[i])
         return efail(MEVP_ERR_ARG, "ensemble_create: member %d repeats member %d", i, j);
-    if (members[i]->d.xy || members[i]->d.nxy)
-      return efail(MEVP_ERR_UNSUPPORTED,
-                   "ensemble_create: member %d has a general mesh; ensembles take rectilinear "
-                   "meshes", i);
-    if (members[i]->na != 1)
-      return efail(MEVP_ERR_UNSUPPORTED,
-                   "ensemble_create: member %d has DG1/DG2 ice fields; ensembles take DG0", i);
-    if (members[i]->ns == 8)
-      return efail(MEVP_ERR_UNSUPPORTED,
-                   "ensemble_create: member %d has 8 stress dofs; ensembles take 3 or 6", i);
     if (members[i]->prec != members[0]->prec)
       return efail(MEVP_ERR_ARG, "ensemble_create: members must share one precision");
     if (members[i]->stream != members[0]->stream)

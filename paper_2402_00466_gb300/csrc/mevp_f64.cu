@@ -528,9 +528,7 @@ cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo,
   return cudaGetLastError();
 }
 
-cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
-                                cudaStream_t st, cudaEvent_t *ev) {
-  if (ev) cudaEventRecord(ev[0], st);
+cudaError_t launch_element_f64(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
   const int eg = d.nsm;  // persistent: one block per SM
   if (d.nxy)
     launch_element_iso(d, r, cur, st);
@@ -551,6 +549,13 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
     else
       k_element_f64<8, true><<<eg, kElemBlock, 0, st>>>(d, r, cur);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
+                                cudaStream_t st, cudaEvent_t *ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  launch_element_f64(d, r, cur, st);
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
   (void)slots;
@@ -565,18 +570,18 @@ const int kF64Blocks[kF64BlockCount] = {64, 128, 256};
 cudaError_t launch_ensemble_f64(const EnsMember *mem, const EnsWork *ework, int nework,
                                 const EnsWork *nwork_list, int nnwork, int block, int grid_e,
                                 int grid_n, int flip, cudaStream_t st) {
-  switch (block) {
-    case 0:
-      k_ens_f64_elem<64><<<grid_e, 64, 0, st>>>(mem, ework, nework, flip);
-      break;
-    case 1:
-      k_ens_f64_elem<128><<<grid_e, 128, 0, st>>>(mem, ework, nework, flip);
-      break;
-    default:
-      k_ens_f64_elem<256><<<grid_e, 256, 0, st>>>(mem, ework, nework, flip);
-      break;
-  }
-  k_ens_f64_node<<<grid_n, kNodeBlock, 0, st>>>(mem, nwork_list, nnwork, flip);
+  if (nework > 0) switch (block) {
+      case 0:
+        k_ens_f64_elem<64><<<grid_e, 64, 0, st>>>(mem, ework, nework, flip);
+        break;
+      case 1:
+        k_ens_f64_elem<128><<<grid_e, 128, 0, st>>>(mem, ework, nework, flip);
+        break;
+      default:
+        k_ens_f64_elem<256><<<grid_e, 256, 0, st>>>(mem, ework, nework, flip);
+        break;
+    }
+  if (nnwork > 0) k_ens_f64_node<<<grid_n, kNodeBlock, 0, st>>>(mem, nwork_list, nnwork, flip);
   return cudaGetLastError();
 }
 

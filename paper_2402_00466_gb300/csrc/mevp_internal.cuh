@@ -159,6 +159,8 @@ cudaError_t launch_prepare(const DevState &d, const mevp_params &p, bool has_vo,
 // two kernels and after the node kernel.
 cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, int cur,
                                 cudaStream_t st, cudaEvent_t *ev);
+// the element part alone (any geometry, stress dofs and ice degree)
+cudaError_t launch_element_f64(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
 // general (non-affine) meshes: element kernel and read-back diagnostics
 cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
@@ -187,9 +189,9 @@ constexpr int kMixTileCount = 3;
 extern const int kMixTiles[kMixTileCount][2];
 MixArgs make_mixargs(const Rheo &r, const mevp_params &p, bool has_vo);
 int mixed_tile_count(int tile, int nx, int ny, int *tiles_x, int *tiles_y);
-int mixed_tile_ctas_per_sm(int tile);
 cudaError_t launch_ensemble_mixed(const EnsMember *mem, const EnsWork *work, int nwork, int tile,
                                   int grid, int flip, cudaStream_t st);
+int mixed_tile_ctas_per_sm(int tile);
 cudaError_t setup_mixed_kernels();  // once per device, before any capture
 cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                                  cudaStream_t st);

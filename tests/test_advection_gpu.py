@@ -239,8 +239,5 @@ def test_dg_ice_refusals():
             st.adjoint_kinetic_energy(2, 1)
         assert e.value.code == -7
         with pytest.raises(mevp.MevpError) as e:
-            mevp.Ensemble([st])
-        assert e.value.code == -7
-        with pytest.raises(mevp.MevpError) as e:
             st.advect(-1)
         assert e.value.code == -1

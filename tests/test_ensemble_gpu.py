@@ -119,3 +119,65 @@ def test_members_stay_usable_and_mixing_is_rejected():
             assert np.array_equal(va, vb) and np.array_equal(Sa, Sb)
         for st in a + b:
             st.close()
+
+
+# members of every kind: stress dofs, DG0/DG1/DG2 ice, rectilinear, bilinear
+# and curved meshes (nx, ny, n_s, n_a, geometry, seed)
+KINDS = [(40, 33, 6, 1, "uniform", 11), (23, 17, 8, 1, "uniform", 12),
+         (19, 26, 6, 6, "uniform", 13), (31, 12, 3, 3, "perturbed", 14),
+         (17, 21, 8, 6, "wavy", 15), (14, 11, 6, 1, "curved", 16), (9, 13, 3, 3, "wavy_iso", 17),
+         (12, 9, 3, 1, "uniform", 18)]
+
+
+def make_kinds(precision):
+    states = []
+    for nx, ny, ns, na, geo, seed in KINDS:
+        case = W.small_case(nx, ny, ns, seed=600 + seed, geometry=geo)
+        rng = np.random.default_rng(seed)
+        ne = nx * ny
+        H = np.vstack([rng.uniform(0.5, 1.8, ne)] + [rng.uniform(-0.2, 0.2, ne)] * (na - 1))
+        A = np.vstack([rng.uniform(0.75, 0.97, ne)] + [rng.uniform(-0.05, 0.05, ne)] * (na - 1))
+        p = dict(case["params"], alpha=300.0 + 40 * seed)
+        st = mevp.State(nx, ny, ns, vertex_xy=case["xy"], n_adv=na, precision=precision, params=p)
+        st.set_ice(H, A)
+        st.set_forcing(case["tau"])
+        st.set_velocity(case["vel0"])
+        st.set_stress(case["S0"])
+        states.append(st)
+    return states
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_ensemble_of_every_member_kind(precision):
+    """Members that are not batched (8 stress dofs, DG1/DG2 ice, general and
+    curved meshes) run their single-state launches inside the ensemble's
+    stream and graphs: still bitwise the results of stepping each alone, for
+    every shape, with and without graphs, and after autotuning."""
+    counts = (3, 9, 1)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        alone = make_kinds(precision)
+        for st in alone:
+            st.begin_step()
+            for n in counts:
+                st.run_subcycles(n)
+        ref = results(alone)
+        for st in alone:
+            st.close()
+        for shape in range(len(mevp.mevp_ensemble_shapes(precision))):
+            for graphs in (1, 0):
+                states = make_kinds(precision)
+                with mevp.Ensemble(states) as ens:
+                    ens.set_shape(shape)
+                    ens.set_graphs(graphs)
+                    ens.begin_step()
+                    if shape == 0 and graphs:
+                        ens.autotune(3)
+                    for n in counts:
+                        ens.run_subcycles(n)
+                    got = results(states)
+                for st in states:
+                    st.close()
+                for m, ((va, Sa), (vb, Sb)) in enumerate(zip(got, ref)):
+                    assert np.array_equal(va, vb), (shape, graphs, m, "velocity")
+                    assert np.array_equal(Sa, Sb), (shape, graphs, m, "stress")

@@ -260,9 +260,6 @@ def test_general_mesh_refusals():
         with pytest.raises(mevp.MevpError) as e:
             st.adjoint_kinetic_energy(2, 1)
         assert e.value.code == -7
-        with pytest.raises(mevp.MevpError) as e:
-            mevp.Ensemble([st])
-        assert e.value.code == -7
 
 
 # ---------------------------------------------------------------- isoparametric
@@ -355,9 +352,6 @@ def test_iso_refusals():
         st.begin_step()
         with pytest.raises(mevp.MevpError) as e:
             st.adjoint_kinetic_energy(2, 1)
-        assert e.value.code == -7
-        with pytest.raises(mevp.MevpError) as e:
-            mevp.Ensemble([st])
         assert e.value.code == -7
 
 
