@@ -344,8 +344,10 @@ MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp
  * Afterwards the state holds the result of the n subcycles, as after
  * mevp_run_subcycles(n).  Allocates its working memory (cudaMalloc):
  * about (n/checkpoint_every) (2 N_n + 3 n_stress N_e) + (checkpoint_every
- * + 8) 2 N_n + 40 N_e doubles.  MEVP_ERR_UNSUPPORTED for MEVP_MIXED, for 8
- * stress dofs and for general meshes. */
+ * + 8) 2 N_n + 40 N_e doubles.  Any stress dofs and ice degree; with DG1/DG2
+ * ice the strength at each Gauss point is P*_K times that point's
+ * max(0, h) exp(-C (1 - clamp(a))).  MEVP_ERR_UNSUPPORTED for MEVP_MIXED and
+ * for general or curved meshes. */
 MEVP_API int mevp_adjoint_kinetic_energy(mevp_state *state, int n, int checkpoint_every,
                                          double *J, double *dJ_dPstar, double *dJ_dtau,
                                          int on_device);

@@ -156,9 +156,13 @@ __global__ void k_adj_node(DevState d, AdjBuf b, const double *__restrict__ vpre
 }
 
 // ---- element stage ---------------------------------------------------------------
-template <int NS>
+// VAR: DG1/DG2 ice, the strength P_g = P*_K f_g per Gauss point with
+// f_g = max(0, h_g) exp(-C (1 - clamp(a_g))), and the -P/2 term projected
+// per Gauss point as in the forward update; Pbar then accumulates
+// dJ/dP*_K = sum_g dJ/dP_g f_g directly.
+template <int NS, bool VAR>
 __device__ __forceinline__ void adj_elem(const DevState &d, const Rheo &r, const AdjBuf &b,
-                                         const double *__restrict__ vprev, int K) {
+                                         const double *__restrict__ vprev, int K, double C) {
   constexpr int NGP = DgSpace<NS>::NGP;
   constexpr int NG = NGP * NGP;
   const int ky = K / d.nx, kx = K - ky * d.nx;
@@ -181,7 +185,7 @@ __device__ __forceinline__ void adj_elem(const DevState &d, const Rheo &r, const
   gauss_eval<NS>(Pc, pg_);
   gauss_eval<NS>(Qc, qg_);
   gauss_eval<NS>(Gc, gg_);
-  const double Ph = d.Pe[K] * r.hainv;
+  const double Ph = VAR ? 0.0 : d.Pe[K] * r.hainv;
   // element-force adjoints from the nodal force adjoints
   double fbx[9], fby[9];
 #pragma unroll
@@ -229,7 +233,7 @@ __device__ __forceinline__ void adj_elem(const DevState &d, const Rheo &r, const
     Qb[s] = r.ie * (B11[s] - B22[s]);
     Gb[s] = r.ie * B12[s];
   }
-  double Phbar = -(B11[0] + B22[0]);
+  double Phbar = VAR ? 0.0 : -(B11[0] + B22[0]);
   double pb[NG], qb[NG], gb[NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
@@ -245,10 +249,19 @@ __device__ __forceinline__ void adj_elem(const DevState &d, const Rheo &r, const
     }
     const double d2 = fma(gg_[g], gg_[g], fma(qg_[g], qg_[g], fma(pg_[g], pg_[g], r.dmin2)));
     const double R = rsqrt(d2);
-    const double X = Ph * R;
+    double Phg = Ph;
+    if constexpr (VAR) Phg = d.Pg[(size_t)g * ne + K] * r.hainv;
+    const double X = Phg * R;
     const double Xbar = xpb * pg_[g] + xqb * qg_[g] + xgb * gg_[g];
-    Phbar += Xbar * R;
-    const double d2bar = -0.5 * (Xbar * Ph) * R * R * R;
+    if constexpr (VAR) {
+      const int gx = g % NGP, gy = g / NGP;
+      const double h = fmax(0.0, dg_at_gauss<NGP>(d.H, d.na, ne, K, gx, gy));
+      const double a = fmin(1.0, fmax(0.0, dg_at_gauss<NGP>(d.A, d.na, ne, K, gx, gy)));
+      Phbar = fma(Xbar * R - xpb, h * exp(-C * (1.0 - a)), Phbar);
+    } else {
+      Phbar += Xbar * R;
+    }
+    const double d2bar = -0.5 * (Xbar * Phg) * R * R * R;
     pb[g] = X * xpb + 2.0 * pg_[g] * d2bar;
     qb[g] = X * xqb + 2.0 * qg_[g] * d2bar;
     gb[g] = X * xgb + 2.0 * gg_[g] * d2bar;
@@ -308,27 +321,28 @@ __device__ __forceinline__ void adj_elem(const DevState &d, const Rheo &r, const
 // 760 slots, 3 or 4 per SM).
 constexpr int kAdjElemBlock = 128;
 
-template <int NS>
+template <int NS, bool VAR>
 __global__ void __launch_bounds__(kAdjElemBlock) k_adj_elem(DevState d, Rheo r, AdjBuf b,
-                                                            const double *__restrict__ vprev) {
+                                                            const double *__restrict__ vprev,
+                                                            double C) {
   const int nwarps = (d.ne + 31) >> 5;
   const int w0 = (int)((long long)nwarps * blockIdx.x / gridDim.x);
   const int w1 = (int)((long long)nwarps * (blockIdx.x + 1) / gridDim.x);
   const int lane = threadIdx.x & 31;
   for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += kAdjElemBlock / 32) {
     const int K = (w << 5) + lane;
-    if (K < d.ne) adj_elem<NS>(d, r, b, vprev, K);
+    if (K < d.ne) adj_elem<NS, VAR>(d, r, b, vprev, K, C);
   }
 }
 
 // Grid of the persistent reverse element kernel: resident blocks x SMs, at
 // most one block per 128 elements.
-template <int NS>
+template <int NS, bool VAR>
 int adj_elem_grid(const DevState &d) {
   static int resident = 0;
   if (resident == 0) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adj_elem<NS>, kAdjElemBlock, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adj_elem<NS, VAR>, kAdjElemBlock, 0) !=
             cudaSuccess ||
         n < 1) {
       cudaGetLastError();
@@ -361,13 +375,18 @@ __global__ void k_adj_area(DevState d, AdjBuf b) {
   b.area[node] = l;
 }
 
-// dJ/dP*_K = Pbar_K max(0,H) exp(-C(1-clamp A)),  dJ/dtau_j = l_j qbar_j
+// dJ/dP*_K = Pbar_K max(0,H) exp(-C(1-clamp A)) (DG0 ice; with DG1/DG2 ice
+// Pbar already holds dJ/dP*_K),  dJ/dtau_j = l_j qbar_j
 __global__ void k_adj_grads(DevState d, AdjBuf b, double C, double *gP, double *gT) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < d.ne && gP) {
-    const double h = fmax(0.0, d.H[i]);
-    const double a = fmin(1.0, fmax(0.0, d.A[i]));
-    gP[i] = b.Pbar[i] * h * exp(-C * (1.0 - a));
+    if (d.na > 1) {
+      gP[i] = b.Pbar[i];
+    } else {
+      const double h = fmax(0.0, d.H[i]);
+      const double a = fmin(1.0, fmax(0.0, d.A[i]));
+      gP[i] = b.Pbar[i] * h * exp(-C * (1.0 - a));
+    }
   }
   if (i < d.nn && gT) {
     const size_t nn = d.nn;
@@ -411,9 +430,7 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
   int rc = api_check_state(s);
   if (rc) return rc;
   if (s->prec != MEVP_FP64) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: FP64 states only");
-  if (s->ns == 8) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: 3 or 6 stress dofs only");
   if (s->d.xy || s->d.nxy) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: rectilinear meshes only");
-  if (s->na != 1) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: DG0 ice fields only");
   if (n < 1) return afail(MEVP_ERR_ARG, "adjoint: n=%d < 1", n);
   if (checkpoint_every < 1) return afail(MEVP_ERR_ARG, "adjoint: checkpoint_every < 1");
   if (!s->prepared) return afail(MEVP_ERR_STATE, "adjoint: call mevp_begin_step first");
@@ -511,16 +528,25 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
                                  cudaMemcpyDeviceToDevice, st),
                  "adjoint history");
       }
-      const int eg = ns == 3 ? adj_elem_grid<3>(d) : adj_elem_grid<6>(d);
+      const bool var = d.na > 1;
+      const int eg = ns == 3 ? (var ? adj_elem_grid<3, true>(d) : adj_elem_grid<3, false>(d))
+                   : ns == 6 ? (var ? adj_elem_grid<6, true>(d) : adj_elem_grid<6, false>(d))
+                             : (var ? adj_elem_grid<8, true>(d) : adj_elem_grid<8, false>(d));
+      const double C = s->prm.C;
       for (int i = len - 1; i >= 0; --i) {
         const double *vprev = hist + (size_t)i * 2 * nn;
         const double *vnext = hist + (size_t)(i + 1) * 2 * nn;
         k_adj_node<<<blocks(nn, kBlock), kBlock, 0, st>>>(d, b, vprev, vnext, s->has_vo ? 1 : 0,
                                                            first ? 0 : 1);
         if (ns == 3)
-          k_adj_elem<3><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev);
+          var ? k_adj_elem<3, true><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C)
+              : k_adj_elem<3, false><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C);
+        else if (ns == 6)
+          var ? k_adj_elem<6, true><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C)
+              : k_adj_elem<6, false><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C);
         else
-          k_adj_elem<6><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev);
+          var ? k_adj_elem<8, true><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C)
+              : k_adj_elem<8, false><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C);
         ADJ_CUDA(cudaGetLastError(), "adjoint reverse");
         first = false;
       }

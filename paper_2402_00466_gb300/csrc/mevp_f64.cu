@@ -291,15 +291,6 @@ __global__ void k_strength(DevState d, double Pstar, double C) {
   d.Pe[K] = (d.pstar ? d.pstar[K] : Pstar) * h * exp(-C * (1.0 - a));
 }
 
-// Value at 2-D Gauss point (gx, gy) of the N-point rule of the DG1/DG2 field
-// F ([na][ne]) of element K.
-template <int N>
-__device__ __forceinline__ double dg_at_gauss(const double *F, int na, size_t ne, int K, int gx,
-                                              int gy) {
-  double v = 0.0;
-  for (int i = 0; i < na; ++i) v = fma(F[(size_t)i * ne + K], pg<N>(dgx(i), gx) * pg<N>(dgy(i), gy), v);
-  return v;
-}
 
 // DG1/DG2 H, A: the ice strength P = P* max(0,H) exp(-C(1 - clamp(A,0,1)))
 // at each Gauss point of the stress rule (Listing 1 evaluates H, A there).

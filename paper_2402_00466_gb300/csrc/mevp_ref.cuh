@@ -73,6 +73,16 @@ template <int NGP> __host__ __device__ constexpr double pg(int k, int g) {
        : (NGP == 3 ? (g == 1 ? -1.0 / 12.0 : 1.0 / 15.0) : 0.0 /* (1/12 - 1/12) */);
 }
 
+// Value at 2-D Gauss point (gx, gy) of the N-point rule of the DG1/DG2 field
+// F ([na][ne]) of element K.
+template <int N>
+__device__ __forceinline__ double dg_at_gauss(const double *F, int na, size_t ne, int K, int gx,
+                                              int gy) {
+  double v = 0.0;
+  for (int i = 0; i < na; ++i) v = fma(F[(size_t)i * ne + K], pg<N>(dgx(i), gx) * pg<N>(dgy(i), gy), v);
+  return v;
+}
+
 template <int NS> struct DgSpace;
 template <> struct DgSpace<3> { static constexpr int NGP = 2; };
 template <> struct DgSpace<6> { static constexpr int NGP = 3; };

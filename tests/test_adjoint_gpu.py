@@ -46,7 +46,7 @@ def J_gpu(st, case, n, pstar, tau):
     return 0.5 * float(np.sum(m * (v[0] ** 2 + v[1] ** 2)))
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 def test_adjoint_matches_gpu_finite_differences(n_s):
     case = W.small_case(12, 10, n_s, seed=81)
     n = 30
@@ -57,6 +57,39 @@ def test_adjoint_matches_gpu_finite_differences(n_s):
     assert abs(J - J_gpu(st, case, n, P0, case["tau"])) <= 1e-12 * abs(J)
     rng = np.random.default_rng(3)
     for _ in range(4):
+        dP = rng.standard_normal(ne)
+        dT = rng.standard_normal((2, nn))
+        for dirP, dirT in ((dP, 0 * dT), (0 * dP, dT)):
+            eP = 1e-6 * P0.mean() / np.abs(dirP).max() if np.any(dirP) else 0.0
+            eT = 1e-6 * np.abs(case["tau"]).max() / np.abs(dirT).max() if np.any(dirT) else 0.0
+            Jp = J_gpu(st, case, n, P0 + eP * dirP, case["tau"] + eT * dirT)
+            Jm = J_gpu(st, case, n, P0 - eP * dirP, case["tau"] - eT * dirT)
+            fd = (Jp - Jm) / 2.0
+            ad = eP * float(gP @ dirP) + eT * float(np.sum(gT * dirT))
+            assert abs(fd - ad) <= 1e-5 * abs(ad) + 1e-14 * abs(J), (fd, ad)
+    st.close()
+
+
+@pytest.mark.parametrize("n_a", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6])
+def test_adjoint_with_dg_ice_matches_gpu_finite_differences(n_a, n_s):
+    """DG1/DG2 H and A: the strength varies over the element (P_g at the Gauss
+    points, the -P/2 term projected per point); per-element P* and nodal
+    wind-stress directions against central differences of the GPU forward."""
+    nx, ny = 11, 9
+    case = W.small_case(nx, ny, n_s, seed=91 + n_a)
+    ne, nn, _ = W.sizes(nx, ny)
+    rng = np.random.default_rng(92 + n_a)
+    H = np.vstack([rng.uniform(0.6, 1.6, ne)] + [rng.uniform(-0.2, 0.2, ne)] * (n_a - 1))
+    A = np.vstack([rng.uniform(0.8, 0.95, ne)] + [rng.uniform(-0.04, 0.04, ne)] * (n_a - 1))
+    case = dict(case, H=H, A=A)
+    n = 25
+    P0 = case["params"]["Pstar"] * rng.uniform(0.8, 1.2, ne)
+    st = mevp.State(nx, ny, n_s, vertex_xy=case["xy"], n_adv=n_a, params=case["params"])
+    reset(st, case, P0)
+    J, gP, gT = st.adjoint_kinetic_energy(n, checkpoint_every=6)
+    assert abs(J - J_gpu(st, case, n, P0, case["tau"])) <= 1e-12 * abs(J)
+    for _ in range(3):
         dP = rng.standard_normal(ne)
         dT = rng.standard_normal((2, nn))
         for dirP, dirT in ((dP, 0 * dT), (0 * dP, dT)):

@@ -236,8 +236,5 @@ def test_dg_ice_refusals():
     with make_state(case, 3, H, A) as st:
         st.begin_step()
         with pytest.raises(mevp.MevpError) as e:
-            st.adjoint_kinetic_energy(2, 1)
-        assert e.value.code == -7
-        with pytest.raises(mevp.MevpError) as e:
             st.advect(-1)
         assert e.value.code == -1
