@@ -148,7 +148,10 @@ __device__ __forceinline__ void gather_force(const double *__restrict__ fb, int 
 
 // The up-to-four CG2 nodes (2kx + dx, 2ky + dy), dx, dy in {0,1}, of node
 // slot (kx, ky): force gather and velocity update.
-__device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int has_vo, int kx,
+// VO: an ocean velocity is set (else the ocean is at rest and its terms,
+// exact zeros, are left out at compile time).
+template <bool VO>
+__device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int kx,
                                               int ky) {
   const double *__restrict__ vp = d.vel[cur];
   double *__restrict__ vq = d.vel[cur ^ 1];
@@ -196,16 +199,19 @@ __device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int ha
       const double cA = ck_ldg(d.flags, (const double *)d.nodec, (long long)(0 * nn + node), 6LL * nn, 113), cB = ck_ldg(d.flags, (const double *)d.nodec, (long long)(1 * nn + node), 6LL * nn, 113);
       const double cK = ck_ldg(d.flags, (const double *)d.nodec, (long long)(2 * nn + node), 6LL * nn, 113), qx = ck_ldg(d.flags, (const double *)d.nodec, (long long)(3 * nn + node), 6LL * nn, 113);
       const double qy = ck_ldg(d.flags, (const double *)d.nodec, (long long)(4 * nn + node), 6LL * nn, 113), cD = ck_ldg(d.flags, (const double *)d.nodec, (long long)(5 * nn + node), 6LL * nn, 113);
-      double ox = 0.0, oy = 0.0;
-      if (has_vo) {
-        ox = ck_ldg(d.flags, (const double *)d.vo, (long long)node, 2LL * nn, 114);
-        oy = ck_ldg(d.flags, (const double *)d.vo, (long long)(nn + node), 2LL * nn, 114);
+      double c, rx = fma(cK, vx, qx) + Fx, ry = fma(cK, vy, qy) + Fy;
+      if constexpr (VO) {
+        const double ox = ck_ldg(d.flags, (const double *)d.vo, (long long)node, 2LL * nn, 114);
+        const double oy =
+            ck_ldg(d.flags, (const double *)d.vo, (long long)(nn + node), 2LL * nn, 114);
+        const double dvx = ox - vx, dvy = oy - vy;
+        c = cD * sqrt(dvx * dvx + dvy * dvy);
+        rx += c * ox;
+        ry += c * oy;
+      } else {
+        c = cD * sqrt(vx * vx + vy * vy);  // |0 - v|
       }
-      const double dvx = ox - vx, dvy = oy - vy;
-      const double c = cD * sqrt(dvx * dvx + dvy * dvy);
       const double a = cA + c;
-      const double rx = fma(cK, vx, qx) + Fx + c * ox;
-      const double ry = fma(cK, vy, qy) + Fy + c * oy;
       const double det = fma(a, a, cB * cB);
       double ux = 0.0, uy = 0.0;
       if (det != 0.0) {
@@ -224,15 +230,15 @@ __device__ __forceinline__ void node_slot_f64(const DevState &d, int cur, int ha
 //   a = m(1+beta)/dt + c,  b = m f,  c = l Cw rho_w |v_o - v^{p-1}|
 //   r = m beta/dt v^{p-1} + (m/dt v^n + l tau) + F + c v_o
 //   (a + i b) v^p = r   (complex notation)
-__global__ void __launch_bounds__(kNodeSlotThreads, 1) k_node_f64(DevState d, int cur,
-                                                                   int has_vo) {
+template <bool VO>
+__global__ void __launch_bounds__(kNodeSlotThreads, 1) k_node_f64(DevState d, int cur) {
   const int sw = d.nx + 1;
   const int nslots = sw * (d.ny + 1);
   const int s0 = (int)((long long)nslots * blockIdx.x / gridDim.x);
   const int s1 = (int)((long long)nslots * (blockIdx.x + 1) / gridDim.x);
   for (int slot = s0 + (int)threadIdx.x; slot < s1; slot += kNodeSlotThreads) {
     const int ky = slot / sw, kx = slot - ky * sw;
-    node_slot_f64(d, cur, has_vo, kx, ky);
+    node_slot_f64<VO>(d, cur, kx, ky);
   }
 }
 
@@ -263,7 +269,10 @@ __global__ void __launch_bounds__(kNodeBlock) k_ens_f64_node(const EnsMember *__
     const int sw = m.d.nx + 1;
     if (slot >= sw * (m.d.ny + 1)) continue;
     const int ky = slot / sw, kx = slot - ky * sw;
-    node_slot_f64(m.d, m.base_cur ^ flip, m.has_vo, kx, ky);
+    if (m.has_vo)
+      node_slot_f64<true>(m.d, m.base_cur ^ flip, kx, ky);
+    else
+      node_slot_f64<false>(m.d, m.base_cur ^ flip, kx, ky);
   }
 }
 
@@ -550,7 +559,10 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
   if (ev) cudaEventRecord(ev[1], st);
   const long long slots = (long long)(d.nx + 1) * (d.ny + 1);
   (void)slots;
-  k_node_f64<<<d.nsm, kNodeSlotThreads, 0, st>>>(d, cur, has_vo ? 1 : 0);
+  if (has_vo)
+    k_node_f64<true><<<d.nsm, kNodeSlotThreads, 0, st>>>(d, cur);
+  else
+    k_node_f64<false><<<d.nsm, kNodeSlotThreads, 0, st>>>(d, cur);
   if (ev) cudaEventRecord(ev[2], st);
   return cudaGetLastError();
 }
