@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, iso32, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, iso32, mfac, isoJ, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -88,6 +88,9 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   L.map32ab = take(m->general && prec == MEVP_MIXED ? sizeof(float4) * ne : 0);
   L.map32c = take(m->general && prec == MEVP_MIXED ? sizeof(float2) * ne : 0);
   L.iso32 = take(m->iso && prec == MEVP_MIXED ? 4 * sizeof(float4) * ne : 0);
+  const bool geo64 = (m->general || m->iso) && prec == MEVP_FP64;
+  L.mfac = take(geo64 ? sizeof(double) * (ns * (ns + 1) / 2) * ne : 0);
+  L.isoJ = take(m->iso && prec == MEVP_FP64 ? sizeof(double) * 4 * (ns == 3 ? 4 : 9) * ne : 0);
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(sizeof(double) * 3 * ns * ne);
@@ -405,6 +408,9 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
   d.yline = (const double *)(b + L.yline);
   d.xy = mesh->general ? (const double2 *)(b + L.xy) : nullptr;
   d.nxy = mesh->iso ? (const double2 *)(b + L.nxy) : nullptr;
+  const bool geo64 = (mesh->general || mesh->iso) && precision == MEVP_FP64;
+  d.mfac = geo64 ? (double *)(b + L.mfac) : nullptr;
+  d.isoJ = mesh->iso && precision == MEVP_FP64 ? (double *)(b + L.isoJ) : nullptr;
   d.lines = (double *)(b + L.lines);
   s->pstar_buf = (double *)(b + L.pstar);
   s->adv1 = (double *)(b + L.adv1);
@@ -461,6 +467,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
                         cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && mesh->iso) e = mevp::setup_iso_kernels();
   if (e == cudaSuccess && mesh->general && !mesh->iso) e = mevp::setup_general_kernels();
+  if (e == cudaSuccess && d.mfac) e = mevp::launch_geom_factors(d, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) r2 = cuda_fail(e, "state_create: initialise workspace");
   if (r2) {

@@ -27,12 +27,29 @@ __device__ __forceinline__ void warp_share(int ne, int &w0, int &w1) {
   w1 = (int)((long long)nwarps * (blockIdx.x + 1) / gridDim.x);
 }
 
+// The element's mass factor from the records written at state creation.
+template <int NS>
+__device__ __forceinline__ void load_mass_factor(const DevState &d, int K, MassFactor<NS> &F) {
+  constexpr int NL = NS * (NS - 1) / 2;
+  const long long ne = d.ne, n = (long long)mass_factor_words<NS>() * ne;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) F.L[i] = ck_ldg(d.flags, (const double *)d.mfac, i * ne + K, n, 145);
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+    F.Dinv[i] = ck_ldg(d.flags, (const double *)d.mfac, (NL + i) * ne + K, n, 145);
+}
+
+// FP64 general and curved elements read the L D L^T factor of M_K (and a
+// curved element its Jacobians) from records computed once per state: on
+// this chip an FP64 operation costs about as much as 5 bytes of memory
+// traffic, so the factorisation (with its divisions) and the curved map's
+// 252-flop Jacobians are cheaper read than recomputed every subcycle.
 template <int NS, bool VAR>
 __device__ __forceinline__ void elem_gen(const DevState &d, const Rheo &r, int cur, int K) {
   const int ky = K / d.nx, kx = K - ky * d.nx;
   const QuadMap m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
   MassFactor<NS> F;
-  mass_factor<NS>(m, F);
+  load_mass_factor<NS>(d, K, F);
   double Pc[NS], Qc[NS], Gc[NS];
   {
     double u[9], v[9];
@@ -175,14 +192,16 @@ __device__ __forceinline__ IsoGeo<N, double> iso_geometry(const DevState &d, int
   return IsoGeo<N, double>{col, stride};
 }
 
+// The element's Jacobians at the Gauss points are read where they are used,
+// from the records written at state creation (the [4 N^2][ne] array is sized
+// for every K < ne, so these reads stay in bounds by construction).
 template <int NS, bool VAR>
-__device__ __forceinline__ void elem_iso(const DevState &d, const Rheo &r, int cur, int K,
-                                         double *sm) {
+__device__ __forceinline__ void elem_iso(const DevState &d, const Rheo &r, int cur, int K) {
   constexpr int N = DgSpace<NS>::NGP;
   const int ky = K / d.nx, kx = K - ky * d.nx;
-  const IsoGeo<N, double> m = iso_geometry<N>(d, kx, ky, sm);
+  const IsoGeoG<N, double> m{d.isoJ + K, (size_t)d.ne};
   MassFactor<NS> F;
-  mass_factor<NS>(m, F);
+  load_mass_factor<NS>(d, K, F);
   double Pc[NS], Qc[NS], Gc[NS];
   {
     double u[9], v[9];
@@ -238,13 +257,12 @@ constexpr size_t iso_smem() {
 
 template <int NS, bool VAR>
 __global__ void __launch_bounds__(kIsoBlock) k_element_iso(DevState d, Rheo r, int cur) {
-  extern __shared__ double iso_sm[];
   int w0, w1;
   warp_share(d.ne, w0, w1);
   const int lane = threadIdx.x & 31;
   for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += kIsoBlock / 32) {
     const int K = (w << 5) + lane;
-    if (K < d.ne) elem_iso<NS, VAR>(d, r, cur, K, iso_sm);
+    if (K < d.ne) elem_iso<NS, VAR>(d, r, cur, K);
   }
 }
 
@@ -297,6 +315,42 @@ __global__ void __launch_bounds__(kIsoBlock) k_force_elem_iso(DevState d) {
 
 inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
+// Per-element geometry records of an FP64 general (ISO = false) or curved
+// mesh: the L D L^T factor of M_K, and for a curved element its Jacobians at
+// the Gauss points, by the same functions the on-the-fly diagnostics use.
+template <int NS, bool ISO>
+__global__ void __launch_bounds__(kIsoBlock) k_geom_factors(DevState d) {
+  extern __shared__ double iso_sm[];
+  constexpr int N = DgSpace<NS>::NGP, NG = N * N;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  MassFactor<NS> F;
+  if constexpr (ISO) {
+    const IsoGeo<N, double> m = iso_geometry<N>(d, kx, ky, iso_sm);
+    mass_factor<NS>(m, F);
+    for (int i = 0; i < 4 * NG; ++i)
+      ck_st(d.flags, d.isoJ, (long long)i * d.ne + K, 4LL * NG * d.ne, 147, m.sJ[i * m.stride]);
+  } else {
+    const QuadMap m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
+    mass_factor<NS>(m, F);
+  }
+  constexpr int NL = NS * (NS - 1) / 2;
+  const long long n = (long long)mass_factor_words<NS>() * d.ne;
+  for (int i = 0; i < NL; ++i) ck_st(d.flags, d.mfac, (long long)i * d.ne + K, n, 148, F.L[i]);
+  for (int i = 0; i < NS; ++i)
+    ck_st(d.flags, d.mfac, (long long)(NL + i) * d.ne + K, n, 148, F.Dinv[i]);
+}
+
+template <int NS>
+void launch_geom_factors_ns(const DevState &d, cudaStream_t st) {
+  const int g = blocks(d.ne, kIsoBlock);
+  if (d.nxy)
+    k_geom_factors<NS, true><<<g, kIsoBlock, iso_smem<NS>(), st>>>(d);
+  else
+    k_geom_factors<NS, false><<<g, kIsoBlock, 0, st>>>(d);
+}
+
 // Resident blocks per SM of the persistent element kernels, [NS index][VAR];
 // filled at state creation, 2 until then (the grid size only affects speed).
 int g_gen_resident[3][2] = {{2, 2}, {2, 2}, {2, 2}};
@@ -321,7 +375,7 @@ cudaError_t resident_blocks(Kernel k, int block, size_t smem, int &out) {
 template <int NS, bool VAR>
 void launch_iso_ns(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
   const int g = persistent_grid(d, g_iso_resident[ns_index(NS)][VAR], kIsoBlock);
-  k_element_iso<NS, VAR><<<g, kIsoBlock, iso_smem<NS>(), st>>>(d, r, cur);
+  k_element_iso<NS, VAR><<<g, kIsoBlock, 0, st>>>(d, r, cur);
 }
 
 template <int NS, bool VAR>
@@ -332,13 +386,7 @@ void launch_gen_ns(const DevState &d, const Rheo &r, int cur, cudaStream_t st) {
 
 template <int NS, bool VAR>
 cudaError_t setup_iso_ns() {
-  cudaError_t e = cudaFuncSetAttribute(k_element_iso<NS, VAR>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)iso_smem<NS>());
-  if (e == cudaSuccess)
-    e = resident_blocks(k_element_iso<NS, VAR>, kIsoBlock, iso_smem<NS>(),
-                        g_iso_resident[ns_index(NS)][VAR]);
-  return e;
+  return resident_blocks(k_element_iso<NS, VAR>, kIsoBlock, 0, g_iso_resident[ns_index(NS)][VAR]);
 }
 
 template <int NS, bool VAR>
@@ -395,6 +443,16 @@ cudaError_t launch_force_elem_iso(const DevState &d, cudaStream_t st) {
     k_force_elem_iso<6><<<g, kIsoBlock, iso_smem<6>(), st>>>(d);
   else
     k_force_elem_iso<8><<<g, kIsoBlock, iso_smem<8>(), st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geom_factors(const DevState &d, cudaStream_t st) {
+  if (d.ns == 3)
+    launch_geom_factors_ns<3>(d, st);
+  else if (d.ns == 6)
+    launch_geom_factors_ns<6>(d, st);
+  else
+    launch_geom_factors_ns<8>(d, st);
   return cudaGetLastError();
 }
 

@@ -113,6 +113,32 @@ __device__ __forceinline__ void jac_at(const IsoGeo<N, T> &m, int gx, int gy, T 
   j11 = m.sJ[(3 * NG + g) * m.stride];
 }
 
+// The same Jacobians read from per-element records in global memory:
+// entry q of point g of element K at J[(q * N * N + g) * ne] (J = base + K).
+template <int N, typename T> struct IsoGeoG {
+  const T *__restrict__ J;
+  size_t ne;
+};
+
+// A read-only load that the compiler may not merge with an earlier one of
+// the same address: each stage re-reads J (an L1 hit) instead of keeping all
+// 4 N^2 values live in registers between the stages.
+__device__ __forceinline__ double ld_nc_fresh(const double *p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+template <int N>
+__device__ __forceinline__ void jac_at(const IsoGeoG<N, double> &m, int gx, int gy, double &j00,
+                                       double &j01, double &j10, double &j11) {
+  const int g = gx + N * gy, NG = N * N;
+  j00 = ld_nc_fresh(m.J + (size_t)(0 * NG + g) * m.ne);
+  j01 = ld_nc_fresh(m.J + (size_t)(1 * NG + g) * m.ne);
+  j10 = ld_nc_fresh(m.J + (size_t)(2 * NG + g) * m.ne);
+  j11 = ld_nc_fresh(m.J + (size_t)(3 * NG + g) * m.ne);
+}
+
 // Reference gradients (d/dxi, d/deta) of a Q2 field at the N x N Gauss
 // points, sum-factorised: row sums along xi, then columns along eta.
 template <int N, typename T>
@@ -256,6 +282,10 @@ __device__ __forceinline__ void mass_factor(const IsoGeo<DgSpace<NS>::NGP, T> &m
       },
       F);
 }
+
+// A factor in a [NS (NS + 1) / 2][ne] array of element records: L row by
+// row, then 1/D (SoA, entry i of element K at f[i * ne + K]).
+template <int NS> constexpr int mass_factor_words() { return NS * (NS + 1) / 2; }
 
 // x <- M^-1 x with the factor above.
 template <int NS, typename T>

@@ -98,6 +98,8 @@ struct DevState {
   float4 *map32ab;     // general mesh: [ne] (Ax, Ay, Bx, By) of the element map
   float2 *map32c;      // general mesh: [ne] (cx, cy)
   float4 *iso32;       // curved mesh: [4][ne] node offsets from the centre node
+  double *mfac;        // FP64, general or curved mesh: [ns(ns+1)/2][ne] L D L^T of M_K
+  double *isoJ;        // FP64, curved mesh: [4 NGP^2][ne] J at the Gauss points
   float4 *nodec4;      // [nn] (m/dt, qx, qy, l Cw rho_w) records
   float2 *vo2;         // [nn] ocean velocity
   float2 *lines32;     // [nx + ny] (h, 1/h) per mesh column, then per row
@@ -169,6 +171,9 @@ cudaError_t launch_force_elem_general(const DevState &d, cudaStream_t st);
 // isoparametric (Q2) meshes
 cudaError_t setup_iso_kernels();
 cudaError_t setup_general_kernels();  // once per device, before any capture
+// FP64 general / curved meshes: the per-element mass factors (and curved
+// Jacobians) the element kernels read, once at state creation
+cudaError_t launch_geom_factors(const DevState &d, cudaStream_t st);
 cudaError_t launch_element_iso(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
 cudaError_t launch_strain_diag_iso(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_force_elem_iso(const DevState &d, cudaStream_t st);
