@@ -42,17 +42,18 @@ UNIT = "element-subcycles/s"
 # forces 254.  DG1: 153, 36, 44, 63, 32, 146.
 ELEM_FLOPS = {3: 474, 6: 1055}
 # The same count for the general-quad element kernel k_element_gen (bilinear
-# map and L D L^T of the local mass matrix per element, Gauss-point strain,
-# stress and forces with det J cancelled): DG2 = map 18, mass factor 147,
-# reference gradients 252, strain integrands 165, moments 195 + 195,
-# solves 198 + 198, invariants 24, Gauss evaluation 132 + 132, rheology 183,
+# map per element, Gauss-point strain, stress and forces with det J
+# cancelled; the L D L^T factor of the local mass matrix is read from the
+# per-element records written at state creation): DG2 = map 18, reference
+# gradients 252, strain integrands 165, moments 195 + 195, solves
+# 198 + 198, invariants 24, Gauss evaluation 132 + 132, rheology 183,
 # update 61, force integrands 192, force sums 270.
-GEN_ELEM_FLOPS = {3: 1051, 6: 2362, 8: 2990}
+GEN_ELEM_FLOPS = {3: 1019, 6: 2215, 8: 2675}
 # Isoparametric (curved Q2) elements, k_element_iso: the same stages with the
-# Jacobians at the Gauss points formed once per element from the 9 node
-# positions (reference gradients 252, det J 27, weights 18) and the local
-# mass matrix by the Gauss rule instead of the exact moments.
-ISO_ELEM_FLOPS = {3: 1199, 6: 2724, 8: 3491}
+# Jacobians at the Gauss points read from the per-element records (no map
+# coefficients and no Jacobian arithmetic in the strain, rheology and force
+# integrands).
+ISO_ELEM_FLOPS = {3: 905, 6: 2053, 8: 2513}
 # Transport step (k_advect, rectilinear mesh), per element and Runge-Kutta
 # stage: volume terms at NQ x NQ points (velocity, contravariant flux,
 # traces, basis gradients), NQ points on each of the 4 edges (velocity,
@@ -82,7 +83,6 @@ NCU_TRAFFIC = {
     ("mesh256_dg2", "fp64", "k_element_f64<6>"): 14248448 + 768,
     ("mesh1024_dg2", "fp64", "k_element_f64<6>"): 234955776 + 248424704,
     ("mesh1024_dg2", "mixed", "k_subcycle_mix<6,32,8>"): 214103552 + 103840256,
-    ("mesh256_dg2_iso", "fp64", "k_element_iso<6>"): 18532608 + 18688000,
 }
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
