@@ -338,13 +338,15 @@ MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp
  * four stages: strain, the stress update of Listing 1, divergence, velocity):
  * the forward sweep keeps checkpoints (v, S) every checkpoint_every
  * subcycles, and each segment's velocities are recomputed before it is
- * reversed.  The drag's kink |v_o - v| = 0 takes derivative 0.  Outputs (any
+ * reversed; the last segment's velocities are recorded during the forward
+ * sweep, so checkpoint_every >= n stores every velocity and recomputes
+ * nothing.  The drag's kink |v_o - v| = 0 takes derivative 0.  Outputs (any
  * may be NULL): *J; dJ_dPstar [N_e]; dJ_dtau [2][N_n]; host memory with
  * on_device = 0 (the call then waits), device memory with on_device = 1.
  * Afterwards the state holds the result of the n subcycles, as after
  * mevp_run_subcycles(n).  Allocates its working memory (cudaMalloc):
- * about (n/checkpoint_every) (2 N_n + 3 n_stress N_e) + (checkpoint_every
- * + 8) 2 N_n + 40 N_e doubles.  Any stress dofs and ice degree; with DG1/DG2
+ * about (n/k) (2 N_n + 3 n_stress N_e) + (k + 8) 2 N_n + 40 N_e doubles,
+ * k = min(checkpoint_every, n).  Any stress dofs and ice degree; with DG1/DG2
  * ice the strength at each Gauss point is P*_K times that point's
  * max(0, h) exp(-C (1 - clamp(a))).  MEVP_ERR_UNSUPPORTED for MEVP_MIXED and
  * for general or curved meshes. */

@@ -436,7 +436,7 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
   if (!s->prepared) return afail(MEVP_ERR_STATE, "adjoint: call mevp_begin_step first");
   const DevState &d = s->d;
   const size_t nn = d.nn, ne = d.ne, ns = s->ns;
-  const int k = checkpoint_every;
+  const int k = checkpoint_every < n ? checkpoint_every : n;
   const int nseg = (n + k - 1) / k;
   const size_t vbytes = sizeof(double) * 2 * nn, sbytes = sizeof(double) * 3 * ns * ne;
   const int nparts = blocks((long long)nn, kBlock);
@@ -489,10 +489,21 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
       ADJ_CUDA(cudaMemcpyAsync(ck_S[g], d.S, sbytes, cudaMemcpyDeviceToDevice, st),
                "adjoint checkpoint");
       const int len = (g == nseg - 1) ? n - g * k : k;
+      // the last segment's velocities are recorded as they are computed, so
+      // the reverse sweep needs no recomputation for it (with
+      // checkpoint_every >= n: none at all)
+      const bool record = g == nseg - 1;
+      if (record)
+        ADJ_CUDA(cudaMemcpyAsync(hist, d.vel[s->cur], vbytes, cudaMemcpyDeviceToDevice, st),
+                 "adjoint history");
       for (int i = 0; i < len; ++i) {
         ADJ_CUDA(launch_subcycle_f64(d, s->rheo, s->has_vo, s->cur, st, nullptr),
                  "adjoint forward");
         s->cur ^= 1;
+        if (record)
+          ADJ_CUDA(cudaMemcpyAsync(hist + (size_t)(i + 1) * 2 * nn, d.vel[s->cur], vbytes,
+                                   cudaMemcpyDeviceToDevice, st),
+                   "adjoint history");
       }
     }
     // final forward state, restored after the reverse sweep
@@ -512,16 +523,19 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
     bool first = true;
     for (int g = nseg - 1; g >= 0; --g) {
       const int len = (g == nseg - 1) ? n - g * k : k;
-      // recompute the segment's velocities: hist[i] = v after i subcycles of the segment
+      // recompute the segment's velocities: hist[i] = v after i subcycles of
+      // the segment (the last segment's were recorded by the forward sweep)
       const int cur_g = cur0 ^ ((g * k) & 1);
-      ADJ_CUDA(cudaMemcpyAsync(d.vel[cur_g], ck_v[g], vbytes, cudaMemcpyDeviceToDevice, st),
-               "adjoint restore");
-      ADJ_CUDA(cudaMemcpyAsync(d.S, ck_S[g], sbytes, cudaMemcpyDeviceToDevice, st),
-               "adjoint restore");
-      ADJ_CUDA(cudaMemcpyAsync(hist, ck_v[g], vbytes, cudaMemcpyDeviceToDevice, st),
-               "adjoint restore");
+      if (g != nseg - 1) {
+        ADJ_CUDA(cudaMemcpyAsync(d.vel[cur_g], ck_v[g], vbytes, cudaMemcpyDeviceToDevice, st),
+                 "adjoint restore");
+        ADJ_CUDA(cudaMemcpyAsync(d.S, ck_S[g], sbytes, cudaMemcpyDeviceToDevice, st),
+                 "adjoint restore");
+        ADJ_CUDA(cudaMemcpyAsync(hist, ck_v[g], vbytes, cudaMemcpyDeviceToDevice, st),
+                 "adjoint restore");
+      }
       int c = cur_g;
-      for (int i = 0; i < len; ++i) {
+      for (int i = 0; i < len && g != nseg - 1; ++i) {
         ADJ_CUDA(launch_subcycle_f64(d, s->rheo, s->has_vo, c, st, nullptr), "adjoint recompute");
         c ^= 1;
         ADJ_CUDA(cudaMemcpyAsync(hist + (size_t)(i + 1) * 2 * nn, d.vel[c], vbytes,
