@@ -348,8 +348,9 @@ MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp
  * about (n/k) (2 N_n + 3 n_stress N_e) + (k + 8) 2 N_n + 40 N_e doubles,
  * k = min(checkpoint_every, n).  Any stress dofs and ice degree; with DG1/DG2
  * ice the strength at each Gauss point is P*_K times that point's
- * max(0, h) exp(-C (1 - clamp(a))).  MEVP_ERR_UNSUPPORTED for MEVP_MIXED and
- * for general or curved meshes. */
+ * max(0, h) exp(-C (1 - clamp(a))).  Any mesh: on general and curved
+ * elements the reverse mode follows the Gauss-point form of the forward
+ * kernels.  MEVP_ERR_UNSUPPORTED for MEVP_MIXED. */
 MEVP_API int mevp_adjoint_kinetic_energy(mevp_state *state, int n, int checkpoint_every,
                                          double *J, double *dJ_dPstar, double *dJ_dtau,
                                          int on_device);

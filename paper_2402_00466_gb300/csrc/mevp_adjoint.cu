@@ -19,6 +19,12 @@
 //        reversed at every Gauss point (X = P/(2 alpha Delta), Delta^-1/2 etc.)
 //   strain: linear in v^{p-1}  ->  transposed reference operators
 //
+// On general (bilinear) and curved (isoparametric) elements the same stages
+// run through the Gauss-point form of the forward kernels: the transposes of
+// the Gauss evaluation, the weighted moments, the Q2 reference gradients and
+// the mass solve (M_K is symmetric, so M_K^-T = M_K^-1), with the Jacobians
+// and mass factors of the forward kernels.
+//
 // Since the stress update is affine in S, the reverse sweep needs only the
 // velocities v^{p-1}, v^p of each subcycle; the Gauss-point quantities are
 // recomputed from them.  Checkpoints (v, S) are kept every k subcycles and
@@ -32,6 +38,7 @@
 #include <vector>
 
 #include "mevp_elem.cuh"
+#include "mevp_geom.cuh"
 #include "mevp_internal.cuh"
 #include "mevp_ref.cuh"
 
@@ -315,6 +322,243 @@ __device__ __forceinline__ void adj_elem(const DevState &d, const Rheo &r, const
   }
 }
 
+// ---- general and curved elements ---------------------------------------------
+// Transpose of gauss_eval: Fbar_s = sum_g psi_s(g) fbar_g.
+template <int NS>
+__device__ __forceinline__ void psi_T(const double *fbar, double Fbar[NS]) {
+  constexpr int NG = DgSpace<NS>::NGP * DgSpace<NS>::NGP;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double acc = 0.0;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const double c = psi<NS>(s, g);
+      if (c != 0.0) acc = fma(c, fbar[g], acc);
+    }
+    Fbar[s] = acc;
+  }
+}
+
+// Transpose of gauss_moments: Dbar_g = w_g sum_s psi_s(g) Rbar_s.
+template <int NS>
+__device__ __forceinline__ void moments_T(const double Rbar[NS], double *Dbar) {
+  constexpr int N = DgSpace<NS>::NGP;
+  gauss_eval<NS>(Rbar, Dbar);
+#pragma unroll
+  for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) Dbar[gx + N * gy] *= Gauss<N>::w(gx) * Gauss<N>::w(gy);
+}
+
+// Transpose of ref_grad_gauss: wbar_j = sum_g (dphi_j/dxi (g) gxib_g +
+// dphi_j/deta (g) getab_g), sum-factorised.
+template <int N>
+__device__ __forceinline__ void ref_grad_T(const double *gxib, const double *getab,
+                                           double wbar[9]) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    double t1[N], t2[N];
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) {
+      double p = 0.0, q = 0.0;
+#pragma unroll
+      for (int gy = 0; gy < N; ++gy) {
+        const double c0 = lq<N>(b, gy), cd = dlq<N>(b, gy);
+        if (c0 != 0.0) p = fma(c0, gxib[gx + N * gy], p);
+        if (cd != 0.0) q = fma(cd, getab[gx + N * gy], q);
+      }
+      t1[gx] = p;
+      t2[gx] = q;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double x = 0.0;
+#pragma unroll
+      for (int gx = 0; gx < N; ++gx) {
+        const double cd = dlq<N>(a, gx), c0 = lq<N>(a, gx);
+        if (cd != 0.0) x = fma(cd, t1[gx], x);
+        if (c0 != 0.0) x = fma(c0, t2[gx], x);
+      }
+      wbar[a + 3 * b] = x;
+    }
+  }
+}
+
+// Reverse of one subcycle's element stages on a general or curved element
+// (the forward: strain_general, relax_general, forces_general).
+template <int NS, bool VAR, typename G>
+__device__ __forceinline__ void adj_elem_geo(const DevState &d, const Rheo &r, const AdjBuf &b,
+                                             const double *__restrict__ vprev, int K, double C,
+                                             const G &m) {
+  constexpr int N = DgSpace<NS>::NGP, NG = N * N;
+  const int ky = K / d.nx, kx = K - ky * d.nx;
+  const size_t nn = d.nn, ne = d.ne;
+  MassFactor<NS> F;
+  {
+    constexpr int NL = NS * (NS - 1) / 2;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) F.L[i] = d.mfac[(size_t)i * ne + K];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) F.Dinv[i] = d.mfac[(size_t)(NL + i) * ne + K];
+  }
+  // forward recompute: strain invariants at the Gauss points
+  double pg_[NG], qg_[NG], gg_[NG];
+  {
+    double u[9], v[9];
+    gather9(vprev, d.nw, kx, ky, u, d.flags, d.nn);
+    gather9(vprev + nn, d.nw, kx, ky, v, d.flags, d.nn);
+    double E11[NS], E22[NS], Esh[NS], Pc[NS], Qc[NS], Gc[NS];
+    strain_general<NS>(m, F, u, v, E11, E22, Esh);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Pc[s] = E11[s] + E22[s];
+      Qc[s] = r.ie * (E11[s] - E22[s]);
+      Gc[s] = r.ie * Esh[s];
+    }
+    gauss_eval<NS>(Pc, pg_);
+    gauss_eval<NS>(Qc, qg_);
+    gauss_eval<NS>(Gc, gg_);
+  }
+  // divergence reversed: f = -(ref_grad)^T (a, b), so (abar, bbar) = -ref_grad(fbar)
+  double B11[NS], B12[NS], B22[NS];
+  {
+    double fb[9], axb[NG], bxb[NG], ayb[NG], byb[NG];
+    gather9(b.Fbar, d.nw, kx, ky, fb, d.flags, d.nn);
+    ref_grad_gauss<N>(fb, axb, bxb);
+    gather9(b.Fbar + nn, d.nw, kx, ky, fb, d.flags, d.nn);
+    ref_grad_gauss<N>(fb, ayb, byb);
+    double s11b[NG], s12b[NG], s22b[NG];
+#pragma unroll
+    for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+      for (int gx = 0; gx < N; ++gx) {
+        const int g = gx + N * gy;
+        double j00, j01, j10, j11;
+        jac_at<N>(m, gx, gy, j00, j01, j10, j11);
+        const double w = -(Gauss<N>::w(gx) * Gauss<N>::w(gy));
+        s11b[g] = w * fma(axb[g], j11, -(bxb[g] * j10));
+        s12b[g] = w * (fma(bxb[g], j00, -(axb[g] * j01)) + fma(ayb[g], j11, -(byb[g] * j10)));
+        s22b[g] = w * fma(byb[g], j00, -(ayb[g] * j01));
+      }
+    psi_T<NS>(s11b, B11);
+    psi_T<NS>(s12b, B12);
+    psi_T<NS>(s22b, B22);
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    B11[s] += b.Sbar[(size_t)(0 * NS + s) * ne + K];
+    B12[s] += b.Sbar[(size_t)(1 * NS + s) * ne + K];
+    B22[s] += b.Sbar[(size_t)(2 * NS + s) * ne + K];
+    b.Sbar[(size_t)(0 * NS + s) * ne + K] = r.fac * B11[s];
+    b.Sbar[(size_t)(1 * NS + s) * ne + K] = r.fac * B12[s];
+    b.Sbar[(size_t)(2 * NS + s) * ne + K] = r.fac * B22[s];
+  }
+  // stress update reversed: S11 = fac S + RP + ie RQ (- Ph on s = 0 with DG0
+  // ice), S22 = fac S + RP - ie RQ, S12 = fac S + ie RG, R = M^-1 moments
+  double RP[NS], RQ[NS], RG[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    RP[s] = B11[s] + B22[s];
+    RQ[s] = r.ie * (B11[s] - B22[s]);
+    RG[s] = r.ie * B12[s];
+  }
+  double Phbar = VAR ? 0.0 : -RP[0];
+  mass_solve<NS>(F, RP);
+  mass_solve<NS>(F, RQ);
+  mass_solve<NS>(F, RG);
+  double pb[NG], qb[NG], gb[NG];
+  moments_T<NS>(RP, pb);
+  moments_T<NS>(RQ, qb);
+  moments_T<NS>(RG, gb);
+  const double Ph = VAR ? 0.0 : d.Pe[K] * r.hainv;
+#pragma unroll
+  for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) {
+      const int g = gx + N * gy;
+      double j00, j01, j10, j11;
+      jac_at<N>(m, gx, gy, j00, j01, j10, j11);
+      const double det = fma(j00, j11, -(j01 * j10));
+      const double d2 = fma(gg_[g], gg_[g], fma(qg_[g], qg_[g], fma(pg_[g], pg_[g], r.dmin2)));
+      const double R = rsqrt(d2);
+      double Pg = Ph;
+      if constexpr (VAR) Pg = d.Pg[(size_t)g * ne + K] * r.hainv;
+      const double Xd = Pg * R * det;
+      const double Xdbar = pb[g] * pg_[g] + qb[g] * qg_[g] + gb[g] * gg_[g];
+      double Pgbar = Xdbar * R * det;
+      if constexpr (VAR) {
+        Pgbar -= det * pb[g];
+        const double h = fmax(0.0, dg_at_gauss<N>(d.H, d.na, ne, K, gx, gy));
+        const double a = fmin(1.0, fmax(0.0, dg_at_gauss<N>(d.A, d.na, ne, K, gx, gy)));
+        Phbar = fma(Pgbar, h * exp(-C * (1.0 - a)), Phbar);
+      } else {
+        Phbar += Pgbar;
+      }
+      const double d2bar = -0.5 * (Xdbar * Pg * det) * R * R * R;
+      pb[g] = fma(2.0 * pg_[g], d2bar, Xd * pb[g]);
+      qb[g] = fma(2.0 * qg_[g], d2bar, Xd * qb[g]);
+      gb[g] = fma(2.0 * gg_[g], d2bar, Xd * gb[g]);
+    }
+  b.Pbar[K] += Phbar * r.hainv;
+  // Gauss evaluation and invariants reversed, then the strain projection
+  double E11b[NS], E22b[NS], Eshb[NS];
+  {
+    double Pcb[NS], Qcb[NS], Gcb[NS];
+    psi_T<NS>(pb, Pcb);
+    psi_T<NS>(qb, Qcb);
+    psi_T<NS>(gb, Gcb);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      E11b[s] = fma(r.ie, Qcb[s], Pcb[s]);
+      E22b[s] = fma(-r.ie, Qcb[s], Pcb[s]);
+      Eshb[s] = r.ie * Gcb[s];
+    }
+  }
+  mass_solve<NS>(F, E11b);
+  mass_solve<NS>(F, E22b);
+  mass_solve<NS>(F, Eshb);
+  double D11b[NG], D22b[NG], Dshb[NG];
+  moments_T<NS>(E11b, D11b);
+  moments_T<NS>(E22b, D22b);
+  moments_T<NS>(Eshb, Dshb);
+  double uxib[NG], uetab[NG], vxib[NG], vetab[NG];
+#pragma unroll
+  for (int gy = 0; gy < N; ++gy)
+#pragma unroll
+    for (int gx = 0; gx < N; ++gx) {
+      const int g = gx + N * gy;
+      double j00, j01, j10, j11;
+      jac_at<N>(m, gx, gy, j00, j01, j10, j11);
+      uxib[g] = fma(j11, D11b[g], -(j01 * Dshb[g]));
+      uetab[g] = fma(j00, Dshb[g], -(j10 * D11b[g]));
+      vxib[g] = fma(j11, Dshb[g], -(j01 * D22b[g]));
+      vetab[g] = fma(j00, D22b[g], -(j10 * Dshb[g]));
+    }
+  double ub[9], vb[9];
+  ref_grad_T<N>(uxib, uetab, ub);
+  ref_grad_T<N>(vxib, vetab, vb);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    b.ubar[(size_t)j * ne + K] = ub[j];
+    b.ubar[(size_t)(9 + j) * ne + K] = vb[j];
+  }
+}
+
+template <int NS, bool VAR>
+__global__ void __launch_bounds__(128) k_adj_elem_geo(DevState d, Rheo r, AdjBuf b,
+                                                      const double *__restrict__ vprev, double C) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  if (d.isoJ) {
+    const IsoGeoG<DgSpace<NS>::NGP, double> m{d.isoJ + K, (size_t)d.ne};
+    adj_elem_geo<NS, VAR>(d, r, b, vprev, K, C, m);
+  } else {
+    const int ky = K / d.nx, kx = K - ky * d.nx;
+    const QuadMap m = quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1));
+    adj_elem_geo<NS, VAR>(d, r, b, vprev, K, C, m);
+  }
+}
+
 // Persistent: the grid is the number of blocks resident on the chip and each
 // block takes an equal contiguous share of the element warps (a grid of one
 // block per 128 elements ends in a partial wave: 256^2 gives 512 blocks for
@@ -356,25 +600,6 @@ int adj_elem_grid(const DevState &d) {
 }
 
 // ---- gradients -------------------------------------------------------------------
-// lumped area l_j (same quadrature as the mass)
-__global__ void k_adj_area(DevState d, AdjBuf b) {
-  const int node = blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= d.nn) return;
-  const int iy = node / d.nw, ix = node - iy * d.nw;
-  const int kx1 = (ix & 1) ? (ix >> 1) : (ix >> 1) - 1, kx2 = ix >> 1;
-  const int ky1 = (iy & 1) ? (iy >> 1) : (iy >> 1) - 1, ky2 = iy >> 1;
-  double l = 0.0;
-  for (int ky = ky1; ky <= ky2; ++ky) {
-    if (ky < 0 || ky >= d.ny) continue;
-    for (int kx = kx1; kx <= kx2; ++kx) {
-      if (kx < 0 || kx >= d.nx) continue;
-      const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
-      l += area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
-    }
-  }
-  b.area[node] = l;
-}
-
 // dJ/dP*_K = Pbar_K max(0,H) exp(-C(1-clamp A)) (DG0 ice; with DG1/DG2 ice
 // Pbar already holds dJ/dP*_K),  dJ/dtau_j = l_j qbar_j
 __global__ void k_adj_grads(DevState d, AdjBuf b, double C, double *gP, double *gT) {
@@ -430,7 +655,6 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
   int rc = api_check_state(s);
   if (rc) return rc;
   if (s->prec != MEVP_FP64) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: FP64 states only");
-  if (s->d.xy || s->d.nxy) return afail(MEVP_ERR_UNSUPPORTED, "adjoint: rectilinear meshes only");
   if (n < 1) return afail(MEVP_ERR_ARG, "adjoint: n=%d < 1", n);
   if (checkpoint_every < 1) return afail(MEVP_ERR_ARG, "adjoint: checkpoint_every < 1");
   if (!s->prepared) return afail(MEVP_ERR_STATE, "adjoint: call mevp_begin_step first");
@@ -517,7 +741,7 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
     ADJ_CUDA(cudaMemsetAsync(b.Pbar, 0, sizeof(double) * ne, st), "adjoint init");
     k_adj_seed<<<nparts, kBlock, 0, st>>>(d, b, d.vel[cur_final]);
     k_adj_sum<<<1, 32, 0, st>>>(b, nparts);
-    k_adj_area<<<blocks(nn, kBlock), kBlock, 0, st>>>(d, b);
+    ADJ_CUDA(launch_lumped_area(d, b.area, st), "adjoint area");
     ADJ_CUDA(cudaGetLastError(), "adjoint seed");
     // reverse sweep, segment by segment
     bool first = true;
@@ -552,7 +776,18 @@ extern "C" int mevp_adjoint_kinetic_energy(mevp_state *s, int n, int checkpoint_
         const double *vnext = hist + (size_t)(i + 1) * 2 * nn;
         k_adj_node<<<blocks(nn, kBlock), kBlock, 0, st>>>(d, b, vprev, vnext, s->has_vo ? 1 : 0,
                                                            first ? 0 : 1);
-        if (ns == 3)
+        if (d.xy || d.nxy) {
+          const int gg = blocks(ne, 128);
+          if (ns == 3)
+            var ? k_adj_elem_geo<3, true><<<gg, 128, 0, st>>>(d, s->rheo, b, vprev, C)
+                : k_adj_elem_geo<3, false><<<gg, 128, 0, st>>>(d, s->rheo, b, vprev, C);
+          else if (ns == 6)
+            var ? k_adj_elem_geo<6, true><<<gg, 128, 0, st>>>(d, s->rheo, b, vprev, C)
+                : k_adj_elem_geo<6, false><<<gg, 128, 0, st>>>(d, s->rheo, b, vprev, C);
+          else
+            var ? k_adj_elem_geo<8, true><<<gg, 128, 0, st>>>(d, s->rheo, b, vprev, C)
+                : k_adj_elem_geo<8, false><<<gg, 128, 0, st>>>(d, s->rheo, b, vprev, C);
+        } else if (ns == 3)
           var ? k_adj_elem<3, true><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C)
               : k_adj_elem<3, false><<<eg, kAdjElemBlock, 0, st>>>(d, s->rheo, b, vprev, C);
         else if (ns == 6)

@@ -383,6 +383,36 @@ __device__ __forceinline__ double mass_integral_gauss(const DevState &d, int kx,
   return acc;
 }
 
+// int_K phi_j of the Q2 function of local node (a, b) on element (kx, ky).
+__device__ __forceinline__ double node_area(const DevState &d, int kx, int ky, int a, int b) {
+  if (d.nxy)
+    return d.ns == 3 ? iso_integral<2>(d, kx, ky, a, b, false)
+                     : iso_integral<3>(d, kx, ky, a, b, false);
+  if (d.xy)
+    return node_area_general(
+        quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1)), a, b);
+  const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
+  return area * q2w(a) * q2w(b);
+}
+
+// Lumped area l_j = sum_K int_K phi_j (elements in ascending order).
+__global__ void k_lumped_area(DevState d, double *__restrict__ out) {
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= d.nn) return;
+  const int iy = node / d.nw, ix = node - iy * d.nw;
+  const int kx1 = (ix & 1) ? (ix >> 1) : (ix >> 1) - 1, kx2 = ix >> 1;
+  const int ky1 = (iy & 1) ? (iy >> 1) : (iy >> 1) - 1, ky2 = iy >> 1;
+  double l = 0.0;
+  for (int ky = ky1; ky <= ky2; ++ky) {
+    if (ky < 0 || ky >= d.ny) continue;
+    for (int kx = kx1; kx <= kx2; ++kx) {
+      if (kx < 0 || kx >= d.nx) continue;
+      l += node_area(d, kx, ky, ix - 2 * kx, iy - 2 * ky);
+    }
+  }
+  out[node] = l;
+}
+
 // Lumped mass m_j = rho_ice sum_K max(0,H_K) int_K phi_j and area
 // l_j = sum_K int_K phi_j (hx hy w_a w_b on a rectangle, w = 1/6, 2/3, 1/6;
 // the exact integral against the affine det J on a general element), then the
@@ -398,16 +428,7 @@ __global__ void k_node_constants(DevState d, int cur, mevp_params p, int has_vo)
     if (ky < 0 || ky >= d.ny) continue;
     for (int kx = kx1; kx <= kx2; ++kx) {
       if (kx < 0 || kx >= d.nx) continue;
-      double w;
-      if (d.nxy) {
-        w = d.ns == 3 ? iso_integral<2>(d, kx, ky, ix - 2 * kx, iy - 2 * ky, false)
-                      : iso_integral<3>(d, kx, ky, ix - 2 * kx, iy - 2 * ky, false);
-      } else if (d.xy) {
-        w = node_area_general(quad_map(d.xy, d.nx, kx, ky, d.flags, (long long)(d.nx + 1) * (d.ny + 1)), ix - 2 * kx, iy - 2 * ky);
-      } else {
-        const double area = (d.xline[kx + 1] - d.xline[kx]) * (d.yline[ky + 1] - d.yline[ky]);
-        w = area * q2w(ix - 2 * kx) * q2w(iy - 2 * ky);
-      }
+      const double w = node_area(d, kx, ky, ix - 2 * kx, iy - 2 * ky);
       l += w;
       if (d.na == 1 && !d.nxy)
         mh += fmax(0.0, d.H[ky * d.nx + kx]) * w;
@@ -602,6 +623,11 @@ int f64_node_ctas_per_sm() {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_node, kNodeBlock, 0);
   return n > 0 ? n : 1;
+}
+
+cudaError_t launch_lumped_area(const DevState &d, double *out, cudaStream_t st) {
+  k_lumped_area<<<blocks(d.nn, 256), 256, 0, st>>>(d, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st) {

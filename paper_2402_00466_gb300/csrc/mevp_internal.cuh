@@ -164,6 +164,8 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
 // the element part alone (any geometry, stress dofs and ice degree)
 cudaError_t launch_element_f64(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
 cudaError_t launch_strain_diag(const DevState &d, int cur, cudaStream_t st);
+// l_j = sum_K int_K phi_j into out[nn] (the area weights of the wind stress)
+cudaError_t launch_lumped_area(const DevState &d, double *out, cudaStream_t st);
 // general (non-affine) meshes: element kernel and read-back diagnostics
 cudaError_t launch_element_general(const DevState &d, const Rheo &r, int cur, cudaStream_t st);
 cudaError_t launch_strain_diag_general(const DevState &d, int cur, cudaStream_t st);

@@ -103,6 +103,73 @@ def test_adjoint_with_dg_ice_matches_gpu_finite_differences(n_a, n_s):
     st.close()
 
 
+@pytest.mark.parametrize("n_a", [1, 3])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+@pytest.mark.parametrize("geometry", ["perturbed", "wavy", "curved"])
+def test_adjoint_general_mesh_matches_gpu_finite_differences(geometry, n_s, n_a):
+    """Bilinear and curved elements (the Gauss-point reverse mode with the
+    stored mass factors and Jacobians): per-element P* and nodal wind-stress
+    directions against central differences of the GPU forward."""
+    nx, ny = 10, 8
+    case = W.small_case(nx, ny, n_s, seed=111 + n_s + n_a, geometry=geometry)
+    ne, nn, _ = W.sizes(nx, ny)
+    rng = np.random.default_rng(112 + n_s)
+    if n_a > 1:
+        H = np.vstack([rng.uniform(0.6, 1.6, ne)] + [rng.uniform(-0.2, 0.2, ne)] * (n_a - 1))
+        A = np.vstack([rng.uniform(0.8, 0.95, ne)] + [rng.uniform(-0.04, 0.04, ne)] * (n_a - 1))
+        case = dict(case, H=H, A=A)
+    n = 20
+    P0 = case["params"]["Pstar"] * rng.uniform(0.8, 1.2, ne)
+    st = mevp.State(nx, ny, n_s, vertex_xy=case["xy"], n_adv=n_a, params=case["params"])
+    reset(st, case, P0)
+    J, gP, gT = st.adjoint_kinetic_energy(n, checkpoint_every=6)
+    assert abs(J - J_gpu(st, case, n, P0, case["tau"])) <= 1e-12 * abs(J)
+    for _ in range(3):
+        dP = rng.standard_normal(ne)
+        dT = rng.standard_normal((2, nn))
+        for dirP, dirT in ((dP, 0 * dT), (0 * dP, dT)):
+            eP = 1e-6 * P0.mean() / np.abs(dirP).max() if np.any(dirP) else 0.0
+            eT = 1e-6 * np.abs(case["tau"]).max() / np.abs(dirT).max() if np.any(dirT) else 0.0
+            Jp = J_gpu(st, case, n, P0 + eP * dirP, case["tau"] + eT * dirT)
+            Jm = J_gpu(st, case, n, P0 - eP * dirP, case["tau"] - eT * dirT)
+            fd = (Jp - Jm) / 2.0
+            ad = eP * float(gP @ dirP) + eT * float(np.sum(gT * dirT))
+            assert abs(fd - ad) <= 1e-5 * abs(ad) + 1e-14 * abs(J), (fd, ad)
+    st.close()
+
+
+def test_adjoint_general_mesh_matches_oracle_finite_differences():
+    """Curved mesh: wind-stress directions and a uniform P* direction against
+    central differences of the FP64 oracle."""
+    nx, ny = 8, 7
+    case = W.small_case(nx, ny, 6, seed=121, geometry="curved")
+    n = 15
+    ne, nn, _ = W.sizes(nx, ny)
+    st = setup(case)
+    J, gP, gT = st.adjoint_kinetic_energy(n, checkpoint_every=4)
+    st.close()
+    m, _ = oracle.lumped(nx, ny, case["xy"], 6, 1, case["params"], case["H"])
+
+    def J_orc(params, tau):
+        v, _ = oracle.subcycles(nx, ny, case["xy"], 6, 1, params, case["H"], case["A"], tau,
+                                case["vel0"], case["S0"], n)
+        return 0.5 * float(np.sum(m * (v[0] ** 2 + v[1] ** 2)))
+
+    p0 = case["params"]
+    assert abs(J_orc(p0, case["tau"]) - J) <= 1e-10 * abs(J)
+    eps = 1e-6 * p0["Pstar"]
+    fd = (J_orc(dict(p0, Pstar=p0["Pstar"] + eps), case["tau"]) -
+          J_orc(dict(p0, Pstar=p0["Pstar"] - eps), case["tau"])) / (2 * eps)
+    assert abs(fd - gP.sum()) <= 1e-5 * abs(fd), (fd, gP.sum())
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        d = rng.standard_normal((2, nn))
+        e = 1e-6 * np.abs(case["tau"]).max() / np.abs(d).max()
+        fd = (J_orc(p0, case["tau"] + e * d) - J_orc(p0, case["tau"] - e * d)) / (2 * e)
+        ad = float(np.sum(gT * d))
+        assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)
+
+
 def test_adjoint_matches_oracle_finite_differences():
     """Directional derivatives against central differences of the FP64 oracle:
     nodal wind-stress directions and a uniform P* direction (the oracle takes
