@@ -83,6 +83,7 @@ NCU_TRAFFIC = {
     ("mesh256_dg2", "fp64", "k_element_f64<6>"): 14248448 + 768,
     ("mesh1024_dg2", "fp64", "k_element_f64<6>"): 234955776 + 248424704,
     ("mesh1024_dg2", "mixed", "k_subcycle_mix<6,32,8>"): 214103552 + 103840256,
+    ("mesh256_dg2_iso", "fp64", "k_element_iso<6>"): 44171776 + 55296000,
 }
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
