@@ -164,10 +164,14 @@ def test_adjoint_general_mesh_matches_oracle_finite_differences():
     rng = np.random.default_rng(7)
     for _ in range(3):
         d = rng.standard_normal((2, nn))
-        e = 1e-6 * np.abs(case["tau"]).max() / np.abs(d).max()
+        # a larger step than elsewhere: a direction whose derivative is small
+        # against the terms it sums (cancellation) needs the rounding of the
+        # two oracle runs divided by less
+        e = 1e-5 * np.abs(case["tau"]).max() / np.abs(d).max()
         fd = (J_orc(p0, case["tau"] + e * d) - J_orc(p0, case["tau"] - e * d)) / (2 * e)
         ad = float(np.sum(gT * d))
-        assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)
+        scale = float(np.sum(np.abs(gT * d)))
+        assert abs(fd - ad) <= 1e-5 * abs(ad) + 1e-8 * scale, (fd, ad, scale)
 
 
 def test_adjoint_matches_oracle_finite_differences():
