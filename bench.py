@@ -780,15 +780,18 @@ def _run_ours(a, torch, dist, ws, rank):
                                                     a.steps)}
         stable_ab = max(300.0, 4e6 / (case["L"] / nx))  # stable when alpha*h >~ 4e6 m
         variants["mixed_field_error"] = field_error(mevp, case, n_sub, stable_ab)
-        if a.workload != "mesh1024_dg2" and not general:
-            big = W.make_case("mesh1024_dg2")
+        big_name = {"mesh256_dg2_wavy": "mesh1024_dg2_wavy",
+                    "mesh256_dg2_iso": "mesh1024_dg2_iso"}.get(
+                        a.workload, None if general else "mesh1024_dg2")
+        if big_name and a.workload != big_name:
+            big = W.make_case(big_name)
             for prec in ("fp64", "mixed"):
                 mb = measure(mevp, torch, barrier, 1, big, prec, 2 if prec == "fp64" else 5, 3,
                              flush)
                 mb["state"].close()
                 nsteps = 2 if prec == "fp64" else 5
-                variants[f"{prec}_mesh1024_dg2"] = {
-                    "workload": "mesh1024_dg2", "value": mb["value"],
+                variants[f"{prec}_{big_name}"] = {
+                    "workload": big_name, "value": mb["value"],
                     "ms_per_step": mb["total_ms"] / nsteps,
                     "roofline": roofline_for(prec, big, mb["kt"], mb["total_ms"], nsteps)}
 

@@ -51,6 +51,11 @@ CONFIGS = {
     # (isoparametric Q2) elements, DG2, 500 subcycles
     "mesh256_dg2_iso": dict(nx=256, ny=256, n_s=6, n_a=1, n_sub=500, ice="grf", seeds=(2, 3),
                             wind_seed=12, geometry="wavy_iso"),
+    # the curvilinear meshes at 1024x1024 (the mixed path's HBM-bound size)
+    "mesh1024_dg2_wavy": dict(nx=1024, ny=1024, n_s=6, n_a=1, n_sub=500, ice="grf",
+                              seeds=(4, 5), wind_seed=13, geometry="wavy"),
+    "mesh1024_dg2_iso": dict(nx=1024, ny=1024, n_s=6, n_a=1, n_sub=500, ice="grf",
+                             seeds=(4, 5), wind_seed=13, geometry="wavy_iso"),
     # transport of DG2 H and A on 1024x1024 quads with a smooth velocity held
     # fixed (the step before the subcycles); one advection step per bench step
     "advect1024_dg2": dict(nx=1024, ny=1024, n_s=6, n_a=6, n_sub=0, ice="grf", seeds=(4, 5),
