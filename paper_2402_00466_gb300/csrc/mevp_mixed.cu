@@ -527,16 +527,21 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY))
 }
 
 // General (bilinear) elements: the per-element mass factorisation needs more
-// registers, so half as many threads per SM (128 registers a thread).
+// registers, so 768 threads per SM (80 registers a thread, 68 B spilled for
+// DG2).  Measured (element-subcycles/s, 1024^2 / 256^2 wavy DG2): 512
+// threads 8.14e9 / 4.81e9, 768 threads 8.65e9 / 5.17e9, 1024 threads
+// 7.89e9 / 4.37e9.
 template <int NS, int TX, int TY, bool VAR>
-__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
+__global__ void __launch_bounds__(TX *TY, 768 / (TX * TY))
     k_subcycle_mix_gen(DevState d, MixArgs ma, int cur) {
   extern __shared__ float4 smem[];
   mix_tile<NS, TX, TY, VAR, kGeoQuad>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
 }
 
 // Isoparametric elements: as the bilinear kernel, with the Jacobians at the
-// Gauss points in shared memory after the tile's buffers.
+// Gauss points in shared memory after the tile's buffers, at 512 threads per
+// SM (128 registers): with 768 or 1024 threads the spills cost more than the
+// occupancy gains (1024^2: 6.00e9 -> 4.89e9 / 4.46e9 element-subcycles/s).
 template <int NS, int TX, int TY, bool VAR>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
     k_subcycle_mix_iso(DevState d, MixArgs ma, int cur) {
