@@ -374,9 +374,9 @@ def _roofline_for(precision, case, kt, total_ms, steps):
     geo = case.get("geometry", "uniform")
     general = geo != "uniform"
     iso = geo in ("wavy_iso", "curved")
-    # FP32 map record (A, B, c) per bilinear element; 8 FP32 node offsets per
-    # isoparametric element
-    extra = 64 if iso else 24 if general else 0
+    # FP32 map record (A, B, c) per bilinear element, 8 FP32 node offsets per
+    # isoparametric element, and on both the FP32 factor of the mass matrix
+    extra = (64 if iso else 24) + 4 * ns * (ns + 1) // 2 if general else 0
     ach = (MIXED_SINGLE_PASS_BYTES[ns] + extra) * ne / el_s / 1e9
     own = (MIXED_OWN_BYTES[ns] + extra) * ne / el_s / 1e9
     return dict({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -385,7 +385,8 @@ def _roofline_for(precision, case, kt, total_ms, steps):
                            f"<{ns},32,{8 if big else 4}>",
                  "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
                  "bytes_per_element": MIXED_SINGLE_PASS_BYTES[ns] + extra,
-                 "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x (v R+W, v^n, tau, m)",
+                 "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x (v R+W, v^n, tau, m)"
+                                 + (" + FP32 geometry and mass-factor records" if general else ""),
                  "own_bytes_per_element": MIXED_OWN_BYTES[ns] + extra,
                  "achieved_own_bytes": own, "frac_own_bytes": own / hbm_peak,
                  "fp32_TFLOPs_approx": (ELEM_FLOPS[ns] * 1.1 + 4 * 40) * ne / el_s / 1e12,

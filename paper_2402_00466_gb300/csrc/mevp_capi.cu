@@ -60,7 +60,7 @@ constexpr int kMinGraphChunk = 4;
 constexpr int kMaxGraphChunk = 64;
 
 struct Layout {
-  size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, iso32, mfac, isoJ, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
+  size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, iso32, mfac, isoJ, mfac32, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,
       vel2a, vel2b, Pe32, nodec32, vo2, lines32, total;
 };
 
@@ -91,6 +91,8 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   const bool geo64 = (m->general || m->iso) && prec == MEVP_FP64;
   L.mfac = take(geo64 ? sizeof(double) * (ns * (ns + 1) / 2) * ne : 0);
   L.isoJ = take(m->iso && prec == MEVP_FP64 ? sizeof(double) * 4 * (ns == 3 ? 4 : 9) * ne : 0);
+  const bool geo32 = (m->general || m->iso) && prec == MEVP_MIXED;
+  L.mfac32 = take(geo32 ? sizeof(float) * (ns * (ns + 1) / 2) * ne : 0);
   L.vel0 = take(sizeof(double) * 2 * nn);
   L.vel1 = take(sizeof(double) * 2 * nn);
   L.S = take(sizeof(double) * 3 * ns * ne);
@@ -447,6 +449,7 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
     d.map32ab = (float4 *)(b + L.map32ab);
     d.map32c = (float2 *)(b + L.map32c);
     d.iso32 = mesh->iso ? (float4 *)(b + L.iso32) : nullptr;
+    d.mfac32 = (mesh->general || mesh->iso) ? (float *)(b + L.mfac32) : nullptr;
     d.nodec4 = (float4 *)(b + L.nodec32);
     d.vo2 = (float2 *)(b + L.vo2);
     d.lines32 = (float2 *)(b + L.lines32);

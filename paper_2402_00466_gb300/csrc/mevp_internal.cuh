@@ -100,6 +100,7 @@ struct DevState {
   float4 *iso32;       // curved mesh: [4][ne] node offsets from the centre node
   double *mfac;        // FP64, general or curved mesh: [ns(ns+1)/2][ne] L D L^T of M_K
   double *isoJ;        // FP64, curved mesh: [4 NGP^2][ne] J at the Gauss points
+  float *mfac32;       // mixed, general or curved mesh: [ns(ns+1)/2][ne] FP32 factor of M_K
   float4 *nodec4;      // [nn] (m/dt, qx, qy, l Cw rho_w) records
   float2 *vo2;         // [nn] ocean velocity
   float2 *lines32;     // [nx + ny] (h, 1/h) per mesh column, then per row

@@ -100,6 +100,7 @@ template <int NS, bool VAR, typename G>
 __device__ __forceinline__ void element_core_general(const float4 pv[9], float S11[NS],
                                                      float S12[NS], float S22[NS],
                                                      const Strength<NS, VAR> &P, const G &m,
+                                                     const MassFactor<NS, float> &F,
                                                      const MixArgs &a, float fx[9], float fy[9]) {
   float du[9], dv[9];
 #pragma unroll
@@ -107,8 +108,6 @@ __device__ __forceinline__ void element_core_general(const float4 pv[9], float S
     du[j] = __fsub_rn(pv[j].x, pv[4].x) + __fsub_rn(pv[j].y, pv[4].y);
     dv[j] = __fsub_rn(pv[j].z, pv[4].z) + __fsub_rn(pv[j].w, pv[4].w);
   }
-  MassFactor<NS, float> F;
-  mass_factor<NS>(m, F);
   float Pc[NS], Qc[NS], Gc[NS];
   {
     float E11[NS], E22[NS], Esh[NS];
@@ -178,6 +177,21 @@ __device__ __forceinline__ IsoGeo<N, float> iso_record(const DevState &d, size_t
     col[(3 * NG + g) * stride] = geta[g];
   }
   return IsoGeo<N, float>{col, stride};
+}
+
+// FP32 L D L^T factor of the element's mass matrix from the records written
+// once per outer step (the FP32 arithmetic of the element, done once).
+template <int NS>
+__device__ __forceinline__ MassFactor<NS, float> mass_record(const DevState &d, size_t K) {
+  constexpr int NL = NS * (NS - 1) / 2;
+  const long long ne = d.ne, n = (long long)mass_factor_words<NS>() * ne;
+  MassFactor<NS, float> F;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) F.L[i] = ck_ldg(d.flags, (const float *)d.mfac32, i * ne + (long long)K, n, 165);
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+    F.Dinv[i] = ck_ldg(d.flags, (const float *)d.mfac32, (NL + i) * ne + (long long)K, n, 165);
+  return F;
 }
 
 // Shared memory of the isoparametric Jacobian columns: 4 N^2 floats a thread.
@@ -260,11 +274,11 @@ __global__ void __launch_bounds__(kElemBlock) k_element_mix(DevState d, MixArgs 
   float fx[9], fy[9];
   if constexpr (GEO == kGeoIso) {
     const auto m = iso_record<DgSpace<NS>::NGP>(d, K, jcols + threadIdx.x, blockDim.x);
-    element_core_general<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K), m, a, fx,
-                                  fy);
+    element_core_general<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K), m,
+                                  mass_record<NS>(d, K), a, fx, fy);
   } else if constexpr (GEO == kGeoQuad) {
     element_core_general<NS, VAR>(pv, S11, S12, S22, load_strength<NS, VAR>(d, a, K),
-                                  map_record(d, K), a, fx, fy);
+                                  map_record(d, K), mass_record<NS>(d, K), a, fx, fy);
   } else {
     float hx, ihx, hy, ihy;
     line_geometry(d, kx, ky, hx, ihx, hy, ihy);
@@ -448,9 +462,10 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
       // Jacobian columns after the tile's own shared memory
       float *jc = (float *)((char *)smem + Tile<TX, TY>::smem) + tid;
       const auto m = iso_record<DgSpace<NS>::NGP>(d, K, jc, TX * TY);
-      element_core_general<NS, VAR>(pv, S11, S12, S22, P, m, ma, fx, fy);
+      element_core_general<NS, VAR>(pv, S11, S12, S22, P, m, mass_record<NS>(d, K), ma, fx, fy);
     } else if constexpr (GEO == kGeoQuad) {
-      element_core_general<NS, VAR>(pv, S11, S12, S22, P, map_record(d, K), ma, fx, fy);
+      element_core_general<NS, VAR>(pv, S11, S12, S22, P, map_record(d, K), mass_record<NS>(d, K),
+                                    ma, fx, fy);
     } else {
       float hx, ihx, hy, ihy;
       line_geometry(d, kx, ky, hx, ihx, hy, ihy);
@@ -526,11 +541,11 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY))
   mix_tile<NS, TX, TY, VAR>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
 }
 
-// General (bilinear) elements: the per-element mass factorisation needs more
-// registers, so 768 threads per SM (80 registers a thread, 68 B spilled for
-// DG2).  Measured (element-subcycles/s, 1024^2 / 256^2 wavy DG2): 512
-// threads 8.14e9 / 4.81e9, 768 threads 8.65e9 / 5.17e9, 1024 threads
-// 7.89e9 / 4.37e9.
+// General (bilinear) elements: the mass solves need more registers, so 768
+// threads per SM (80 registers a thread).  Measured with the stored FP32 mass
+// factors (element-subcycles/s, 1024^2 / 256^2 wavy DG2): 768 threads
+// 9.22e9 / 5.59e9, 1024 threads 9.22e9 / 5.23e9; factorising per element
+// instead: 512 threads 8.14e9 / 4.81e9, 768 threads 8.65e9 / 5.17e9.
 template <int NS, int TX, int TY, bool VAR>
 __global__ void __launch_bounds__(TX *TY, 768 / (TX * TY))
     k_subcycle_mix_gen(DevState d, MixArgs ma, int cur) {
@@ -541,7 +556,7 @@ __global__ void __launch_bounds__(TX *TY, 768 / (TX * TY))
 // Isoparametric elements: as the bilinear kernel, with the Jacobians at the
 // Gauss points in shared memory after the tile's buffers, at 512 threads per
 // SM (128 registers): with 768 or 1024 threads the spills cost more than the
-// occupancy gains (1024^2: 6.00e9 -> 4.89e9 / 4.46e9 element-subcycles/s).
+// occupancy gains (1024^2: 6.07e9 -> 5.35e9 / 4.29e9 element-subcycles/s).
 template <int NS, int TX, int TY, bool VAR>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
     k_subcycle_mix_iso(DevState d, MixArgs ma, int cur) {
@@ -703,6 +718,29 @@ __global__ void k_consts_to_f32(DevState d, double dt, int has_vo) {
 
 inline int blocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
+// FP32 mass-factor records of a general or curved mixed state, once per outer
+// step after the geometry records: the element's own FP32 factorisation
+// (bilinear map record, or the Jacobians of the curved record in a local
+// column), so the tile kernels read what they would have computed.
+template <int NS>
+__global__ void k_mass_records(DevState d) {
+  constexpr int N = DgSpace<NS>::NGP;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= d.ne) return;
+  MassFactor<NS, float> F;
+  if (d.nxy) {
+    float col[4 * N * N];
+    mass_factor<NS>(iso_record<N>(d, (size_t)K, col, 1), F);
+  } else {
+    mass_factor<NS>(map_record(d, (size_t)K), F);
+  }
+  constexpr int NL = NS * (NS - 1) / 2;
+  const long long n = (long long)mass_factor_words<NS>() * d.ne;
+  for (int i = 0; i < NL; ++i) ck_st(d.flags, d.mfac32, (long long)i * d.ne + K, n, 166, F.L[i]);
+  for (int i = 0; i < NS; ++i)
+    ck_st(d.flags, d.mfac32, (long long)(NL + i) * d.ne + K, n, 166, F.Dinv[i]);
+}
+
 }  // namespace
 
 cudaError_t setup_mixed_kernels() {
@@ -791,6 +829,14 @@ cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool h
   if (n < d.nx) n = d.nx;
   if (n < d.ny) n = d.ny;
   k_consts_to_f32<<<blocks(n, 256), 256, 0, st>>>(d, p.dt, has_vo ? 1 : 0);
+  if (d.mfac32) {
+    if (d.ns == 3)
+      k_mass_records<3><<<blocks(d.ne, 128), 128, 0, st>>>(d);
+    else if (d.ns == 6)
+      k_mass_records<6><<<blocks(d.ne, 128), 128, 0, st>>>(d);
+    else
+      k_mass_records<8><<<blocks(d.ne, 128), 128, 0, st>>>(d);
+  }
   return cudaGetLastError();
 }
 
