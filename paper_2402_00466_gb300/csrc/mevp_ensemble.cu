@@ -4,8 +4,9 @@
 // sizes and kinds, one precision, one stream) together.  Per subcycle, the
 // members on rectilinear meshes with 3 or 6 stress dofs and DG0 ice are
 // batched: in the mixed precision one persistent launch covers their
-// (member, tile) work list, in FP64 one persistent element launch their
-// element blocks, and one persistent node launch the nodes of all members.
+// (member, tile) work list, in FP64 one persistent element launch per stress
+// space their element blocks, and one persistent node launch the nodes of
+// all members.
 // The other members (8 stress dofs, DG1/DG2 ice, general or curved meshes)
 // run their single-state launches (FP64: the element launch) within the same
 // stream and graphs: batching every variant into one kernel would make its
@@ -41,6 +42,9 @@ struct mevp_ensemble {
   int nwork = 0, nnwork = 0;
   size_t work_cap = 0, nwork_cap = 0;
   int grid = 0, grid_n = 0;
+  // FP64: the element work is two sublists of d_work, the 3-dof members'
+  // first (n3 items), then the 6-dof members' (grid3 / grid6 blocks)
+  int n3 = 0, grid3 = 0, grid6 = 0;
   std::vector<int> solo;              // members stepped with their own launches
   bool use_graphs = true;
   struct Graph {
@@ -89,20 +93,29 @@ int build_work(mevp_ensemble *e) {
   });
   std::vector<EnsWork> w, nw;
   e->solo.clear();
-  for (int m : order) {
-    const mevp_state *s = e->members[m];
-    if (!batched(s)) {
-      e->solo.push_back(m);
-    } else if (e->prec == MEVP_MIXED) {
+  for (int m : order)
+    if (!batched(e->members[m])) e->solo.push_back(m);
+  if (e->prec == MEVP_MIXED) {
+    for (int m : order) {
+      const mevp_state *s = e->members[m];
+      if (!batched(s)) continue;
       int tx = 0, ty = 0;
       mevp::mixed_tile_count(e->shape, s->d.nx, s->d.ny, &tx, &ty);
       for (int y = 0; y < ty; ++y)
         for (int x = 0; x < tx; ++x) w.push_back({m, x, y});
-    } else {
-      const int B = mevp::kF64Blocks[e->shape];
-      for (int b = 0; b * B < s->d.ne; ++b) w.push_back({m, b, 0});
     }
-    if (e->prec != MEVP_MIXED) {
+  } else {
+    const int B = mevp::kF64Blocks[e->shape];
+    for (int pass = 0; pass < 2; ++pass) {  // 3-dof members, then 6-dof
+      for (int m : order) {
+        const mevp_state *s = e->members[m];
+        if (!batched(s) || (s->ns == 3) != (pass == 0)) continue;
+        for (int b = 0; b * B < s->d.ne; ++b) w.push_back({m, b, 0});
+      }
+      if (pass == 0) e->n3 = (int)w.size();
+    }
+    for (int m : order) {
+      const mevp_state *s = e->members[m];
       const int slots = (s->d.nx + 1) * (s->d.ny + 1);
       for (int b = 0; b * mevp::kNodeSlotBlock < slots; ++b) nw.push_back({m, b, 0});
     }
@@ -135,7 +148,9 @@ int build_work(mevp_ensemble *e) {
     const int per_sm = mevp::mixed_tile_ctas_per_sm(e->shape);
     e->grid = std::max(1, std::min(e->nwork, sms * per_sm));
   } else {
-    e->grid = std::max(1, std::min(e->nwork, sms * mevp::f64_block_ctas_per_sm(e->shape)));
+    const int n6 = e->nwork - e->n3;
+    e->grid3 = std::max(1, std::min(e->n3, sms * mevp::f64_block_ctas_per_sm(e->shape, 3)));
+    e->grid6 = std::max(1, std::min(n6, sms * mevp::f64_block_ctas_per_sm(e->shape, 6)));
     e->grid_n = std::max(1, std::min(e->nnwork, sms * mevp::f64_node_ctas_per_sm()));
   }
   drop_graphs(e);
@@ -189,8 +204,9 @@ int sync_descriptors(mevp_ensemble *e, int *flip) {
 
 // One subcycle of every member.  Mixed: the batched tile launch, then each
 // other member's fused single-state launch.  FP64: each other member's own
-// element launch, the batched element launch, then the node launch over all
-// members.  Member m's current buffer is base_cur(m) ^ flip.
+// element launch, the batched element launches (3-dof, then 6-dof members),
+// then the node launch over all members.  Member m's current buffer is
+// base_cur(m) ^ flip.
 cudaError_t launch_one(mevp_ensemble *e, int flip) {
   cudaError_t err = cudaSuccess;
   if (e->prec == MEVP_MIXED) {
@@ -210,9 +226,15 @@ cudaError_t launch_one(mevp_ensemble *e, int flip) {
     const int cur = e->host_mem[e->solo[i]].base_cur ^ flip;
     err = mevp::launch_element_f64(s->d, s->rheo, cur, e->stream);
   }
+  if (err == cudaSuccess)
+    err = mevp::launch_ensemble_f64(e->d_mem, e->d_work, e->n3, 3, e->shape, e->grid3, flip,
+                                    e->stream);
+  if (err == cudaSuccess)
+    err = mevp::launch_ensemble_f64(e->d_mem, e->d_work + e->n3, e->nwork - e->n3, 6, e->shape,
+                                    e->grid6, flip, e->stream);
   if (err != cudaSuccess) return err;
-  return mevp::launch_ensemble_f64(e->d_mem, e->d_work, e->nwork, e->d_nwork, e->nnwork, e->shape,
-                                   e->grid, e->grid_n, flip, e->stream);
+  return mevp::launch_ensemble_f64_node(e->d_mem, e->d_nwork, e->nnwork, e->grid_n, flip,
+                                        e->stream);
 }
 
 int chunk_graph(mevp_ensemble *e, int flip, int len, cudaGraphExec_t *out) {

@@ -243,19 +243,22 @@ __global__ void __launch_bounds__(kNodeSlotThreads, 1) k_node_f64(DevState d, in
 }
 
 // Ensemble kernels: persistent, grid-stride over (member, block) work items.
-template <int B>
-__global__ void __launch_bounds__(B) k_ens_f64_elem(const EnsMember *__restrict__ mem,
-                                                    const EnsWork *__restrict__ work, int nwork,
-                                                    int flip) {
+// One launch per stress space (the members' work lists are kept per n_S), so
+// that each runs the element arithmetic of one space alone.  The 3-dof
+// kernel fits the single-state budget of 512 resident threads per SM; the
+// 6-dof one keeps the member descriptor's pointers in registers besides, and
+// capped at 128 registers it spilled 272 B a thread, so it is left uncapped.
+template <int B, int NS>
+__global__ void __launch_bounds__(B, NS == 3 ? 512 / B : 1)
+    k_ens_f64_elem(const EnsMember *__restrict__ mem,
+                                                             const EnsWork *__restrict__ work,
+                                                             int nwork, int flip) {
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const EnsWork it = work[w];
     const EnsMember &m = mem[it.member];
     const int K = it.tx * B + threadIdx.x;
     if (K >= m.d.ne) continue;
-    if (m.d.ns == 3)
-      elem_f64<3>(m.d, m.r, m.base_cur ^ flip, K);
-    else
-      elem_f64<6>(m.d, m.r, m.base_cur ^ flip, K);
+    elem_f64<NS>(m.d, m.r, m.base_cur ^ flip, K);
   }
 }
 
@@ -591,32 +594,45 @@ cudaError_t launch_subcycle_f64(const DevState &d, const Rheo &r, bool has_vo, i
 // FP64 ensemble element block sizes the autotuner chooses from.
 const int kF64Blocks[kF64BlockCount] = {64, 128, 256};
 
-cudaError_t launch_ensemble_f64(const EnsMember *mem, const EnsWork *ework, int nework,
-                                const EnsWork *nwork_list, int nnwork, int block, int grid_e,
-                                int grid_n, int flip, cudaStream_t st) {
-  if (nework > 0) switch (block) {
-      case 0:
-        k_ens_f64_elem<64><<<grid_e, 64, 0, st>>>(mem, ework, nework, flip);
-        break;
-      case 1:
-        k_ens_f64_elem<128><<<grid_e, 128, 0, st>>>(mem, ework, nework, flip);
-        break;
-      default:
-        k_ens_f64_elem<256><<<grid_e, 256, 0, st>>>(mem, ework, nework, flip);
-        break;
-    }
+template <int NS>
+void launch_ens_elem(const EnsMember *mem, const EnsWork *ework, int nework, int block,
+                     int grid, int flip, cudaStream_t st) {
+  switch (block) {
+    case 0: k_ens_f64_elem<64, NS><<<grid, 64, 0, st>>>(mem, ework, nework, flip); break;
+    case 1: k_ens_f64_elem<128, NS><<<grid, 128, 0, st>>>(mem, ework, nework, flip); break;
+    default: k_ens_f64_elem<256, NS><<<grid, 256, 0, st>>>(mem, ework, nework, flip); break;
+  }
+}
+
+cudaError_t launch_ensemble_f64(const EnsMember *mem, const EnsWork *ework, int nework, int ns,
+                                int block, int grid, int flip, cudaStream_t st) {
+  if (nework <= 0) return cudaSuccess;
+  if (ns == 3)
+    launch_ens_elem<3>(mem, ework, nework, block, grid, flip, st);
+  else
+    launch_ens_elem<6>(mem, ework, nework, block, grid, flip, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble_f64_node(const EnsMember *mem, const EnsWork *nwork_list, int nnwork,
+                                     int grid_n, int flip, cudaStream_t st) {
   if (nnwork > 0) k_ens_f64_node<<<grid_n, kNodeBlock, 0, st>>>(mem, nwork_list, nnwork, flip);
   return cudaGetLastError();
 }
 
-int f64_block_ctas_per_sm(int block) {
+template <int NS>
+int ens_elem_ctas(int block) {
   int n = 0;
   switch (block) {
-    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<64>, 64, 0); break;
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<128>, 128, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<256>, 256, 0); break;
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<64, NS>, 64, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<128, NS>, 128, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_f64_elem<256, NS>, 256, 0); break;
   }
   return n > 0 ? n : 1;
+}
+
+int f64_block_ctas_per_sm(int block, int ns) {
+  return ns == 3 ? ens_elem_ctas<3>(block) : ens_elem_ctas<6>(block);
 }
 
 int f64_node_ctas_per_sm() {

@@ -186,10 +186,12 @@ cudaError_t launch_force_elem_iso(const DevState &d, cudaStream_t st);
 constexpr int kF64BlockCount = 3;
 extern const int kF64Blocks[kF64BlockCount];
 constexpr int kNodeSlotBlock = 256;
-cudaError_t launch_ensemble_f64(const EnsMember *mem, const EnsWork *ework, int nework,
-                                const EnsWork *nwork_list, int nnwork, int block, int grid_e,
-                                int grid_n, int flip, cudaStream_t st);
-int f64_block_ctas_per_sm(int block);
+// element launch over the work items of the members with n_S = ns
+cudaError_t launch_ensemble_f64(const EnsMember *mem, const EnsWork *ework, int nework, int ns,
+                                int block, int grid, int flip, cudaStream_t st);
+cudaError_t launch_ensemble_f64_node(const EnsMember *mem, const EnsWork *nwork_list, int nnwork,
+                                     int grid_n, int flip, cudaStream_t st);
+int f64_block_ctas_per_sm(int block, int ns);
 int f64_node_ctas_per_sm();
 
 // mixed precision
