@@ -519,8 +519,12 @@ def run_ensemble(a, torch, dist, ws, rank):
                    "l2": "flushed between timed steps (512 MB write)"},
         "roofline": roofline, "sequential_ms_per_step": seq_ms,
         "speedup_vs_sequential": seq_ms / (total_ms / a.steps),
+        # per member begin_step (3 kernels, mixed 5); per subcycle one tile
+        # launch (mixed) or one element launch per stress space present plus
+        # the node launch (FP64)
         "gpu_launches": a.steps * (len(members) * (5 if a.precision == "mixed" else 3) +
-                                   n_sub * (1 if a.precision == "mixed" else 2)),
+                                   n_sub * (1 if a.precision == "mixed" else
+                                            1 + len({c["n_s"] for c in members}))),
         "clocks": clk, "cpu_baseline": None, "e2e": None,
     }
     if rank == 0:
