@@ -305,7 +305,8 @@ MEVP_API int mevp_ensemble_set_graphs(mevp_ensemble *ensemble, int on);
  * layouts above: xline [nx+1] and yline [ny+1] are the strictly increasing
  * vertex coordinates of a rectilinear mesh; H, A [N_e] (DG0); tau [2][N_n];
  * v_ocean [2][N_n] or NULL (ocean at rest); vel [2][N_n] and
- * S [3][n_stress][N_e] are read and overwritten.  params is host memory.
+ * S [3][n_stress][N_e] (n_stress 3, 6 or 8) are read and overwritten.
+ * params is host memory.
  * Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default
  * stream) and the call returns without waiting.
  *

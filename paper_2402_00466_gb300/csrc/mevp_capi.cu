@@ -877,8 +877,8 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
   mevp::NvtxRange nvtx_range_("mevp_run_subcycles_noalloc");
   if (nx < 1 || ny < 1)
     return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: nx=%d ny=%d must be >= 1", nx, ny);
-  if (n_stress != 3 && n_stress != 6)
-    return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: n_stress=%d must be 3 or 6", n_stress);
+  if (n_stress != 3 && n_stress != 6 && n_stress != 8)
+    return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: n_stress=%d must be 3, 6 or 8", n_stress);
   if (n < 0) return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: n=%d < 0", n);
   if (!p) return fail(MEVP_ERR_ARG, "run_subcycles_noalloc: params is NULL");
   const long long nn_ll = (2LL * nx + 1) * (2LL * ny + 1);

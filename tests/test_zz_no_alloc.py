@@ -30,7 +30,7 @@ def _close(x, ref, what):
     assert l2 <= L2_TOL and linf <= INF_TOL, f"{what}: rel L2 {l2:.3e}, rel Linf {linf:.3e}"
 
 
-@pytest.mark.parametrize("n_s", [3, 6])
+@pytest.mark.parametrize("n_s", [3, 6, 8])
 def test_noalloc_matches_state_api_on_two_calls(n_s):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
