@@ -123,6 +123,34 @@ def test_general_mesh_workspace():
         mevp.mevp_mesh_destroy(r)
 
 
+def test_geometry_record_workspace():
+    """The stored geometry records: an FP64 general state holds the L D L^T
+    factor of every M_K (n_s (n_s + 1) / 2 doubles per element) on top of its
+    vertices, a curved one also the Jacobians at the Gauss points (4 NGP^2
+    doubles); the mixed states hold the FP32 factor (n_s (n_s + 1) / 2 floats)
+    beside their FP32 geometry records.  Each region is 256-byte aligned, so
+    the differences are bounded from below by the record sizes."""
+    nx, ny = 40, 30
+    ne, nn, nv = W.sizes(nx, ny)
+    g = mevp.mevp_mesh_create(nx, ny, 0, 0, W.perturbed_vertices(nx, ny, 3))
+    r = mevp.mevp_mesh_create(nx, ny, 1e3, 1e3)
+    c = mevp.mevp_mesh_create_nodes(nx, ny, W.curved_nodes(nx, ny, 5, L=3e3))
+    try:
+        for ns in (3, 6, 8):
+            ngp2 = 4 if ns == 3 else 9
+            w = ns * (ns + 1) // 2
+            rect64 = mevp.mevp_state_workspace_bytes(r, ns, 1, 0)
+            rect32 = mevp.mevp_state_workspace_bytes(r, ns, 1, 1)
+            assert mevp.mevp_state_workspace_bytes(g, ns, 1, 0) >= rect64 + 8 * (2 * nv + w * ne)
+            assert mevp.mevp_state_workspace_bytes(c, ns, 1, 0) >= (
+                rect64 + 8 * (2 * nn + w * ne + 4 * ngp2 * ne))
+            assert mevp.mevp_state_workspace_bytes(g, ns, 1, 1) >= rect32 + 4 * (6 + w) * ne
+            assert mevp.mevp_state_workspace_bytes(c, ns, 1, 1) >= rect32 + 4 * (16 + w) * ne
+    finally:
+        for m in (g, r, c):
+            mevp.mevp_mesh_destroy(m)
+
+
 def test_isoparametric_mesh_validation():
     """mesh_create_nodes: the CG2 node positions of curved elements; an
     element whose map folds (det J <= 0 somewhere) is rejected; the mixed
