@@ -87,7 +87,20 @@ def run_all():
             J, gP, gT = st.adjoint_kinetic_energy(12, 5)
             st.sync()
             out["adj_gP"], out["adj_gT"] = gP, gT
+        for geo, ns in (("curved", 6), ("perturbed", 8)):  # general-mesh adjoint, DG1 ice
+            case = W.small_case(13, 11, ns, seed=335 + ns, geometry=geo)
+            ne = 13 * 11
+            rng = np.random.default_rng(ns)
+            H = np.vstack([rng.uniform(0.6, 1.5, ne)] + [rng.uniform(-0.1, 0.1, ne)] * 2)
+            A = np.vstack([rng.uniform(0.8, 0.95, ne)] + [rng.uniform(-0.02, 0.02, ne)] * 2)
+            with state(case, n_a=3, H=H, A=A) as st:
+                st.begin_step()
+                J, gP, gT = st.adjoint_kinetic_energy(8, 3)
+                st.sync()
+                out[f"adj_{geo}_gP"], out[f"adj_{geo}_gT"] = gP, gT
         members = [W.small_case(n, n + 3, 3 + 3 * (n % 2), seed=340 + n) for n in (9, 14, 20)]
+        members.append(W.small_case(11, 9, 8, seed=345, geometry="curved"))
+        members.append(W.small_case(10, 12, 6, seed=346, geometry="wavy"))
         for prec in ("mixed", "fp64"):
             sts = [state(c, prec) for c in members]
             ens = mevp.Ensemble(sts)
