@@ -419,3 +419,28 @@ def test_mixed_iso_mesh_100_subcycles_from_rest():
     assert np.abs(vo).max() > 1e-3
     assert_close(vg, vo, "velocity", 5e-6, 3e-5)
     assert_close(Sg, So, "stress", 5e-5, 2e-4)
+
+
+@pytest.mark.parametrize("workload", ["mesh1024_dg2_wavy", "mesh1024_dg2_iso"])
+def test_curvilinear_1024_max_size(workload):
+    """The 1024x1024 curvilinear workloads (1M elements, 4.2M nodes) in the
+    benchmark's launch configuration: 2 FP64 subcycles from a moving state at
+    the stability-bound alpha = beta, every output against the oracle, and
+    the mixed path at its stated tolerances."""
+    case = W.make_case(workload)
+    p = dict(case["params"], alpha=8000.0, beta=8000.0)
+    case["vel0"] = W.smooth_velocity(1024, 1024, 5, amp=0.05)
+    vg, Sg = gpu_run(case, 2, params=p)
+    vo, So = oracle_run(case, 2, params=p, openmp=True)
+    assert_close(vg, vo, "velocity")
+    assert_close(Sg, So, "stress")
+    with mevp.State(1024, 1024, 6, vertex_xy=case["xy"], params=p, precision="mixed") as st:
+        st.set_ice(case["H"], case["A"])
+        st.set_forcing(case["tau"])
+        st.set_velocity(case["vel0"])
+        st.set_stress(case["S0"])
+        st.begin_step()
+        st.run_subcycles(2)
+        vm, Sm = st.velocity(), st.stress()
+    assert_close(vm, vo, "velocity (mixed)", 5e-6, 3e-5)
+    assert_close(Sm, So, "stress (mixed)", 5e-5, 2e-4)
