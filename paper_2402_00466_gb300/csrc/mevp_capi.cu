@@ -164,7 +164,7 @@ void drop_graphs(mevp_state *s) {
 cudaError_t launch_one(mevp_state *s, int cur, cudaEvent_t *ev) {
   return s->prec == MEVP_MIXED
              ? mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, cur, s->stream, ev,
-                                           s->fused)
+                                           s->fused, s->maps)
              : mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, cur, s->stream, ev);
 }
 
@@ -453,6 +453,12 @@ int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, int precis
     d.nodec4 = (float4 *)(b + L.nodec32);
     d.vo2 = (float2 *)(b + L.vo2);
     d.lines32 = (float2 *)(b + L.lines32);
+    e = mevp::make_mix_maps(d, &s->maps);
+    if (e != cudaSuccess) {
+      if (s->owns_ws) cudaFree(s->ws);
+      delete s;
+      return cuda_fail(e, "state_create: tensor maps of the mixed kernels");
+    }
   }
   int r2 = MEVP_OK;
   e = cudaMemsetAsync(s->ws, 0, need, s->stream);

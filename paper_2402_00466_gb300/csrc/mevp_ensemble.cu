@@ -217,7 +217,7 @@ cudaError_t launch_one(mevp_ensemble *e, int flip) {
       const mevp_state *s = e->members[e->solo[i]];
       const int cur = e->host_mem[e->solo[i]].base_cur ^ flip;
       err = mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, cur, e->stream,
-                                        nullptr, true);
+                                        nullptr, true, s->maps);
     }
     return err;
   }

@@ -1,6 +1,8 @@
 // mevp_internal.cuh -- internal data structures and kernel launchers.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder is reached through the runtime)
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -205,9 +207,18 @@ int mixed_tile_ctas_per_sm(int tile);
 cudaError_t setup_mixed_kernels();  // once per device, before any capture
 cudaError_t launch_prepare_mixed(const DevState &d, const mevp_params &p, bool has_vo, int cur,
                                  cudaStream_t st);
+// Tensor maps of a mixed state's node records for the fused kernels' TMA
+// staging: both velocity buffers and the node constants, boxes of one tile's
+// owned-node window (rows: the tile height they were built for)
+struct MixMaps {
+  CUtensorMap vel[2];
+  CUtensorMap cons;
+  int rows = 0;
+};
+cudaError_t make_mix_maps(const DevState &d, MixMaps *mm);
 cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
                                   bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
-                                  bool fused);
+                                  bool fused, const MixMaps &mm);
 cudaError_t launch_vel_split(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_vel_join(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_stress_to_f32(const DevState &d, int cur, cudaStream_t st);
@@ -246,6 +257,7 @@ struct mevp_state {
   bool has_pstar = false;  // per-element P* field set (mevp_set_strength_field)
   double *pstar_buf = nullptr;
   bool fused = true;  // mixed precision: one fused launch per subcycle
+  mevp::MixMaps maps;  // mixed precision: tensor maps of the fused kernels' TMA staging
   double *adv1 = nullptr, *adv2 = nullptr;  // advection stage buffers [2][na][ne]
   int nan_every = 0;         // watchdog interval in subcycles (0 = off)
   long long since_check = 0; // subcycles since the last watchdog scan

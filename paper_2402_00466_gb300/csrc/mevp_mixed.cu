@@ -58,6 +58,47 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Tensor-memory-accelerator (TMA) copies of 3-D boxes into shared memory,
+// completed on an mbarrier (transaction count in bytes).
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  // make the initialised barrier visible to the copy engine
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return done != 0;
+}
+// Bounded wait for phase `parity`: false after kMbarTries attempts (each
+// try_wait itself suspends for up to a hardware time limit), so a copy that
+// never completes cannot hang the kernel.
+constexpr int kMbarTries = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  for (int i = 0; i < kMbarTries; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 
 
 // Element step in FP32 from the 9 nodal velocity records (u_hi, u_lo, v_hi,
@@ -416,32 +457,54 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_mix(DevState d, MixArgs ma,
 // the node stage, are copied into shared memory asynchronously from the start.
 template <int TX, int TY> struct Tile {
   static constexpr int NW = 2 * (TX - 1), NH = 2 * (TY - 1);  // owned-node window
-  static constexpr size_t smem = sizeof(float4) * 2 * NW * NH + sizeof(float2) * 9 * TX * TY;
+  // records per window, rounded up to 8 (128 bytes: a TMA destination)
+  static constexpr int NWH = (NW * NH + 7) / 8 * 8;
+  static constexpr size_t smem = sizeof(float4) * 2 * NWH + sizeof(float2) * 9 * TX * TY;
 };
 
-template <int NS, int TX, int TY, bool VAR = false, int GEO = kGeoRect>
+// Staging of the owned nodes' records.  TMA: one thread issues two tensor
+// copies of the (NW x NH) window (velocity records of buffer cur, constant
+// records) at the tile's first owned node; nodes past the domain read as
+// zeros and are not used.  Otherwise (ensemble tiles, whose members each
+// have their own buffers) every thread issues 16-byte cp.async copies.
+struct TileMaps {
+  const CUtensorMap *vel;   // velocity records of the current buffer, box {4, NW, NH}
+  const CUtensorMap *cons;  // node-constant records, same box
+};
+
+template <int NS, int TX, int TY, bool VAR = false, int GEO = kGeoRect, bool TMA = false>
 __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, int cur, int bx,
-                                         int by, float4 *smem) {
-  constexpr int TNW = Tile<TX, TY>::NW, TNH = Tile<TX, TY>::NH;
+                                         int by, float4 *smem, TileMaps maps = {nullptr, nullptr},
+                                         unsigned long long *bar = nullptr) {
+  constexpr int TNW = Tile<TX, TY>::NW, TNH = Tile<TX, TY>::NH, NWH = Tile<TX, TY>::NWH;
   float4 *sv = smem;              // [TNH][TNW] velocity records of the owned nodes
-  float4 *sk = sv + TNW * TNH;    // [TNH][TNW] constant records of the owned nodes
-  float2(*fs)[TY][TX] = (float2(*)[TY][TX])(sk + TNW * TNH);  // [9][TY][TX] forces
+  float4 *sk = sv + NWH;          // [TNH][TNW] constant records of the owned nodes
+  float2(*fs)[TY][TX] = (float2(*)[TY][TX])(sk + NWH);  // [9][TY][TX] forces
   const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * TX + lx;
   const int x0 = bx * (TX - 1), y0 = by * (TY - 1);
   const int ixs = 2 * x0, iys = 2 * y0;
   const float4 *__restrict__ vel = d.vel4[cur];
   // The node stage's inputs do not depend on the element stage: start their
   // copies now, so that they arrive while the elements are computed.
-  for (int i = tid; i < TNW * TNH; i += TX * TY) {
-    const int r = i / TNW, c = i - r * TNW;
-    const int gx = ixs + c, gy = iys + r;
-    if (gx < d.nw && gy < d.nh) {
-      const size_t node = (size_t)gy * d.nw + gx;
-      cp_async16(sv + i, vel + node);
-      cp_async16(sk + i, d.nodec4 + node);
+  if constexpr (TMA) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_expect_tx(bar, 2u * (unsigned)(sizeof(float4) * TNW * TNH));
+      tma_load_3d(sv, maps.vel, 0, ixs, iys, bar);
+      tma_load_3d(sk, maps.cons, 0, ixs, iys, bar);
     }
+  } else {
+    for (int i = tid; i < TNW * TNH; i += TX * TY) {
+      const int r = i / TNW, c = i - r * TNW;
+      const int gx = ixs + c, gy = iys + r;
+      if (gx < d.nw && gy < d.nh) {
+        const size_t node = (size_t)gy * d.nw + gx;
+        cp_async16(sv + i, vel + node);
+        cp_async16(sk + i, d.nodec4 + node);
+      }
+    }
+    cp_async_commit();
   }
-  cp_async_commit();
   const int kx = x0 - 1 + lx, ky = y0 - 1 + ly;
   const bool active = kx >= 0 && ky >= 0 && kx < d.nx && ky < d.ny;
   float2 f[9];
@@ -480,8 +543,18 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
   }
 #pragma unroll
   for (int j = 0; j < 9; ++j) fs[j][ly][lx] = f[j];
-  cp_async_wait_all();
-  __syncthreads();
+  if constexpr (!TMA) cp_async_wait_all();
+  __syncthreads();  // forces written; with TMA also: the barrier is initialised
+  if constexpr (TMA) {
+    if (!mbar_wait(bar, 0)) {
+      // the copies did not complete: report it, give them a last bounded
+      // chance to land (they target this CTA's shared memory), and skip the
+      // node stage; mevp_sync returns MEVP_ERR_TIMEOUT
+      if (tid == 0) atomicExch(d.flags + 2, 1);
+      mbar_wait(bar, 0);
+      return;
+    }
+  }
   const int ixe = (x0 + TX - 1 >= d.nx) ? d.nw : ixs + TNW;
   const int iye = (y0 + TY - 1 >= d.ny) ? d.nh : iys + TNH;
   float4 *__restrict__ vq = d.vel4[cur ^ 1];
@@ -536,9 +609,12 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
 // because 32x8 tiles no longer fill four rounds of CTAs per SM.
 template <int NS, int TX, int TY, bool VAR>
 __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY))
-    k_subcycle_mix(DevState d, MixArgs ma, int cur) {
-  extern __shared__ float4 smem[];
-  mix_tile<NS, TX, TY, VAR>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+    k_subcycle_mix(DevState d, MixArgs ma, int cur, const __grid_constant__ CUtensorMap tmv,
+                   const __grid_constant__ CUtensorMap tmk) {
+  extern __shared__ __align__(128) float4 smem[];
+  __shared__ unsigned long long bar;
+  mix_tile<NS, TX, TY, VAR, kGeoRect, true>(d, ma, cur, blockIdx.x, blockIdx.y, smem,
+                                            TileMaps{&tmv, &tmk}, &bar);
 }
 
 // General (bilinear) elements: the mass solves need more registers, so 768
@@ -548,9 +624,12 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY))
 // instead: 512 threads 8.14e9 / 4.81e9, 768 threads 8.65e9 / 5.17e9.
 template <int NS, int TX, int TY, bool VAR>
 __global__ void __launch_bounds__(TX *TY, 768 / (TX * TY))
-    k_subcycle_mix_gen(DevState d, MixArgs ma, int cur) {
-  extern __shared__ float4 smem[];
-  mix_tile<NS, TX, TY, VAR, kGeoQuad>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+    k_subcycle_mix_gen(DevState d, MixArgs ma, int cur, const __grid_constant__ CUtensorMap tmv,
+                       const __grid_constant__ CUtensorMap tmk) {
+  extern __shared__ __align__(128) float4 smem[];
+  __shared__ unsigned long long bar;
+  mix_tile<NS, TX, TY, VAR, kGeoQuad, true>(d, ma, cur, blockIdx.x, blockIdx.y, smem,
+                                            TileMaps{&tmv, &tmk}, &bar);
 }
 
 // Isoparametric elements: as the bilinear kernel, with the Jacobians at the
@@ -559,30 +638,36 @@ __global__ void __launch_bounds__(TX *TY, 768 / (TX * TY))
 // occupancy gains (1024^2: 6.07e9 -> 5.35e9 / 4.29e9 element-subcycles/s).
 template <int NS, int TX, int TY, bool VAR>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
-    k_subcycle_mix_iso(DevState d, MixArgs ma, int cur) {
-  extern __shared__ float4 smem[];
-  mix_tile<NS, TX, TY, VAR, kGeoIso>(d, ma, cur, blockIdx.x, blockIdx.y, smem);
+    k_subcycle_mix_iso(DevState d, MixArgs ma, int cur, const __grid_constant__ CUtensorMap tmv,
+                       const __grid_constant__ CUtensorMap tmk) {
+  extern __shared__ __align__(128) float4 smem[];
+  __shared__ unsigned long long bar;
+  mix_tile<NS, TX, TY, VAR, kGeoIso, true>(d, ma, cur, blockIdx.x, blockIdx.y, smem,
+                                           TileMaps{&tmv, &tmk}, &bar);
 }
 
 template <int NS, int TX, int TY>
-cudaError_t launch_fused(const DevState &d, const MixArgs &a, int cur, cudaStream_t st) {
+cudaError_t launch_fused(const DevState &d, const MixArgs &a, int cur, const MixMaps &mm,
+                         cudaStream_t st) {
+  if (mm.rows != TY) return cudaErrorInvalidValue;  // maps built for another tile shape
   const dim3 grid((d.nx + TX - 2) / (TX - 1), (d.ny + TY - 2) / (TY - 1));
   const size_t sm = Tile<TX, TY>::smem;
+  const CUtensorMap &tv = mm.vel[cur], &tk = mm.cons;
   if (d.nxy) {
     const size_t smi = sm + iso_cols_bytes<NS>(TX * TY);
     if (d.na > 1)
-      k_subcycle_mix_iso<NS, TX, TY, true><<<grid, dim3(TX, TY), smi, st>>>(d, a, cur);
+      k_subcycle_mix_iso<NS, TX, TY, true><<<grid, dim3(TX, TY), smi, st>>>(d, a, cur, tv, tk);
     else
-      k_subcycle_mix_iso<NS, TX, TY, false><<<grid, dim3(TX, TY), smi, st>>>(d, a, cur);
+      k_subcycle_mix_iso<NS, TX, TY, false><<<grid, dim3(TX, TY), smi, st>>>(d, a, cur, tv, tk);
   } else if (d.xy) {
     if (d.na > 1)
-      k_subcycle_mix_gen<NS, TX, TY, true><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+      k_subcycle_mix_gen<NS, TX, TY, true><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur, tv, tk);
     else
-      k_subcycle_mix_gen<NS, TX, TY, false><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+      k_subcycle_mix_gen<NS, TX, TY, false><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur, tv, tk);
   } else if (d.na > 1) {
-    k_subcycle_mix<NS, TX, TY, true><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+    k_subcycle_mix<NS, TX, TY, true><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur, tv, tk);
   } else {
-    k_subcycle_mix<NS, TX, TY, false><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur);
+    k_subcycle_mix<NS, TX, TY, false><<<grid, dim3(TX, TY), sm, st>>>(d, a, cur, tv, tk);
   }
   return cudaGetLastError();
 }
@@ -874,22 +959,58 @@ void launch_element_mix(const DevState &d, const MixArgs &a, int cur, cudaStream
     var ? launch_element_mix_ns<8, true>(d, a, cur, st) : launch_element_mix_ns<8, false>(d, a, cur, st);
 }
 
+// Rows of the single-state fused tiles: 32x8 tiles once they fill four rounds
+// of CTAs on every SM, else 32x4.
+int mixed_tile_rows(const DevState &d) {
+  const long long big = (long long)((d.nx + 29) / 31) * ((d.ny + 5) / 7);
+  return big < 4LL * 4 * d.nsm ? 4 : 8;
+}
+
+cudaError_t make_mix_maps(const DevState &d, MixMaps *mm) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  // a node record is 4 floats; the window of a tile's owned nodes is
+  // 2 (TX - 1) x 2 (TY - 1) records, TX = 32
+  const int rows = mixed_tile_rows(d);
+  const cuuint64_t dims[3] = {4, (cuuint64_t)d.nw, (cuuint64_t)d.nh};
+  const cuuint64_t strides[2] = {sizeof(float4), sizeof(float4) * (cuuint64_t)d.nw};
+  const cuuint32_t box[3] = {4, 2 * (32 - 1), (cuuint32_t)(2 * (rows - 1))};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void *bases[3] = {d.vel4[0], d.vel4[1], d.nodec4};
+  CUtensorMap *maps[3] = {&mm->vel[0], &mm->vel[1], &mm->cons};
+  for (int i = 0; i < 3; ++i) {
+    const CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, bases[i], dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  mm->rows = rows;
+  return cudaSuccess;
+}
+
 cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
                                   bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
-                                  bool fused) {
+                                  bool fused, const MixMaps &mm) {
   const MixArgs a = make_mixargs(r, p, has_vo);
   if (ev) cudaEventRecord(ev[0], st);
   if (fused) {
-    // 32x8 tiles once they fill four rounds of CTAs on every SM, else 32x4
-    const long long big = (long long)((d.nx + 29) / 31) * ((d.ny + 5) / 7);
-    const bool small = big < 4LL * 4 * d.nsm;
+    const bool small = mixed_tile_rows(d) == 4;
     cudaError_t e;
     if (d.ns == 3)
-      e = small ? launch_fused<3, 32, 4>(d, a, cur, st) : launch_fused<3, 32, 8>(d, a, cur, st);
+      e = small ? launch_fused<3, 32, 4>(d, a, cur, mm, st) : launch_fused<3, 32, 8>(d, a, cur, mm, st);
     else if (d.ns == 6)
-      e = small ? launch_fused<6, 32, 4>(d, a, cur, st) : launch_fused<6, 32, 8>(d, a, cur, st);
+      e = small ? launch_fused<6, 32, 4>(d, a, cur, mm, st) : launch_fused<6, 32, 8>(d, a, cur, mm, st);
     else
-      e = small ? launch_fused<8, 32, 4>(d, a, cur, st) : launch_fused<8, 32, 8>(d, a, cur, st);
+      e = small ? launch_fused<8, 32, 4>(d, a, cur, mm, st) : launch_fused<8, 32, 8>(d, a, cur, mm, st);
     if (ev) cudaEventRecord(ev[1], st);
     if (ev) cudaEventRecord(ev[2], st);
     return e;
