@@ -240,7 +240,13 @@ enum {
   /* k > 0: after every k subcycles a watchdog kernel scans the velocity for
    * NaN/Inf and raises a device flag, which the next mevp_sync reports as
    * MEVP_ERR_NAN (and clears); 0 (default) = off. */
-  MEVP_OPT_NAN_CHECK = 3
+  MEVP_OPT_NAN_CHECK = 3,
+  /* Failure-detection test hook, MEVP_MIXED fused launches only: 1 = the
+   * tiles' shared-memory staging barrier expects 16 bytes more than its
+   * copies deliver, so its bounded wait runs out; the tiles skip their node
+   * stage (the velocity is then not updated) and the next mevp_sync returns
+   * MEVP_ERR_TIMEOUT (and clears the flag).  0 (default) = off. */
+  MEVP_OPT_STALL_TEST = 4
 };
 MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
 

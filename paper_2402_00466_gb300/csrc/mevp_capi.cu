@@ -164,7 +164,7 @@ void drop_graphs(mevp_state *s) {
 cudaError_t launch_one(mevp_state *s, int cur, cudaEvent_t *ev) {
   return s->prec == MEVP_MIXED
              ? mevp::launch_subcycle_mixed(s->d, s->rheo, s->prm, s->has_vo, cur, s->stream, ev,
-                                           s->fused, s->maps)
+                                           s->fused, s->maps, s->stall_test)
              : mevp::launch_subcycle_f64(s->d, s->rheo, s->has_vo, cur, s->stream, ev);
 }
 
@@ -686,6 +686,11 @@ int mevp_set_option(mevp_state *s, int option, int value) {
       s->nan_every = value;
       s->since_check = 0;
       return MEVP_OK;
+    case MEVP_OPT_STALL_TEST:
+      if (value != 0 && value != 1) return fail(MEVP_ERR_ARG, "set_option: STALL_TEST takes 0 or 1");
+      s->stall_test = value;
+      drop_graphs(s);
+      return MEVP_OK;
     case MEVP_OPT_GRAPHS:
       if (value != 0 && value != 1) return fail(MEVP_ERR_ARG, "set_option: GRAPHS takes 0 or 1");
       s->use_graphs = value != 0;
@@ -789,6 +794,15 @@ int mevp_sync(mevp_state *s) {
     }
   }
 #endif
+  {
+    int stalled = 0;
+    MEVP_CUDA(cudaMemcpy(&stalled, s->d.flags + 2, sizeof(int), cudaMemcpyDeviceToHost), "sync");
+    if (stalled) {
+      MEVP_CUDA(cudaMemset(s->d.flags + 2, 0, sizeof(int)), "sync");
+      return fail(MEVP_ERR_TIMEOUT, "sync: a bounded device wait gave up (staging copies of "
+                                    "the fused kernel did not complete)");
+    }
+  }
   if (s->nan_every > 0) {
     int flag = 0;
     MEVP_CUDA(cudaMemcpy(&flag, s->d.flags, sizeof(int), cudaMemcpyDeviceToHost), "sync");

@@ -142,6 +142,7 @@ struct MixArgs {
   float ie, hainv, dmin2, fac;  // stress update
   float opb, fdt;               // 1 + beta, f dt (velocity update)
   int has_vo;
+  int stall;                    // test hook: extra bytes the staging barrier waits for
 };
 
 // Ensemble member as the persistent kernels see it.
@@ -218,7 +219,7 @@ struct MixMaps {
 cudaError_t make_mix_maps(const DevState &d, MixMaps *mm);
 cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
                                   bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
-                                  bool fused, const MixMaps &mm);
+                                  bool fused, const MixMaps &mm, int stall = 0);
 cudaError_t launch_vel_split(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_vel_join(const DevState &d, int cur, cudaStream_t st);
 cudaError_t launch_stress_to_f32(const DevState &d, int cur, cudaStream_t st);
@@ -257,6 +258,7 @@ struct mevp_state {
   bool has_pstar = false;  // per-element P* field set (mevp_set_strength_field)
   double *pstar_buf = nullptr;
   bool fused = true;  // mixed precision: one fused launch per subcycle
+  int stall_test = 0;  // MEVP_OPT_STALL_TEST
   mevp::MixMaps maps;  // mixed precision: tensor maps of the fused kernels' TMA staging
   double *adv1 = nullptr, *adv2 = nullptr;  // advection stage buffers [2][na][ne]
   int nan_every = 0;         // watchdog interval in subcycles (0 = off)

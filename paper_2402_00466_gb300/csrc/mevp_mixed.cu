@@ -89,13 +89,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
       " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
   return done != 0;
 }
-// Bounded wait for phase `parity`: false after kMbarTries attempts (each
-// try_wait itself suspends for up to a hardware time limit), so a copy that
-// never completes cannot hang the kernel.
-constexpr int kMbarTries = 1 << 20;
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-  for (int i = 0; i < kMbarTries; ++i)
+// Bounded wait for phase `parity`: false once `limit_ns` of the global timer
+// have passed (or after 2^22 attempts, whichever comes first), so a copy that
+// never completes cannot hang the kernel.  A staging copy normally lands in
+// microseconds.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < (1 << 22); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
   return false;
 }
 
@@ -489,7 +498,7 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
   if constexpr (TMA) {
     if (tid == 0) {
       mbar_init(bar, 1);
-      mbar_expect_tx(bar, 2u * (unsigned)(sizeof(float4) * TNW * TNH));
+      mbar_expect_tx(bar, 2u * (unsigned)(sizeof(float4) * TNW * TNH) + 16u * ma.stall);
       tma_load_3d(sv, maps.vel, 0, ixs, iys, bar);
       tma_load_3d(sk, maps.cons, 0, ixs, iys, bar);
     }
@@ -546,12 +555,12 @@ __device__ __forceinline__ void mix_tile(const DevState &d, const MixArgs &ma, i
   if constexpr (!TMA) cp_async_wait_all();
   __syncthreads();  // forces written; with TMA also: the barrier is initialised
   if constexpr (TMA) {
-    if (!mbar_wait(bar, 0)) {
-      // the copies did not complete: report it, give them a last bounded
-      // chance to land (they target this CTA's shared memory), and skip the
-      // node stage; mevp_sync returns MEVP_ERR_TIMEOUT
+    if (!mbar_wait(bar, 0, 1000000000ull)) {
+      // the copies did not complete within a second: report it, give them a
+      // last bounded chance to land (they target this CTA's shared memory),
+      // and skip the node stage; mevp_sync returns MEVP_ERR_TIMEOUT
       if (tid == 0) atomicExch(d.flags + 2, 1);
-      mbar_wait(bar, 0);
+      mbar_wait(bar, 0, 100000000ull);
       return;
     }
   }
@@ -934,6 +943,7 @@ MixArgs make_mixargs(const Rheo &r, const mevp_params &p, bool has_vo) {
   a.opb = (float)(1.0 + p.beta);
   a.fdt = (float)(p.coriolis_f * p.dt);
   a.has_vo = has_vo ? 1 : 0;
+  a.stall = 0;
   return a;
 }
 
@@ -999,8 +1009,9 @@ cudaError_t make_mix_maps(const DevState &d, MixMaps *mm) {
 
 cudaError_t launch_subcycle_mixed(const DevState &d, const Rheo &r, const mevp_params &p,
                                   bool has_vo, int cur, cudaStream_t st, cudaEvent_t *ev,
-                                  bool fused, const MixMaps &mm) {
-  const MixArgs a = make_mixargs(r, p, has_vo);
+                                  bool fused, const MixMaps &mm, int stall) {
+  MixArgs a = make_mixargs(r, p, has_vo);
+  a.stall = stall ? 1 : 0;
   if (ev) cudaEventRecord(ev[0], st);
   if (fused) {
     const bool small = mixed_tile_rows(d) == 4;

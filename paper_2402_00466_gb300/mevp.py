@@ -273,6 +273,7 @@ def mevp_run_subcycles_noalloc(nx, ny, n_stress, params, xline, yline, H, A, tau
 MEVP_OPT_FUSED = 1
 MEVP_OPT_GRAPHS = 2
 MEVP_OPT_NAN_CHECK = 3
+MEVP_OPT_STALL_TEST = 4
 
 
 def mevp_set_option(state, option: int, value: int):

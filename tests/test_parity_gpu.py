@@ -372,3 +372,35 @@ def test_nan_watchdog_reports_device_side_corruption(precision):
             st.begin_step()
             st.run_subcycles(40)
             st.sync()
+
+
+def test_bounded_staging_wait_reports_timeout():
+    """Failure detection without a GPU fault: with the stall test hook the
+    fused mixed kernel's staging barrier waits for 16 bytes that never come,
+    its bounded wait gives up (about a second), the tile skips its node stage
+    and sync reports MEVP_ERR_TIMEOUT once; the state stays usable and the
+    next run matches a state that never stalled."""
+    case = W.small_case(9, 5, 6, seed=63)  # one tile: one CTA waits
+    with make_state(case, precision="mixed") as st:
+        st.set_option(mevp.MEVP_OPT_STALL_TEST, 1)
+        st.begin_step()
+        st.run_subcycles(1)
+        with pytest.raises(mevp.MevpError) as e:
+            st.sync()
+        assert e.value.code == -6
+        st.sync()  # the flag was cleared
+        st.set_option(mevp.MEVP_OPT_STALL_TEST, 0)
+        st.set_velocity(case["vel0"])
+        st.set_stress(case["S0"])
+        st.begin_step()
+        st.run_subcycles(3)
+        st.sync()
+        v, S = st.velocity(), st.stress()
+    with make_state(case, precision="mixed") as ref:
+        ref.begin_step()
+        ref.run_subcycles(3)
+        assert np.array_equal(v, ref.velocity()) and np.array_equal(S, ref.stress())
+    with pytest.raises(mevp.MevpError) as e:
+        with make_state(case, precision="mixed") as st:
+            st.set_option(mevp.MEVP_OPT_STALL_TEST, 2)
+    assert e.value.code == -1
