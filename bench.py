@@ -817,8 +817,10 @@ def _run_ours(a, torch, dist, ws, rank):
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            # per step: begin_step (3 kernels; mixed adds 2 conversions) + 2 per subcycle
-            "gpu_launches": a.steps * ((5 if a.precision == "mixed" else 3) + 2 * n_sub),
+            # per step: begin_step (3 kernels; mixed adds 2 conversions) + per
+            # subcycle 2 (FP64: element, node) or 1 (mixed: the fused tile kernel)
+            "gpu_launches": a.steps * ((5 if a.precision == "mixed" else 3) +
+                                       (1 if a.precision == "mixed" else 2) * n_sub),
             "clocks": clk, "wall_s": m["wall"], "variants": variants,
         }
         print(json.dumps(line), flush=True)
