@@ -81,7 +81,7 @@ HBM_BYTES = {("fp64", 6): 608, ("fp64", 3): 464}
 # and valid while that kernel is unchanged.  Summaries: profiles/.
 NCU_TRAFFIC = {
     ("mesh256_dg2", "fp64", "k_element_f64<6>"): 14248448 + 768,
-    ("mesh1024_dg2", "fp64", "k_element_f64<6>"): 234955776 + 248424704,
+    ("mesh1024_dg2", "fp64", "k_element_f64<6>"): 234245632 + 248352768,
     ("mesh1024_dg2", "mixed", "k_subcycle_mix<6,32,8>"): 214122496 + 105039360,
     ("mesh256_dg2_iso", "fp64", "k_element_iso<6>"): 44171776 + 55296000,
 }
