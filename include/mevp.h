@@ -255,12 +255,13 @@ MEVP_API int mevp_set_option(mevp_state *state, int option, int value);
  * domains (sizes, stress dofs, ice degree, mesh kind and parameters may
  * differ per member).  The members are existing states that share one
  * precision, one device and one stream; the ensemble borrows them (they must
- * outlive it) and they remain usable on their own.  Per subcycle, MEVP_MIXED
- * issues one persistent launch over the (member, tile) work list of the
- * members on rectilinear meshes with 3 or 6 stress dofs and DG0 ice; MEVP_FP64
- * issues a persistent element launch over the members on rectilinear meshes
- * and a persistent node launch over all members.  The remaining members run
- * their single-state launches in the same stream (and CUDA graphs).  Results
+ * outlive it) and they remain usable on their own.  The members on
+ * rectilinear meshes with 3 or 6 stress dofs and DG0 ice are batched: per
+ * subcycle, MEVP_MIXED issues one persistent launch over their (member, tile)
+ * work list, MEVP_FP64 one persistent element launch per stress space over
+ * their element blocks and one persistent node launch over all members.  The
+ * remaining members run their single-state launches (FP64: the element
+ * launch) in the same stream (and CUDA graphs).  Results
  * are bitwise those of stepping each member alone.  The ensemble allocates
  * small device tables (cudaMalloc) for its member descriptors and work
  * lists. */
