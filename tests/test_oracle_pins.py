@@ -532,3 +532,21 @@ def test_iso_matches_bruteforce(n_s):
     vb, Sb, _ = bf.subcycles(vel, case["S0"], case["H"], case["A"], case["tau"], case["params"], 3)
     assert rel(vo, vb) < 1e-11
     assert rel(bf.values_documented(So), bf.values(Sb)) < 1e-11
+
+
+@pytest.mark.parametrize("n_s", [3, 6, 8])
+def test_iso_lumped_area_tiles_the_square(n_s):
+    """Curved elements whose boundary nodes stay on the square's sides tile
+    the square: sum_j l_j = L^2 (det J of a Q2 map has degree <= 3 in each
+    reference variable, which both Gauss rules integrate exactly), and,
+    since x is itself the Q2 interpolant of the node positions,
+    sum_j l_j x_j = int x dA = L^3 / 2 wherever the rule integrates
+    x det J (degree <= 5: the 3-point rule of the 6- and 8-dof spaces)."""
+    nx, ny, L = 6, 5, 3e3
+    nodes = curved(nx, ny, 11, L=L)
+    H = np.full((1, nx * ny), 1.0)
+    _, l = oracle.lumped(nx, ny, nodes, n_s, 1, P0, H)
+    assert abs(l.sum() - L * L) <= 1e-12 * L * L
+    if n_s != 3:
+        assert abs(np.dot(l, nodes[:, 0]) - L ** 3 / 2) <= 1e-12 * L ** 3
+        assert abs(np.dot(l, nodes[:, 1]) - L ** 3 / 2) <= 1e-12 * L ** 3
