@@ -184,14 +184,24 @@ def cpu_baseline(case, budget_s=12.0, max_sub=400):
     oracle.subcycles(*args, 3, openmp=True)
     t1 = (time.perf_counter() - t0) / 3
     k = int(max(1, min(max_sub, budget_s / max(t1, 1e-6))))
+    ph = np.zeros(4)
     t0 = time.perf_counter()
-    oracle.subcycles(*args, k, openmp=True)
+    oracle.subcycles(*args, k, openmp=True, phase_sec=ph)
     dt = time.perf_counter() - t0
     ne = case["nx"] * case["ny"]
+    # the four stages of Table 1 (strain, stress, divergence, velocity), per
+    # subcycle: OpenMP on all host cores, and serial on a shorter sample
+    ks = int(max(1, min(20, 4.0 / max(t1 * oracle.max_threads(True), 1e-6))))
+    phs = np.zeros(4)
+    oracle.subcycles(*args, ks, openmp=False, phase_sec=phs)
+    names = ("strain", "stress", "divergence", "velocity")
     return {"value": ne * k / dt, "unit": UNIT, "cores": oracle.max_threads(True),
             "kind": "oracle",
             "sample": f"{k} subcycles of {case['name']} ({ne} elements), FP64 C oracle, OpenMP",
-            "seconds": dt}
+            "seconds": dt,
+            "stage_ms_per_subcycle_openmp": {n: 1e3 * v / k for n, v in zip(names, ph)},
+            "stage_ms_per_subcycle_serial": {n: 1e3 * v / ks for n, v in zip(names, phs)},
+            "serial_sample": f"{ks} subcycles, 1 core"}
 
 
 def run_reference(a):
