@@ -298,6 +298,21 @@ class State:
 
     Host inputs are numpy arrays in the external layouts of include/mevp.h;
     device inputs are CUDA float64 tensors.
+
+    nx, ny: elements per direction; n_stress: 3, 6 or 8 DG stress dofs;
+    vertex_xy: None (uniform mesh of side L), the (nx+1)(ny+1) vertices of a
+    bilinear mesh, or the (2nx+1)(2ny+1) CG2 node positions of a curved
+    (isoparametric) mesh; n_adv: 1, 3 or 6 dofs of H and A; precision:
+    "fp64" or "mixed".
+
+    Methods map one to one onto the C ABI: set_params, set_ice(H, A),
+    set_forcing(tau, v_ocean=None), set_velocity, set_stress,
+    set_strength_field(P*), begin_step() (v^n := v, strength and node
+    constants), run_subcycles(n) and advect(n) (asynchronous), sync()
+    (waits; reports NaN / bounds / timeout flags), read(field) and the
+    velocity() / stress() / strain() / force() shortcuts,
+    adjoint_kinetic_energy(n, checkpoint_every), set_option,
+    timing_enable / timing_read.
     """
 
     def __init__(self, nx, ny, n_stress, *, L=None, vertex_xy=None, n_adv=1,
