@@ -92,7 +92,7 @@ enum {
   MEVP_ERR_STATE = -4,       /* call out of order (e.g. run before set_params) */
   MEVP_ERR_NAN = -5,         /* non-finite value detected                     */
   MEVP_ERR_TIMEOUT = -6,     /* bounded device wait gave up                   */
-  MEVP_ERR_UNSUPPORTED = -7, /* valid input this build does not handle        */
+  MEVP_ERR_UNSUPPORTED = -7, /* valid input the library does not handle       */
   MEVP_ERR_BOUNDS = -8       /* a kernel index left its buffer (only builds
                                 compiled with -DMEVP_CHECKED test for this;
                                 reported by mevp_sync with the access site) */
