@@ -1,6 +1,5 @@
 """C-ABI checks that need no GPU: the library builds and loads, exports every
 symbol include/mevp.h declares, and its host-only calls validate arguments."""
-import ctypes
 import os
 import re
 
