@@ -73,9 +73,9 @@ def _lib(openmp: bool = False):
             lib.orc_dg_basis.argtypes = [i, ctypes.c_double, ctypes.c_double, dp]
             lib.orc_q2_basis.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp, dp]
             lib.orc_subcycles.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp, dp, dp, dp, dp, i,
-                                          dp, dp, dp, dp]
+                                          dp, dp, dp, dp, dp]
             lib.orc_strain.argtypes = [i, i, dp, i, i, dp, dp]
-            lib.orc_stress.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp, dp]
+            lib.orc_stress.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp, dp, dp]
             lib.orc_divergence.argtypes = [i, i, dp, i, i, dp, dp, dp]
             lib.orc_lumped.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp]
             lib.orc_velocity.argtypes = [i, i, pp, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -178,14 +178,25 @@ def strain(nx, ny, xy, n_s, vel):
     return _dg_out(E, n_s, ne)
 
 
-def stress(nx, ny, xy, n_s, n_a, params, E, H, A, S):
+def _pstar_k(Pstar_K, ne):
+    """Optional per-element P* field [N_e] (None: params['Pstar'] everywhere)."""
+    if Pstar_K is None:
+        return None
+    a = _c(Pstar_K).reshape(-1)
+    if a.shape[0] != ne:
+        raise ValueError(f"Pstar_K has {a.shape[0]} entries, the mesh {ne} elements")
+    return a
+
+
+def stress(nx, ny, xy, n_s, n_a, params, E, H, A, S, Pstar_K=None):
     ne, nn = sizes(nx, ny)
     Sc = _dg_in(S, n_s, ne)
     prm = Params.from_dict(params)
     g, mode = _geo(nx, ny, xy)
+    pk = _pstar_k(Pstar_K, ne)
     _check(_lib().orc_stress(nx, ny, _p(g), mode, n_s, n_a, ctypes.byref(prm),
                              _p(_dg_in(E, n_s, ne)), _p(_adv_in(H, n_a, ne)),
-                             _p(_adv_in(A, n_a, ne)), _p(Sc)), "stress")
+                             _p(_adv_in(A, n_a, ne)), _p(Sc), _p(pk)), "stress")
     return _dg_out(Sc, n_s, ne)
 
 
@@ -224,10 +235,11 @@ def velocity(nx, ny, params, F, vprev, vn, tau, vo, m, l):
 
 
 def subcycles(nx, ny, xy, n_s, n_a, params, H, A, tau, vel0, S0, n_sub, vn=None, vo=None,
-              want_last=False, openmp=False, phase_sec=None):
+              want_last=False, openmp=False, phase_sec=None, Pstar_K=None):
     """Run n_sub mEVP subcycles; returns (vel, S) [+ (E_last, F_last, fel_last)].
 
-    vn defaults to vel0 (start of an outer step)."""
+    vn defaults to vel0 (start of an outer step); Pstar_K [N_e] is an optional
+    per-element ice strength parameter in place of params['Pstar']."""
     ne, nn = sizes(nx, ny)
     vel = _c(vel0).reshape(-1).copy()
     vn_ = _c(vel0 if vn is None else vn).reshape(-1).copy()
@@ -238,11 +250,12 @@ def subcycles(nx, ny, xy, n_s, n_a, params, H, A, tau, vel0, S0, n_sub, vn=None,
     fel = np.zeros(18 * ne) if want_last else None
     ph = np.zeros(4)
     g, mode = _geo(nx, ny, xy)
+    pk = _pstar_k(Pstar_K, ne)
     rc = _lib(openmp).orc_subcycles(
         nx, ny, _p(g), mode, n_s, n_a, ctypes.byref(prm), _p(_adv_in(H, n_a, ne)),
         _p(_adv_in(A, n_a, ne)), _p(_c(tau).reshape(-1)),
         None if vo is None else _p(_c(vo).reshape(-1)), _p(vn_), _p(vel), _p(Sc), int(n_sub),
-        _p(E), _p(F), _p(fel), _p(ph))
+        _p(E), _p(F), _p(fel), _p(ph), _p(pk))
     _check(rc, "subcycles")
     if phase_sec is not None:
         phase_sec[:] = ph

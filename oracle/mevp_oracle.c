@@ -374,10 +374,12 @@ static int stage_strain(const mesh_t *M, const double *vel, double *Eout) {
  * per element as in Listing 1 / App. A.  The viscous-plastic stress is
  * written for a general ellipse ratio e (zeta = P/(2 Delta), eta = zeta/e^2);
  * at e = 2 every coefficient equals the paper's 5/4, 3/2, 1, 5/8, 3/8, 1/4
- * exactly.
+ * exactly.  PstarK (optional, [N_e]) replaces the scalar P* of the ice
+ * strength P = P* h exp(-C(1-a)) by a per-element value, the field the
+ * adjoint differentiates against; NULL takes params.Pstar everywhere.
  * ---------------------------------------------------------------------- */
 static int stage_stress(const mesh_t *M, const orc_params *p, const double *Ein,
-                        const double *H, const double *A, double *S) {
+                        const double *H, const double *A, const double *PstarK, double *S) {
   int ne = M->nx * M->ny, n_s = M->n_s, n_a = M->n_a, ng = M->ng;
   double ie2 = 1.0 / (p->e * p->e);
   double k_sq = 1.0 + ie2;          /* 5/4 at e = 2 */
@@ -402,7 +404,9 @@ static int stage_stress(const mesh_t *M, const orc_params *p, const double *Ein,
       }
       double h = fmax(0.0, hg);
       double a = fmin(1.0, fmax(0.0, ag));
-      double P = p->Pstar * h * exp(-p->C * (1.0 - a));
+      /* P* is the element's own value when a per-element field is given */
+      double Pst = PstarK ? PstarK[K] : p->Pstar;
+      double P = Pst * h * exp(-p->C * (1.0 - a));
       double e11 = 0.0, e12 = 0.0, e22 = 0.0;
       for (int s = 0; s < n_s; ++s) {
         e11 += Ein[(0 * (size_t)ne + K) * n_s + s] * M->psi_s[s][g];
@@ -577,11 +581,13 @@ static double now_s(void) {
  *   tau  [2][N_n]        nodal wind stress, vo [2][N_n] or NULL (ocean at rest)
  *   E_last [3][N_e][n_s], F_last [2][N_n], fel_last [N_e][18]: optional
  *   outputs of the last subcycle; phase_sec[4] (optional) accumulates the
- *   time of strain / stress / divergence / velocity.                        */
+ *   time of strain / stress / divergence / velocity.
+ *   Pstar_K [N_e] (optional): per-element ice strength parameter P* in place
+ *   of params.Pstar (NULL = the scalar everywhere).                          */
 int orc_subcycles(int nx, int ny, const double *xy, int geo, int n_s, int n_a, const orc_params *p,
                   const double *H, const double *A, const double *tau, const double *vo,
                   const double *vn, double *vel, double *S, int n_sub, double *E_last,
-                  double *F_last, double *fel_last, double *phase_sec) {
+                  double *F_last, double *fel_last, double *phase_sec, const double *Pstar_K) {
   mesh_t M;
   if (!p || !H || !A || !tau || !vn || !vel || !S || n_sub < 0) return ORC_ERR_ARG;
   int rc = mesh_init(&M, nx, ny, xy, geo, n_s, n_a);
@@ -602,7 +608,7 @@ int orc_subcycles(int nx, int ny, const double *xy, int geo, int n_s, int n_a, c
     double t0 = now_s();
     rc = stage_strain(&M, vel, E);
     double t1 = now_s();
-    if (!rc) rc = stage_stress(&M, p, E, H, A, S);
+    if (!rc) rc = stage_stress(&M, p, E, H, A, Pstar_K, S);
     double t2 = now_s();
     if (!rc) rc = stage_divergence(&M, S, F, last ? fel_last : NULL);
     double t3 = now_s();
@@ -631,11 +637,12 @@ int orc_strain(int nx, int ny, const double *xy, int geo, int n_s, const double 
 }
 
 int orc_stress(int nx, int ny, const double *xy, int geo, int n_s, int n_a, const orc_params *p,
-               const double *E, const double *H, const double *A, double *S) {
+               const double *E, const double *H, const double *A, double *S,
+               const double *Pstar_K) {
   mesh_t M;
   int rc = mesh_init(&M, nx, ny, xy, geo, n_s, n_a);
   if (rc) return rc;
-  return stage_stress(&M, p, E, H, A, S);
+  return stage_stress(&M, p, E, H, A, Pstar_K, S);
 }
 
 int orc_divergence(int nx, int ny, const double *xy, int geo, int n_s, const double *S, double *F,

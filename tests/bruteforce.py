@@ -169,13 +169,21 @@ class Mesh:
         rhs = np.einsum("kq,qs,ckq->cks", r["wdet"], r["psi"], eps)
         return np.einsum("kst,ckt->cks", r["Minv"], rhs)
 
-    def stress(self, Ebf, H, A, Sbf, p):
+    def ice_at(self, F, rule):
+        """Values (ne, nq) at a rule's points of a DG ice field given as
+        documented coefficients (n_a, ne); n_a = 1 is the constant."""
+        F = np.asarray(F, dtype=np.float64)
+        return np.einsum("tk,qt->kq", F, dg_documented(F.shape[0], rule["xi"], rule["eta"]))
+
+    def stress(self, Ebf, H, A, Sbf, p, Pstar_K=None):
         r = self.rule_method
         e = np.einsum("cks,qs->ckq", Ebf, r["psi"])  # (3, ne, nq)
         e11, e12, e22 = e
-        h = np.maximum(0.0, H[0])[:, None]
-        a = np.clip(A[0], 0.0, 1.0)[:, None]
-        P = p["Pstar"] * h * np.exp(-p["C"] * (1.0 - a))
+        # clamps at the Gauss points, after evaluating the (DG) ice fields
+        h = np.maximum(0.0, self.ice_at(H, r))
+        a = np.clip(self.ice_at(A, r), 0.0, 1.0)
+        Ps = p["Pstar"] if Pstar_K is None else np.asarray(Pstar_K, dtype=np.float64)[:, None]
+        P = Ps * h * np.exp(-p["C"] * (1.0 - a))
         # Hibler's viscous-plastic law: zeta = P/(2 Delta), eta = zeta/e^2,
         # sigma = 2 eta eps + (zeta - eta) tr(eps) I - P/2 I
         ecc = p["e"]
@@ -202,13 +210,16 @@ class Mesh:
         np.add.at(F[1], self.nodes, fy)
         return F
 
-    def lumped(self, H, rho):
-        r = self.rule_exact
-        h = np.maximum(0.0, H[0])
+    def lumped(self, H, rho, rule="exact"):
+        """m_j = rho sum_K int_K max(0, H) phi_j, l_j = sum_K int_K phi_j with
+        the 10x10 rule ("exact", exact for positive polynomial H) or the
+        method's own NGP x NGP rule ("method")."""
+        r = self.rule_exact if rule == "exact" else self.rule_method
+        h = np.maximum(0.0, self.ice_at(H, r))  # (ne, nq)
         m = np.zeros(self.nn)
         l = np.zeros(self.nn)
         np.add.at(l, self.nodes, np.einsum("kq,qj->kj", r["wdet"], r["phi"]))
-        np.add.at(m, self.nodes, rho * h[:, None] * np.einsum("kq,qj->kj", r["wdet"], r["phi"]))
+        np.add.at(m, self.nodes, rho * np.einsum("kq,kq,qj->kj", r["wdet"], h, r["phi"]))
         return m, l
 
     def boundary(self):
@@ -216,28 +227,37 @@ class Mesh:
         iy = np.arange(self.nn) // self.nw
         return (ix == 0) | (iy == 0) | (ix == self.nw - 1) | (iy == self.nh - 1)
 
-    def velocity(self, F, vprev, vn, tau, m, l, p):
-        """Complex form: (m(1+beta)/dt + c + i m f) v = (m/dt)(beta v^{p-1} + v^n) + F + l tau."""
+    def velocity(self, F, vprev, vn, tau, m, l, p, vo=None):
+        """Complex form with the ocean velocity z_o (0 when vo is None):
+        (m(1+beta)/dt + c + i m f) v = (m/dt)(beta v^{p-1} + v^n) + F + l tau + c z_o,
+        c = l Cw rho_w |z_o - v^{p-1}|."""
         z = vprev[0] + 1j * vprev[1]
         zn = vn[0] + 1j * vn[1]
-        c = l * p["Cw"] * p["rho_water"] * np.abs(z)
+        zo = 0.0 if vo is None else vo[0] + 1j * vo[1]
+        c = l * p["Cw"] * p["rho_water"] * np.abs(zo - z)
         lhs = m * (1 + p["beta"]) / p["dt"] + c + 1j * m * p["coriolis_f"]
-        rhs = m / p["dt"] * (p["beta"] * z + zn) + (F[0] + 1j * F[1]) + l * (tau[0] + 1j * tau[1])
+        rhs = (m / p["dt"] * (p["beta"] * z + zn) + (F[0] + 1j * F[1]) + l * (tau[0] + 1j * tau[1])
+               + c * zo)
         out = np.where(lhs != 0, rhs / np.where(lhs != 0, lhs, 1), 0)
         out[self.boundary()] = 0
         return np.stack([out.real, out.imag])
 
-    def subcycles(self, vel0, S0_documented, H, A, tau, p, n_sub, vn=None):
+    def subcycles(self, vel0, S0_documented, H, A, tau, p, n_sub, vn=None, vo=None,
+                  Pstar_K=None):
+        """H, A: documented DG coefficients (n_a, ne).  The lumped mass of DG0
+        ice takes the 10x10 rule; of DG1/DG2 ice the method's own rule (the
+        reading that integrates the clamped ice field with the stress rule)."""
         vel = np.array(vel0, dtype=np.float64)
         vn = vel.copy() if vn is None else np.asarray(vn)
         S = self.from_documented(S0_documented)
-        m, l = self.lumped(H, p["rho_ice"])
+        H = np.asarray(H, dtype=np.float64)
+        m, l = self.lumped(H, p["rho_ice"], "exact" if H.shape[0] == 1 else "method")
         E = None
         for _ in range(n_sub):
             E = self.strain(vel)
-            S = self.stress(E, H, A, S, p)
+            S = self.stress(E, H, A, S, p, Pstar_K)
             F = self.divergence(S)
-            vel = self.velocity(F, vel, vn, tau, m, l, p)
+            vel = self.velocity(F, vel, vn, tau, m, l, p, vo)
         return vel, S, E
 
 

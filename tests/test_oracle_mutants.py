@@ -46,6 +46,24 @@ MUTANTS = [
      "J01 += xn[0] * M->q2x[g][j];"),
     ("isoparametric map reads y for x", "J00 += xn[0] * M->q2x[g][j];",
      "J00 += xn[1] * M->q2x[g][j];"),
+    ("ocean drag takes the y current in x", "l[j] * tau[j] + c * ox;", "l[j] * tau[j] + c * oy;"),
+    ("drag relative velocity ignores the ocean",
+     "double dvx = ox - vprev[j], dvy = oy - vprev[nn + j];",
+     "double dvx = -vprev[j], dvy = -vprev[nn + j];"),
+    ("ice height evaluated with the stress basis",
+     "hg += H[(size_t)K * n_a + t] * M->psi_a[t][g];\n        ag",
+     "hg += H[(size_t)K * n_a + t] * M->psi_s[t][g];\n        ag"),
+    ("ice concentration evaluated with the stress basis",
+     "ag += A[(size_t)K * n_a + t] * M->psi_a[t][g];",
+     "ag += A[(size_t)K * n_a + t] * M->psi_s[t][g];"),
+    ("lumped mass from the constant ice coefficient only",
+     "for (int t = 0; t < n_a; ++t) hg += H", "for (int t = 0; t < 1; ++t) hg += H"),
+    ("concentration not clamped above", "double a = fmin(1.0, fmax(0.0, ag));",
+     "double a = fmax(0.0, ag);"),
+    ("per-element P* ignored", "double Pst = PstarK ? PstarK[K] : p->Pstar;",
+     "double Pst = p->Pstar;"),
+    ("P* of the neighbouring element", "PstarK ? PstarK[K] :",
+     "PstarK ? PstarK[(K + 1) % (M->nx * M->ny)] :"),
 ]
 
 

@@ -550,3 +550,232 @@ def test_iso_lumped_area_tiles_the_square(n_s):
     if n_s != 3:
         assert abs(np.dot(l, nodes[:, 0]) - L ** 3 / 2) <= 1e-12 * L ** 3
         assert abs(np.dot(l, nodes[:, 1]) - L ** 3 / 2) <= 1e-12 * L ** 3
+
+
+# --------------------------------------------------------------------------
+# Ocean current (Eq. 2's water drag with v_o != 0, reading 7: c = l Cw rho_w
+# |v_o - v^{p-1}|, drag implicit in v^p and explicit in v_o)
+# --------------------------------------------------------------------------
+def test_free_drift_with_ocean_current_recurrence():
+    """P* = 0 (sigma = 0), uniform H, tau and ocean current z_o: every interior
+    node follows the complex recurrence (divided by l, m/l = rho H)
+      (rho H (1+beta)/dt + c + i rho H f) z^p
+          = (rho H/dt)(beta z^{p-1} + z^n) + tau + c z_o,
+      c = Cw rho_w |z_o - z^{p-1}|,
+    iterated here in scalar complex arithmetic."""
+    p, xy, H, A, tau = _free_drift_case()
+    nx = ny = 4
+    ne, nn, _ = W.sizes(nx, ny)
+    zo = complex(0.23, -0.41)  # distinct components: a swapped x/y shows
+    vo = np.stack([np.full(nn, zo.real), np.full(nn, zo.imag)])
+    z0 = complex(0.05, 0.02)
+    vel0 = np.stack([np.full(nn, z0.real), np.full(nn, z0.imag)])
+    n_sub = 40
+    vel, _ = oracle.subcycles(nx, ny, xy, 3, 1, p, H, A, tau, vel0, np.zeros((3, 3, ne)), n_sub,
+                              vn=np.zeros((2, nn)), vo=vo)
+    rhoH = p["rho_ice"] * 1.3
+    k = p["Cw"] * p["rho_water"]
+    t = complex(0.21, -0.13)
+    z = z0
+    for _ in range(n_sub):
+        c = k * abs(zo - z)
+        z = (rhoH / p["dt"] * p["beta"] * z + t + c * zo) / (
+            rhoH * (1 + p["beta"]) / p["dt"] + c + 1j * rhoH * p["coriolis_f"])
+    nw = 2 * nx + 1
+    grid = vel.reshape(2, nw, nw)[:, 1:-1, 1:-1]
+    assert np.allclose(grid[0], z.real, rtol=1e-13) and np.allclose(grid[1], z.imag, rtol=1e-13)
+    assert np.all(vel.reshape(2, nw, nw)[:, :, 0] == 0)
+
+
+def test_ice_at_rest_in_still_air_is_dragged_to_the_ocean_velocity():
+    """No wind, no Coriolis, P* = 0 and a uniform ocean current: the converged
+    subcycle of an outer step from v^n = z_o is v = z_o exactly (no drag at
+    zero relative velocity, the momentum balance is already satisfied), and
+    from rest the iterates approach z_o monotonically along its direction."""
+    p, xy, H, A, tau = _free_drift_case(f=0.0)
+    nx = ny = 4
+    ne, nn, _ = W.sizes(nx, ny)
+    zo = complex(-0.31, 0.17)
+    vo = np.stack([np.full(nn, zo.real), np.full(nn, zo.imag)])
+    still = np.zeros((2, nn))
+    nw = 2 * nx + 1
+    inner = (slice(None), slice(1, -1), slice(1, -1))
+    # from v = v^n = z_o nothing changes
+    vel, _ = oracle.subcycles(nx, ny, xy, 3, 1, p, H, A, still, vo, np.zeros((3, 3, ne)), 25,
+                              vo=vo)
+    g = vel.reshape(2, nw, nw)[inner]
+    assert np.allclose(g[0], zo.real, rtol=1e-15) and np.allclose(g[1], zo.imag, rtol=1e-15)
+    # from rest (v^n = 0): the direction is that of z_o and |v| grows towards |z_o|
+    last = 0.0
+    vel = still.copy()
+    S = np.zeros((3, 3, ne))
+    for _ in range(5):
+        vel, S = oracle.subcycles(nx, ny, xy, 3, 1, p, H, A, still, vel, S, 1, vn=still, vo=vo)
+        g = vel.reshape(2, nw, nw)[inner]
+        zz = complex(g[0].mean(), g[1].mean())
+        assert abs(zz.imag * zo.real - zz.real * zo.imag) < 1e-15  # parallel to z_o
+        assert last < abs(zz) < abs(zo)
+        last = abs(zz)
+
+
+# --------------------------------------------------------------------------
+# DG1/DG2 ice (n_A = 3 or 6): Listing 1 evaluates H and A at every Gauss
+# point (H.row(i) times the ice basis there) and clamps the values there;
+# the lumped mass integrates the clamped height (reading 8)
+# --------------------------------------------------------------------------
+def dg_ice(ne, n_a, seed):
+    """DG coefficients (n_a, N_e) of H and A: a mean plus slopes/curvatures
+    (H stays positive everywhere; A exceeds 1 at some points, so its clamp acts)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H = np.zeros((n_a, ne)); A = np.zeros((n_a, ne))
+    H[0] = rng.uniform(0.5, 1.8, ne)
+    A[0] = rng.uniform(0.75, 0.97, ne)
+    H[1:] = rng.uniform(-0.3, 0.3, (n_a - 1, ne))
+    A[1:] = rng.uniform(-0.08, 0.08, (n_a - 1, ne))
+    return H, A
+
+
+def _documented_basis(n, xi, eta):
+    """The documented DG basis, written out as scalars."""
+    xh, eh = xi - 0.5, eta - 0.5
+    return [1.0, xh, eh, xh * xh - 1.0 / 12.0, xh * eh, eh * eh - 1.0 / 12.0,
+            (xh * xh - 1.0 / 12.0) * eh, xh * (eh * eh - 1.0 / 12.0)][:n]
+
+
+@pytest.mark.parametrize("n_s,n_a", [(3, 3), (3, 6), (6, 3), (6, 6), (8, 3), (8, 6)])
+def test_stress_with_dg_ice_evaluates_strength_at_each_gauss_point(n_s, n_a):
+    """E = 0 and S = 0: one update gives S_11 = S_22 = -(1/alpha) Proj(P_g / 2) and
+    S_12 = 0.  P_g is computed here point by point in scalar code (h = max(0,
+    sum_t H_t psi_t(x_g)), a = clamp(sum_t A_t psi_t(x_g), 0, 1), P = P* h
+    exp(-C(1-a))) at numpy's Gauss points, and projected with the documented
+    basis, which is orthogonal on rectangles (M_K diagonal, det J cancels)."""
+    nx, ny = 3, 2
+    ne = nx * ny
+    xy = W.uniform_vertices(nx, ny, 3 * 2.5e3, 2 * 1.5e3)  # rectangles, hx != hy
+    H, A = dg_ice(ne, n_a, 40 + n_s + n_a)
+    A[0, ::2] = 0.995  # some Gauss-point values above 1: the clamp of A acts
+    A[1:3, ::2] = 0.08
+    p = dict(P0)
+    out = oracle.stress(nx, ny, xy, n_s, n_a, p, np.zeros((3, n_s, ne)), H, A,
+                        np.zeros((3, n_s, ne)))
+    ngp = {3: 2, 6: 3, 8: 3}[n_s]
+    x, w = np.polynomial.legendre.leggauss(ngp)
+    x, w = 0.5 * (x + 1.0), 0.5 * w
+    clamped = 0
+    for K in range(ne):
+        num = [0.0] * n_s
+        den = [0.0] * n_s
+        for gy in range(ngp):
+            for gx in range(ngp):
+                psi_a = _documented_basis(n_a, x[gx], x[gy])
+                psi_s = _documented_basis(n_s, x[gx], x[gy])
+                hv = sum(H[t, K] * psi_a[t] for t in range(n_a))
+                av = sum(A[t, K] * psi_a[t] for t in range(n_a))
+                clamped += av > 1.0
+                P = p["Pstar"] * max(0.0, hv) * math.exp(-p["C"] * (1.0 - min(1.0, max(0.0, av))))
+                wg = w[gx] * w[gy]
+                for s in range(n_s):
+                    num[s] += wg * psi_s[s] * (-0.5 * P)
+                    den[s] += wg * psi_s[s] * psi_s[s]
+        expect = np.array([num[s] / den[s] for s in range(n_s)]) / p["alpha"]
+        assert np.allclose(out[0, :, K], expect, rtol=1e-12, atol=1e-12 * abs(expect[0]))
+        assert np.allclose(out[2, :, K], expect, rtol=1e-12, atol=1e-12 * abs(expect[0]))
+        assert np.abs(out[1, :, K]).max() == 0.0
+    assert clamped > 0  # the clamp of A was exercised
+
+
+@pytest.mark.parametrize("n_s,n_a,affine", [(3, 3, True), (6, 3, False), (6, 6, False),
+                                            (8, 6, False)])
+def test_lumped_mass_with_dg_ice_matches_bruteforce(n_s, n_a, affine):
+    """m_j = rho sum_K int_K max(0, H) phi_j with DG1/DG2 H (positive, so the
+    clamp is inactive): for these degrees the method's NGP rule is exact (H phi_j
+    det J has degree <= 2 NGP - 1 per variable), so the oracle equals the brute
+    force's 10x10 rule."""
+    nx, ny, L = 3, 2, 6e3
+    xy = W.uniform_vertices(nx, ny, L, L) if affine else perturbed_vertices(nx, ny, L, 5)
+    H, _ = dg_ice(nx * ny, n_a, 60 + n_s + n_a)
+    m, l = oracle.lumped(nx, ny, xy, n_s, n_a, P0, H)
+    mb, lb = BF.Mesh(nx, ny, xy, n_s).lumped(H, P0["rho_ice"], "exact")
+    assert rel(m, mb) < 1e-14 and rel(l, lb) < 1e-14
+
+
+def test_lumped_mass_with_dg2_ice_on_the_dg1_rule():
+    """DG2 ice with 3 stress dofs: the 2x2 rule is not exact for H phi_j, and the
+    reading integrates with the stress space's rule all the same; the brute
+    force with that rule agrees, and the exact integral differs."""
+    nx, ny, L = 3, 2, 6e3
+    xy = W.uniform_vertices(nx, ny, L, L)
+    H, _ = dg_ice(nx * ny, 6, 71)
+    m, _ = oracle.lumped(nx, ny, xy, 3, 6, P0, H)
+    M = BF.Mesh(nx, ny, xy, 3)
+    assert rel(m, M.lumped(H, P0["rho_ice"], "method")[0]) < 1e-14
+    assert rel(m, M.lumped(H, P0["rho_ice"], "exact")[0]) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Per-element P* field (the ice strength parameter as a field, the input the
+# adjoint differentiates against): a plain substitution of P*_K for P* in
+# Listing 1's P = P* h exp(-C(1-A))
+# --------------------------------------------------------------------------
+def test_uniform_strength_field_equals_scalar_bitwise():
+    case = W.small_case(5, 4, 6, seed=12)
+    ne = 20
+    args = (case["nx"], case["ny"], case["xy"], 6, 1, case["params"], case["H"], case["A"],
+            case["tau"], case["vel0"], case["S0"], 7)
+    a = oracle.subcycles(*args)
+    b = oracle.subcycles(*args, Pstar_K=np.full(ne, case["params"]["Pstar"]))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("n_s,n_a", [(3, 1), (6, 3), (8, 6)])
+def test_strength_field_acts_element_by_element(n_s, n_a):
+    """The stress update is element-local: with a P* field, element K's result
+    equals the result of the scalar P* = P*_K, bitwise, for every K."""
+    nx, ny = 4, 3
+    ne = nx * ny
+    xy = perturbed_vertices(nx, ny, 8e3, 9)
+    rng = np.random.Generator(np.random.PCG64(90 + n_s))
+    H, A = dg_ice(ne, n_a, 91) if n_a > 1 else (rng.uniform(0.3, 2, (1, ne)),
+                                                rng.uniform(0.8, 1, (1, ne)))
+    E = rng.uniform(-2e-7, 2e-7, (3, n_s, ne))
+    S = rng.uniform(-5e3, 5e3, (3, n_s, ne))
+    field = P0["Pstar"] * rng.uniform(0.5, 1.5, ne)
+    out = oracle.stress(nx, ny, xy, n_s, n_a, P0, E, H, A, S, Pstar_K=field)
+    for K in range(ne):
+        one = oracle.stress(nx, ny, xy, n_s, n_a, dict(P0, Pstar=field[K]), E, H, A, S)
+        assert np.array_equal(out[:, :, K], one[:, :, K])
+
+
+# --------------------------------------------------------------------------
+# The whole subcycle with DG ice, an ocean current and a P* field against the
+# brute force
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n_s,n_a", [(3, 3), (3, 6), (6, 3), (6, 6)])
+@pytest.mark.parametrize("affine", [True, False])
+def test_whole_subcycle_with_dg_ice_ocean_and_strength_field_matches_bruteforce(n_s, n_a,
+                                                                                 affine):
+    nx, ny = 2, 2
+    case = W.small_case(nx, ny, n_s, seed=23)
+    L = case["L"]
+    ne, nn, _ = W.sizes(nx, ny)
+    xy = case["xy"] if affine else perturbed_vertices(nx, ny, L, 33, amp=0.15)
+    p = case["params"]
+    H, A = dg_ice(ne, n_a, 80 + n_s + n_a)
+    vo = W.smooth_velocity(nx, ny, 81, amp=0.2, L=L)
+    vo[:, 0] += 0.05  # a current at the boundary nodes too (they stay Dirichlet)
+    field = p["Pstar"] * np.random.Generator(np.random.PCG64(82)).uniform(0.5, 1.5, ne)
+    n_sub = 6
+    vel, S, E, F, fel = oracle.subcycles(nx, ny, xy, n_s, n_a, p, H, A, case["tau"],
+                                         case["vel0"], case["S0"], n_sub, vo=vo,
+                                         want_last=True, Pstar_K=field)
+    M = BF.Mesh(nx, ny, xy, n_s)
+    vb, Sb, Eb = M.subcycles(case["vel0"], case["S0"], H, A, case["tau"], p, n_sub, vo=vo,
+                             Pstar_K=field)
+    assert rel(vel, vb) < 1e-12
+    assert rel(M.values_documented(S), M.values(Sb)) < 1e-12
+    assert rel(M.values_documented(E), M.values(Eb)) < 1e-12
+    # the ocean term moved the ice: without it the result differs
+    v0, _ = oracle.subcycles(nx, ny, xy, n_s, n_a, p, H, A, case["tau"], case["vel0"],
+                             case["S0"], n_sub, Pstar_K=field)
+    assert rel(vel, v0) > 1e-3
