@@ -5,14 +5,16 @@
  * Jendersie, Lessig, Richter, "Towards a GPU-Parallelization of the neXtSIM-DG
  * Dynamical Core", PASC'24) with the mEVP pseudo-time iteration (Eq. 3) on one
  * GPU.  One subcycle is the four stages of the paper's Table 1 -- strain,
- * stress, divergence, velocity -- fused into two kernel launches.  The
- * discretisation is the one of Sec. 2.1: CG2 (Q2) velocity on a structured
- * quadrilateral mesh, tensor-valued DG stress (DG1 = 3, DG2 = 6 or the 8-dof
- * space of App. A per component), DG0 ice height H and concentration A.  The
- * stress update per
- * element is the one printed in Listing 1 / App. A (generalised to any
- * ellipse ratio e), with the inverse element map computed on the fly from the
- * mesh vertices (Sec. 3.2, "on-the-fly map").
+ * stress, divergence, velocity -- in two kernel launches in FP64 (element
+ * stages, then the node gather and velocity update) and in one fused launch
+ * per subcycle in the mixed precision.  The discretisation is the one of
+ * Sec. 2.1: CG2 (Q2) velocity on a structured quadrilateral mesh (rectilinear,
+ * general bilinear or curved isoparametric elements), tensor-valued DG stress
+ * (DG1 = 3, DG2 = 6 or the 8-dof space of App. A per component), and DG ice
+ * height H and concentration A with n_adv in {1, 3, 6} dofs (DG0, DG1, DG2).
+ * The stress update per element is the one printed in Listing 1 / App. A
+ * (generalised to any ellipse ratio e), with the element map computed from
+ * the mesh geometry (Sec. 3.2, "on-the-fly map").
  *
  * Conventions shared by every call:
  *   - Every call returns an int status (MEVP_OK or a negative MEVP_ERR_*);
@@ -161,7 +163,11 @@ MEVP_API int mevp_state_create(const mevp_mesh *mesh, int n_stress, int n_adv, i
                       mevp_state **out);
 MEVP_API void mevp_state_destroy(mevp_state *state);
 
-/* Parameters (copied).  Takes effect at the next mevp_begin_step. */
+/* Parameters (copied; see mevp_params for the passages that define each:
+ * Listing 1 / App. A for Pstar, C, e and DeltaMin, Eq. 3 for alpha, Eq. 2
+ * and the mEVP velocity relaxation for beta, dt, the densities, Cw and
+ * coriolis_f).  Every field must be finite and in the range noted there,
+ * else MEVP_ERR_ARG.  Takes effect at the next mevp_begin_step. */
 MEVP_API int mevp_set_params(mevp_state *state, const mevp_params *params);
 
 /* H and A, [n_adv][N_e] FP64 each.  Takes effect at the next mevp_begin_step. */
@@ -178,11 +184,15 @@ MEVP_API int mevp_set_strength_field(mevp_state *state, const double *Pstar, int
 MEVP_API int mevp_set_forcing(mevp_state *state, const double *tau, const double *v_ocean,
                      int on_device);
 
-/* Velocity [2][N_n]; boundary entries are stored as given but every
- * subcycle writes 0 there (Dirichlet).  Does not change v^n. */
+/* Velocity [2][N_n]: the CG2 velocity v of Eq. 2 and the iterate v^{p-1}
+ * of the mEVP iteration (Eq. 3).  Boundary entries are stored as given but
+ * every subcycle writes 0 there (Dirichlet).  Does not change v^n (that is
+ * mevp_begin_step's).  MEVP_ERR_ARG for a non-finite host value. */
 MEVP_API int mevp_set_velocity(mevp_state *state, const double *uv, int on_device);
 
-/* Stress [3][n_stress][N_e]. */
+/* Stress [3][n_stress][N_e]: the DG coefficients of sigma, the iterate
+ * sigma^{p-1} of Eq. 3 (Listing 1's S11, S12, S22).  MEVP_ERR_ARG for a
+ * non-finite host value. */
 MEVP_API int mevp_set_stress(mevp_state *state, const double *S, int on_device);
 
 /* Advect H and A by n_steps >= 0 steps of length params.dt with the
@@ -215,9 +225,14 @@ MEVP_API int mevp_begin_step(mevp_state *state);
 MEVP_API int mevp_run_subcycles(mevp_state *state, int n);
 
 /* Copy a field (enum mevp_field) to dst, FP64, `count` = number of doubles
- * of dst (must be >= the field's size).  The strain and force fields are
- * computed from the current velocity / stress by diagnostic kernels.  With
- * on_device = 0 the call waits for the state's stream. */
+ * of dst (must be >= the field's size).  The fields are the outputs of the
+ * stages of Table 1: velocity (the velocity stage), stress (the stress
+ * update of Listing 1), strain (the strain stage's E, here of the current
+ * velocity) and nodal force (the divergence stage, of the current stress);
+ * the strain and force fields are computed by diagnostic kernels in FP64
+ * (also for MEVP_MIXED states, from their FP32/compensated state).  With
+ * on_device = 0 the call waits for the state's stream.  MEVP_ERR_ARG for an
+ * unknown field, a NULL dst or a short count. */
 MEVP_API int mevp_read_field(mevp_state *state, int field, double *dst, size_t count, int on_device);
 
 /* Wait for all work on the state's stream; reports asynchronous errors. */
@@ -313,25 +328,37 @@ MEVP_API int mevp_ensemble_set_graphs(mevp_ensemble *ensemble, int on);
  * vertex coordinates of a rectilinear mesh; H, A [N_e] (DG0); tau [2][N_n];
  * v_ocean [2][N_n] or NULL (ocean at rest); vel [2][N_n] and
  * S [3][n_stress][N_e] (n_stress 3, 6 or 8) are read and overwritten.
- * params is host memory.
+ * The library cannot see the lengths of these raw pointers: each must hold
+ * at least the stated number of doubles (shorter buffers are read and
+ * written past their end).  params is host memory.
  * Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default
- * stream) and the call returns without waiting.
+ * stream).  The call checks on the device that xline and yline increase
+ * strictly and waits for that check (4 bytes read back; this waits for the
+ * work already queued on cuda_stream, not for the device); it then enqueues
+ * the subcycles and returns without waiting.  MEVP_ERR_ARG when a line does
+ * not increase strictly.
+ *
+ * No NaN watchdog runs here (MEVP_OPT_NAN_CHECK belongs to states).  In a
+ * library compiled with -DMEVP_CHECKED the call also waits at the end and
+ * returns MEVP_ERR_BOUNDS for a kernel access that left its buffer; a normal
+ * build does not test kernel indices.
  *
  * Scratch: a file-scope static device array of MEVP_NOALLOC_SCRATCH_BYTES
  * (8 MiB), which every process that loads the library holds on every device
  * it uses until exit.  A mesh needs 19 N_e + 9 N_n + 2 (nx + ny) doubles
- * (each region 256-byte aligned): meshes up to 128 x 128 elements fit; larger ones return
- * MEVP_ERR_ARG with the sizes in the message.  All calls on a device share
- * that one array and it keeps the last call's contents; every word a call
- * reads is written by the same call first, so nothing has to be cleared.
+ * and 4 status words (each region 256-byte aligned): meshes up to
+ * 128 x 128 elements fit; larger ones return MEVP_ERR_ARG with the sizes in
+ * the message.  All calls on a device share that one array and it keeps the
+ * last call's contents: each call clears the status words first, and every
+ * other word a call reads is written by the same call before.
  * Calls whose work overlaps on the GPU (other streams, other host threads)
  * race on the scratch: serialise them, e.g. on one stream.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current and caches it; make that
  * first call before any stream capture on the device.  Errors: MEVP_ERR_ARG
- * for bad sizes, parameters or non-device pointers; MEVP_ERR_CUDA for a
- * failed lookup or launch. */
+ * for bad sizes, parameters, coordinate lines or non-device pointers;
+ * MEVP_ERR_CUDA for a failed lookup, copy or launch. */
 MEVP_API int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const mevp_params *params,
                                         const double *xline, const double *yline,
                                         const double *H, const double *A, const double *tau,

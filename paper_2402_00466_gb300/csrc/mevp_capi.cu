@@ -838,7 +838,7 @@ void *g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, 
 // Scratch layout for an nx x ny mesh: offsets (bytes, 256-aligned) of the
 // regions and the total.
 struct NoAllocLayout {
-  size_t lines, Pe, nodec, mass, fbuf, vel2, total;
+  size_t flags, lines, Pe, nodec, mass, fbuf, vel2, total;
 };
 
 NoAllocLayout noalloc_layout(size_t nx, size_t ny, size_t ne, size_t nn) {
@@ -849,6 +849,7 @@ NoAllocLayout noalloc_layout(size_t nx, size_t ny, size_t ne, size_t nn) {
     off = align256(off + bytes);
     return o;
   };
+  L.flags = take(sizeof(int) * 4);
   L.lines = take(sizeof(double) * 2 * (nx + ny));
   L.Pe = take(sizeof(double) * ne);
   L.nodec = take(sizeof(double) * 6 * nn);
@@ -874,6 +875,19 @@ int noalloc_scratch(int device, void **out) {
   }
   *out = g_noalloc_ptr[device];
   return MEVP_OK;
+}
+
+// Sets *bad when a coordinate line does not increase strictly (one thread
+// per interval of xline, then of yline).
+__global__ void k_lines_increasing(const double *xline, int nx, const double *yline, int ny,
+                                   int *bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nx) {
+    if (!(xline[i + 1] > xline[i])) atomicOr(bad, 1);
+  } else if (i < nx + ny) {
+    const int j = i - nx;
+    if (!(yline[j + 1] > yline[j])) atomicOr(bad, 1);
+  }
 }
 
 // True when p is device (or managed) memory usable from `device`.
@@ -966,10 +980,26 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
   d.nodec = (double *)(b + L.nodec);
   d.mass = (double *)(b + L.mass);
   d.fbuf = (double *)(b + L.fbuf);
+  d.flags = (int *)(b + L.flags);
   const bool has_vo = v_ocean != nullptr;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  // v^n := vel at entry; every scratch word is written before it is read, so
-  // nothing in the shared array has to be cleared first.
+  // The status words are the only scratch read before this call writes
+  // them: clear them, then check the coordinate lines on the device and wait
+  // for that one word (the only wait of the call).
+  e = cudaMemsetAsync(d.flags, 0, sizeof(int) * 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: clearing the status words");
+  k_lines_increasing<<<(nx + ny + 255) / 256, 256, 0, st>>>(xline, nx, yline, ny, d.flags + 3);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: line check launch");
+  int lines_bad = 0;
+  e = cudaMemcpyAsync(&lines_bad, d.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: line check");
+  if (lines_bad)
+    return fail(MEVP_ERR_ARG,
+                "run_subcycles_noalloc: xline and yline must increase strictly");
+  // v^n := vel at entry; every other scratch word is written before it is
+  // read, so nothing else in the shared array has to be cleared first.
   e = mevp::launch_prepare(d, *p, has_vo, 0, st);
   if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: prepare launch");
   int cur = 0;
@@ -982,5 +1012,16 @@ extern "C" int mevp_run_subcycles_noalloc(int nx, int ny, int n_stress, const me
     e = cudaMemcpyAsync(vel, d.vel[1], sizeof(double) * 2 * nn, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: copy back");
   }
+#ifdef MEVP_CHECKED
+  {  // the bounds-checked build waits and reports a skipped out-of-bounds access
+    int site = 0;
+    e = cudaMemcpyAsync(&site, d.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "run_subcycles_noalloc: status read");
+    if (site)
+      return fail(MEVP_ERR_BOUNDS, "run_subcycles_noalloc: out-of-bounds access at kernel site %d",
+                  site);
+  }
+#endif
   return MEVP_OK;
 }

@@ -255,9 +255,21 @@ def mevp_run_subcycles_noalloc(nx, ny, n_stress, params, xline, yline, H, A, tau
     the library allocating nothing (its scratch is a fixed static device
     array; see include/mevp.h).  vel and S are updated in place."""
     import torch
+    nx, ny, n_stress = int(nx), int(ny), int(n_stress)
+    if nx < 1 or ny < 1:
+        raise ValueError(f"nx={nx}, ny={ny} must be >= 1")
+    ne, nn = nx * ny, (2 * nx + 1) * (2 * ny + 1)
+    # the C entry point sees raw pointers only: every length is checked here,
+    # before anything is launched
+    need = dict(xline=nx + 1, yline=ny + 1, H=ne, A=ne, tau=2 * nn, vel=2 * nn,
+                S=3 * n_stress * ne, v_ocean=2 * nn)
     arrs = dict(xline=xline, yline=yline, H=H, A=A, tau=tau, vel=vel, S=S)
     if v_ocean is not None:
         arrs["v_ocean"] = v_ocean
+    for k, t in arrs.items():
+        if t.numel() != need[k]:
+            raise ValueError(f"{k} has {t.numel()} elements; a {nx}x{ny} mesh with "
+                             f"{n_stress} stress dofs needs {need[k]}")
     for k, t in arrs.items():
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
             raise ValueError(f"{k} must be a contiguous CUDA float64 tensor")
@@ -266,7 +278,7 @@ def mevp_run_subcycles_noalloc(nx, ny, n_stress, params, xline, yline, H, A, tau
         stream = torch.cuda.current_stream().cuda_stream
     ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
     _check(load().mevp_run_subcycles_noalloc(
-        int(nx), int(ny), int(n_stress), ctypes.byref(p), ptr(xline), ptr(yline), ptr(H), ptr(A),
+        nx, ny, n_stress, ctypes.byref(p), ptr(xline), ptr(yline), ptr(H), ptr(A),
         ptr(tau), ptr(v_ocean), ptr(vel), ptr(S), int(n), ctypes.c_void_p(stream)))
 
 

@@ -193,3 +193,23 @@ def test_oracle_is_not_linked_into_the_library():
     src_dir = os.path.join(os.path.dirname(B.LIB), "..", "csrc")
     for f in os.listdir(src_dir):
         assert "oracle" not in open(os.path.join(src_dir, f)).read().lower() or f.endswith(".md")
+
+
+def test_noalloc_binding_checks_every_length_before_launching():
+    """The no-alloc entry point takes raw device pointers, so the binding
+    checks each tensor's length against the mesh first (on the CPU, before
+    any device check or launch)."""
+    import torch
+    from paper_2402_00466_gb300 import mevp
+    from paper_2402_00466_gb300 import workloads as W
+    nx, ny, ns = 4, 3, 6
+    ne, nn, _ = W.sizes(nx, ny)
+    z = lambda *s: torch.zeros(*s, dtype=torch.float64)  # noqa: E731
+    good = dict(xline=z(nx + 1), yline=z(ny + 1), H=z(ne), A=z(ne), tau=z(2, nn), v_ocean=None,
+                vel=z(2, nn), S=z(3, ns, ne))
+    wrong = dict(xline=z(nx), yline=z(ny + 2), H=z(ne - 1), A=z(ne + 1), tau=z(2, nn - 1),
+                 v_ocean=z(nn), vel=z(2 * nn + 1), S=z(3, 3, ne))
+    for k, bad in wrong.items():
+        args = dict(good, **{k: bad})
+        with pytest.raises(ValueError, match=k):
+            mevp.mevp_run_subcycles_noalloc(nx, ny, ns, W.DEFAULT_PARAMS, n=1, **args)
