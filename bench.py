@@ -99,9 +99,37 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 vector peak: 152 SMs x 2 FP64 FMA/clk/SM (measured 1.90 by a throughput
-# probe) x 2 flop x 2.07 GHz max SM clock.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 vector peak: SMs x 2 FP64 FMA/clk/SM (a throughput probe measured 1.90)
+# x 2 flop x the maximum SM clock; the SM count comes from the device and the
+# clock from nvidia-smi's clocks.max.sm (2070 MHz on GB300 when unavailable).
+FP64_FMA_PER_CLK_SM = 2
+FP32_FMA_PER_CLK_SM = 128
+
+
+def sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def max_sm_mhz(clk=None):
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"])
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits", "-i", "0"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        return float(out.splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return 2070.0
+
+
+def fp64_peak_tflops(clk=None):
+    return sm_count() * FP64_FMA_PER_CLK_SM * 2 * max_sm_mhz(clk) * 1e6 / 1e12
+
+
+def fp64_peak_kind(clk=None):
+    return (f"derived: FP64 pipe {sm_count()} SM x {FP64_FMA_PER_CLK_SM} FMA/clk x 2 flop x "
+            f"{max_sm_mhz(clk):.0f} MHz (max SM clock)")
 
 
 class Clocks:
@@ -218,7 +246,7 @@ def run_reference(a):
     t0 = time.perf_counter()
     oracle.subcycles(*args, 1, openmp=True)
     t1 = time.perf_counter() - t0
-    k_sub = int(max(1, min(case["n_sub"], 6.0 / max(t1, 1e-6))))  # ~6 s per step
+    k_sub = int(max(1, min(case["n_sub"], 4.0 / max(t1, 1e-6))))  # ~4 s per step
     for _ in range(a.warmup):
         oracle.subcycles(*args, 1, openmp=True)
     times = []
@@ -296,15 +324,23 @@ def run_reference_advection(a, case):
 # R + W, 16 B constant record R) = 340 B (DG2) / 268 B (DG1).
 MIXED_SINGLE_PASS_BYTES = {6: 424, 3: 352}
 MIXED_OWN_BYTES = {6: 144 + 4 + 4 * 48, 3: 72 + 4 + 4 * 48}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# per-kernel CUDA events on every 10th subcycle of the timed region (events
-# between every pair of launches would add ~2-4 us per subcycle)
-TIMING_STRIDE = 10
+# subcycles of the untimed run that splits the FP64 subcycle time between its
+# element and node kernels (per-kernel CUDA events around every launch)
+SPLIT_SUBCYCLES = 40
 
 
-def measure(mevp, torch, barrier, ws, case, precision, steps, warmup, flush, timing=True):
+def fp32_peak_tflops(clk=None):
+    return sm_count() * FP32_FMA_PER_CLK_SM * 2 * max_sm_mhz(clk) * 1e6 / 1e12
+
+
+def measure(mevp, torch, barrier, ws, case, precision, steps, warmup, flush):
     """Time `steps` outer steps (begin_step + n_sub subcycles) after `warmup`,
-    L2 flushed between steps.  Returns value, step times and kernel timing."""
+    L2 flushed between steps, with three CUDA events per step on the launching
+    stream: before begin_step, between begin_step and the subcycles, after the
+    subcycles (the subcycle loop itself is not interrupted, so its CUDA-graph
+    replay is what is timed).  For the FP64 path an untimed run afterwards
+    brackets every element and node launch with events, for the split of the
+    subcycle time between the two kernels."""
     nx, ny, ns, n_sub = case["nx"], case["ny"], case["n_s"], case["n_sub"]
     ne = nx * ny
     st = mevp.State(nx, ny, ns, vertex_xy=case["xy"], precision=precision,
@@ -313,117 +349,221 @@ def measure(mevp, torch, barrier, ws, case, precision, steps, warmup, flush, tim
     st.set_forcing(case["tau"])
     st.set_velocity(case["vel0"])
     st.set_stress(case["S0"])
-
-    def step():
-        st.begin_step()
-        st.run_subcycles(n_sub)
-
     for _ in range(warmup):
         flush.zero_()
-        step()
+        st.begin_step()
+        st.run_subcycles(n_sub)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    if timing:
-        st.timing_enable(TIMING_STRIDE)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(steps)]
     t0 = time.perf_counter()
     for k in range(steps):
         flush.zero_()  # L2 flush between timed steps, outside the step events
         evs[k][0].record()
-        step()
+        st.begin_step()
         evs[k][1].record()
+        st.run_subcycles(n_sub)
+        evs[k][2].record()
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - t0
-    kt = st.timing_read() if timing else None
-    st.timing_enable(0)
-    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in evs)
-    return dict(state=st, total_ms=total_ms, kt=kt, wall=wall,
-                value=ws * ne * n_sub * steps / (total_ms / 1e3))
+    total_ms = sum(a.elapsed_time(c) for a, _, c in evs)
+    begin_ms = sum(a.elapsed_time(b) for a, b, _ in evs)
+    sub_ms = sum(b.elapsed_time(c) for _, b, c in evs)
+    split = None
+    if precision == "fp64":
+        st.timing_enable(1)
+        st.run_subcycles(SPLIT_SUBCYCLES)
+        kt = st.timing_read()
+        st.timing_enable(0)
+        el_ms, nd_ms = kt["element"][0], kt["node"][0]
+        split = {"element": el_ms / (el_ms + nd_ms), "node": nd_ms / (el_ms + nd_ms),
+                 "subcycles": kt["element"][1],
+                 "how": "per-kernel CUDA events around every launch of an untimed run of "
+                        f"{SPLIT_SUBCYCLES} direct (non-graph) subcycles"}
+    return dict(state=st, total_ms=total_ms, begin_ms=begin_ms, sub_ms=sub_ms, split=split,
+                wall=wall, value=ws * ne * n_sub * steps / (total_ms / 1e3))
 
 
-def roofline_for(precision, case, kt, total_ms, steps):
-    r = _roofline_for(precision, case, kt, total_ms, steps)
+def roofline_for(precision, case, m, steps, clk):
+    """Roofline of the dominant kernel from the timed region: the subcycle
+    time per launch (CUDA events around the uninterrupted subcycle loop) --
+    for the FP64 path its element-kernel share from the split run."""
+    ns, ne, n_sub = case["n_s"], case["nx"] * case["ny"], case["n_sub"]
+    _, nn, _ = W.sizes(case["nx"], case["ny"])
+    sub_s = (m["sub_ms"] / 1e3) / (n_sub * steps)
+    hbm_peak, hbm_kind = load_peaks()
+    geo = case.get("geometry", "uniform")
+    general = geo != "uniform"
+    iso = geo in ("wavy_iso", "curved")
+    if precision == "fp64":
+        table = ISO_ELEM_FLOPS if iso else (GEN_ELEM_FLOPS if general else ELEM_FLOPS)
+        share = m["split"]["element"]
+        el_s = sub_s * share
+        ach = table[ns] * ne / el_s / 1e12
+        peak = fp64_peak_tflops(clk)
+        bytes_sub = HBM_BYTES.get(("fp64", ns), 0) * ne
+        sub_flops = table[ns] * ne + NODE_FLOPS_PER_NODE * nn
+        kern = ((f"k_element_iso<{ns}>" if iso else f"k_element_gen<{ns}>") if general
+                else f"k_element_f64<{ns}>")
+        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "frac": ach / peak, "traffic": None, "kernel": kern,
+             "flops_per_element": table[ns],
+             "kernel_ms_mean": el_s * 1e3,
+             "kernel_time_source": "subcycle time of the timed region x element share "
+                                   f"{share:.4f} of the split run",
+             "peak_kind": fp64_peak_kind(clk),
+             "subcycle_ms_mean": sub_s * 1e3,
+             "subcycle_TFLOPs": sub_flops / sub_s / 1e12,
+             "subcycle_frac": sub_flops / sub_s / 1e12 / peak,
+             "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
+             "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak}
+    else:
+        # one fused launch per subcycle: its mean duration is at most the
+        # subcycle time (the launch gaps of the graph replay included)
+        nsm = sm_count()
+        big = ((case["nx"] + 29) // 31) * ((case["ny"] + 5) // 7) >= 16 * nsm
+        # FP32 map record (A, B, c) per bilinear element, 8 FP32 node offsets
+        # per isoparametric element, and on both the FP32 mass-matrix factor
+        extra = (64 if iso else 24) + 4 * ns * (ns + 1) // 2 if general else 0
+        byts = MIXED_SINGLE_PASS_BYTES[ns] + extra
+        ach = byts * ne / sub_s / 1e9
+        own = (MIXED_OWN_BYTES[ns] + extra) * ne / sub_s / 1e9
+        kern = f"k_subcycle_mix{'_iso' if iso else '_gen' if general else ''}<{ns},32,{8 if big else 4}>"
+        r = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+             "frac": ach / hbm_peak, "traffic": None, "kernel": kern,
+             "kernel_ms_mean": sub_s * 1e3,
+             "kernel_time_source": "subcycle time of the timed region (one launch per subcycle)",
+             "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
+             "bytes_per_element": byts,
+             "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x "
+                             "(v R+W, v^n, tau, m)"
+                             + (" + FP32 geometry and mass-factor records" if general else ""),
+             "own_bytes_per_element": MIXED_OWN_BYTES[ns] + extra,
+             "achieved_own_bytes": own, "frac_own_bytes": own / hbm_peak,
+             "fp32_TFLOPs_approx": (ELEM_FLOPS[ns] * 1.1 + 4 * 40) * ne / sub_s / 1e12,
+             "fp32_peak_TFLOPs": fp32_peak_tflops(clk)}
     r["traffic"] = NCU_TRAFFIC.get((case["name"], precision, r["kernel"]))
     if r["traffic"] is not None:
         r["traffic_note"] = "ncu dram__bytes_read+write per launch, cold cache"
     return r
 
 
-def _roofline_for(precision, case, kt, total_ms, steps):
-    ns, ne, n_sub = case["n_s"], case["nx"] * case["ny"], case["n_sub"]
-    el_ms, el_n = kt["element"]
-    nd_ms, nd_n = kt["node"]
-    el_s = el_ms / max(el_n, 1) / 1e3
-    nd_s = nd_ms / max(nd_n, 1) / 1e3
-    hbm_peak, hbm_kind = load_peaks()
-    sub_s = (total_ms / 1e3) / (n_sub * steps)
-    common = {"element_kernel_ms_mean": el_s * 1e3, "node_kernel_ms_mean": nd_s * 1e3,
-              "element_share_of_subcycle": el_ms / max(el_ms + nd_ms, 1e-12)}
-    if precision == "fp64":
-        geo = case.get("geometry", "uniform")
-        general = geo != "uniform"
-        iso = geo in ("wavy_iso", "curved")
-        table = ISO_ELEM_FLOPS if iso else (GEN_ELEM_FLOPS if general else ELEM_FLOPS)
-        ach = table[ns] * ne / el_s / 1e12
-        bytes_sub = HBM_BYTES.get(("fp64", ns), 0) * ne
-        return dict({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": (f"k_element_iso<{ns}>" if iso else f"k_element_gen<{ns}>")
-                               if general else f"k_element_f64<{ns}>",
-                     "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz",
-                     "hbm_algorithmic_GBps": bytes_sub / sub_s / 1e9,
-                     "hbm_frac": bytes_sub / sub_s / 1e9 / hbm_peak}, **common)
-    # mixed: one fused launch per subcycle, HBM-bound; the library takes
-    # 32x8-element tiles once they fill four rounds of CTAs per SM, else 32x4
-    import torch
-    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    big = ((case["nx"] + 29) // 31) * ((case["ny"] + 5) // 7) >= 16 * nsm
-    geo = case.get("geometry", "uniform")
-    general = geo != "uniform"
-    iso = geo in ("wavy_iso", "curved")
-    # FP32 map record (A, B, c) per bilinear element, 8 FP32 node offsets per
-    # isoparametric element, and on both the FP32 factor of the mass matrix
-    extra = (64 if iso else 24) + 4 * ns * (ns + 1) // 2 if general else 0
-    ach = (MIXED_SINGLE_PASS_BYTES[ns] + extra) * ne / el_s / 1e9
-    own = (MIXED_OWN_BYTES[ns] + extra) * ne / el_s / 1e9
-    return dict({"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                 "frac": ach / hbm_peak, "traffic": None,
-                 "kernel": f"k_subcycle_mix{'_iso' if iso else '_gen' if general else ''}"
-                           f"<{ns},32,{8 if big else 4}>",
-                 "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                 "bytes_per_element": MIXED_SINGLE_PASS_BYTES[ns] + extra,
-                 "bytes_source": "single-pass count: stress R+W, H, A, vertices, 4 nodes x (v R+W, v^n, tau, m)"
-                                 + (" + FP32 geometry and mass-factor records" if general else ""),
-                 "own_bytes_per_element": MIXED_OWN_BYTES[ns] + extra,
-                 "achieved_own_bytes": own, "frac_own_bytes": own / hbm_peak,
-                 "fp32_TFLOPs_approx": (ELEM_FLOPS[ns] * 1.1 + 4 * 40) * ne / el_s / 1e12,
-                 "fp32_peak_TFLOPs": FP32_PEAK_TFLOPS}, **common)
+def end_to_end(mevp, torch, barrier, ws, case, st, steps):
+    """The same metric through the public API with host buffers: every step
+    copies its inputs from pinned host memory (ice, forcing, velocity,
+    stress), runs begin_step + n_sub subcycles, and reads velocity and stress
+    back to pinned host memory."""
+    nx, ny, ns, n_sub = case["nx"], case["ny"], case["n_s"], case["n_sub"]
+    ne, nn, _ = W.sizes(nx, ny)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()  # noqa: E731
+    hH, hA, htau = pin(case["H"]), pin(case["A"]), pin(case["tau"])
+    hv, hS = pin(case["vel0"]), pin(case["S0"])
+    outs = {f: torch.empty(st.field_shape(f), dtype=torch.float64).pin_memory()
+            for f in ("U", "V", "S11", "S12", "S22")}
+    e2e_steps = max(1, min(steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st.set_ice(hH, hA)
+        st.set_forcing(htau)
+        st.set_velocity(hv)
+        st.set_stress(hS)
+        st.begin_step()
+        st.run_subcycles(n_sub)
+        for f, o in outs.items():
+            mevp.mevp_read_field(st.state, f, o)
+    torch.cuda.synchronize()
+    barrier()
+    dt = time.perf_counter() - t0
+    h2d = 8 * (2 * ne + 2 * nn + 2 * nn + 3 * ns * ne)
+    d2h = 8 * (2 * nn + 3 * ns * ne)
+    return {"value": ws * ne * n_sub * e2e_steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}, dt
 
 
-def field_error(mevp, case, n_sub, alpha_beta):
-    """Mixed vs FP64 GPU path (the FP64 path matches the oracle to 1e-11) after
-    n_sub subcycles at a stable alpha = beta; relative L2 / max errors."""
+def _rel(x, ref, mask=None):
+    x, ref = np.asarray(x, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    if mask is not None:
+        x, ref = x[..., mask], ref[..., mask]
+    n2, ninf = np.linalg.norm(ref), np.abs(ref).max() if ref.size else 0.0
+    return {"rel_l2": float(np.linalg.norm(x - ref) / (n2 if n2 > 0 else 1.0)),
+            "rel_max": float(np.abs(x - ref).max() / (ninf if ninf > 0 else 1.0)) if ref.size
+            else 0.0}
+
+
+def field_errors_vs_oracle(mevp, case, n_sub, alpha_beta, precisions=("mixed", "fp64"),
+                          checkpoints=None):
+    """Per-field errors of the GPU paths against the FP64 oracle after n_sub
+    subcycles of one outer step from the workload's initial state: velocity,
+    stress, strain (of the final velocity), nodal force (divergence of the
+    final stress), and Delta at the Gauss points (of the final strain, both
+    evaluated by the oracle), plus the stress error restricted to the rigid
+    elements (Delta < 10 Delta_min at some Gauss point of the last update).
+    checkpoints (increasing subcycle counts ending at n_sub): velocity and
+    stress errors after each, the growth of the discrepancy with p."""
+    import oracle
     p = dict(case["params"], alpha=alpha_beta, beta=alpha_beta)
-    out = {}
-    for prec in ("fp64", "mixed"):
-        with mevp.State(case["nx"], case["ny"], case["n_s"], vertex_xy=case["xy"],
-                        precision=prec, params=p) as st:
+    nx, ny, ns = case["nx"], case["ny"], case["n_s"]
+    cps = list(checkpoints) if checkpoints else [n_sub]
+    assert cps == sorted(cps) and cps[-1] == n_sub
+    t0 = time.perf_counter()
+    vel, S, done, orc = case["vel0"], case["S0"], 0, []
+    for k in cps:
+        out = oracle.subcycles(nx, ny, case["xy"], ns, 1, p, case["H"], case["A"], case["tau"],
+                               vel, S, k - done, vn=case["vel0"], want_last=(k == n_sub),
+                               openmp=True)
+        vel, S, done = out[0], out[1], k
+        orc.append((vel, S))
+    Elast = out[2]
+    t_orc = time.perf_counter() - t0
+    vo, So = orc[-1]
+    Eo = oracle.strain(nx, ny, case["xy"], ns, vo, openmp=True)
+    Fo = oracle.divergence(nx, ny, case["xy"], ns, So, openmp=True)
+    Do = oracle.delta(nx, ny, ns, p, Eo)
+    rigid = oracle.delta(nx, ny, ns, p, Elast).min(axis=1) < 10 * p["DeltaMin"]
+    res = {"n_sub": n_sub, "alpha_beta": alpha_beta, "reference": "FP64 oracle",
+           "oracle_seconds": t_orc, "rigid_elements": int(rigid.sum())}
+    for prec in precisions:
+        with mevp.State(nx, ny, ns, vertex_xy=case["xy"], precision=prec, params=p) as st:
             st.set_ice(case["H"], case["A"])
             st.set_forcing(case["tau"])
             st.set_velocity(case["vel0"])
             st.set_stress(case["S0"])
             st.begin_step()
-            st.run_subcycles(n_sub)
-            out[prec] = (st.velocity(), st.stress())
-    res = {"n_sub": n_sub, "alpha_beta": alpha_beta, "reference": "FP64 GPU path"}
-    for i, f in enumerate(("velocity", "stress")):
-        x, r = out["mixed"][i], out["fp64"][i]
-        res[f + "_rel_l2"] = float(np.linalg.norm(x - r) / np.linalg.norm(r))
-        res[f + "_rel_max"] = float(np.abs(x - r).max() / np.abs(r).max())
+            done, curve = 0, []
+            for k, (vk, Sk) in zip(cps, orc):
+                st.run_subcycles(k - done)
+                done = k
+                curve.append({"p": k, "velocity": _rel(st.velocity(), vk),
+                              "stress": _rel(st.stress(), Sk)})
+            v, S, E, F = st.velocity(), st.stress(), st.strain(), st.force()
+        D = oracle.delta(nx, ny, ns, p, E)
+        res[prec] = {"velocity": _rel(v, vo), "stress": _rel(S, So), "strain": _rel(E, Eo),
+                     "force": _rel(F, Fo), "delta": _rel(D, Do),
+                     "stress_rigid": _rel(S, So, rigid) if rigid.any() else None}
+        if len(cps) > 1:
+            res[prec]["curve"] = curve
     return res
+
+
+def field_error_block(mevp, name):
+    """The per-field error statement of the benchmark line.
+    - "short_horizon": the workload's own mesh at its alpha = beta, with the
+      discrepancy after p = 1, 2, 3, 5, 10 subcycles (on meshes this fine the
+      iteration amplifies any rounding difference exponentially at that
+      alpha, FP64's own included, so the errors are stated at p = 2);
+    - "full_horizon_256": the 256 x 256 DG2 mesh over the full 500 subcycles
+      at the stability-bound alpha = beta = 2000 (alpha h = 4e6 m)."""
+    case = W.make_case(name)
+    out = {"short_horizon": field_errors_vs_oracle(mevp, case, 2, case["params"]["alpha"])}
+    out["short_horizon_curve"] = field_errors_vs_oracle(mevp, case, 10, case["params"]["alpha"],
+                                                        checkpoints=[1, 2, 3, 5, 10])
+    c256 = W.make_case("mesh256_dg2")
+    out["full_horizon_256"] = field_errors_vs_oracle(mevp, c256, c256["n_sub"], 2000.0)
+    return out
 
 
 def run_ours(a):
@@ -510,8 +650,8 @@ def run_ensemble(a, torch, dist, ws, rank):
     else:
         flops = sum(c["nx"] * c["ny"] * ELEM_FLOPS[c["n_s"]] for c in members)
         ach = flops / sub_s / 1e12
-        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+        roofline = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(clk), "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak_tflops(clk), "traffic": None,
                     "kernel": "k_ens_f64_elem<%d> + k_ens_f64_node" % shapes[shape][0],
                     "note": "whole subcycle (element + node launch) timed"}
     for st in states:
@@ -610,10 +750,10 @@ def run_advection(a, torch, dist, ws, rank):
             "config": {"workload": a.workload, "nx": nx, "ny": ny, "n_adv": na,
                        "rk_stages": ADV_STAGES[na],
                        "l2": "flushed between timed steps (512 MB write)"},
-            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(clk),
+                         "unit": "TFLOP/s", "frac": ach / fp64_peak_tflops(clk), "traffic": None,
                          "kernel": f"k_advect<{na}>", "flops_per_element_stage": ADV_FLOPS[na],
-                         "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"},
+                         "peak_kind": fp64_peak_kind(clk)},
             "cpu_baseline": cpu, "e2e": None,
             "gpu_launches": a.steps * ADV_STAGES[na],
             "clocks": clk,
@@ -696,12 +836,12 @@ def run_adjoint(a, torch, dist, ws, rank):
                        "gradients": "dJ/dP* [N_e], dJ/dtau [2][N_n], J = 1/2 sum m |v|^2",
                        "l2": "flushed between timed steps (512 MB write)"},
             "gradients_per_s": a.steps / (total_ms / 1e3),
-            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops(clk),
+                         "unit": "TFLOP/s", "frac": ach / fp64_peak_tflops(clk), "traffic": None,
                          "kernel": "whole gradient (forward sweep, recomputation of all "
                                    "segments but the last, reverse sweep)",
                          "flops_per_element_subcycle": per_es,
-                         "peak_kind": "derived: FP64 pipe 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"},
+                         "peak_kind": fp64_peak_kind(clk)},
             "cpu_baseline": None, "e2e": None,
             # forward sweep 2n, seeds 3, recompute 2(n - last segment), reverse 2n, gradients 1
             "gpu_launches": a.steps * (6 * n_sub - 2 * last + 4),
@@ -710,7 +850,7 @@ def run_adjoint(a, torch, dist, ws, rank):
                 "checkpoint_every": n_sub, "gradients_per_s": a.steps / (store_ms / 1e3),
                 "value": whole_job_throughput(ne * n_sub * a.steps, ws, store_ms / 1e3),
                 "note": "every velocity kept (2 N_n n doubles), no recomputation",
-                "achieved_TFLOPs": ach_store, "frac": ach_store / FP64_PEAK_TFLOPS,
+                "achieved_TFLOPs": ach_store, "frac": ach_store / fp64_peak_tflops(clk),
                 "flops_per_element_subcycle": per_store}},
         }
         print(json.dumps(line), flush=True)
@@ -739,99 +879,67 @@ def _run_ours(a, torch, dist, ws, rank):
     ne, nn, _ = W.sizes(nx, ny)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
 
-    clocks = Clocks(dev)
-    clocks.start()
-    m = measure(mevp, torch, barrier, ws, case, a.precision, a.steps, a.warmup, flush)
-    clk = clocks.stop()
-    st = m["state"]
-    total_ms = m["total_ms"]
-    if ws > 1:
-        total_ms = reduce_max(total_ms, dist, "cuda")
-    value = whole_job_throughput(ne * n_sub * a.steps, ws, total_ms / 1e3)
-    roofline = roofline_for(a.precision, case, m["kt"], m["total_ms"], a.steps)
-
-    # end to end through the public API with pinned host buffers
-    e2e = None
-    if not a.no_e2e:
-        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()  # noqa: E731
-        hH, hA, htau = pin(case["H"]), pin(case["A"]), pin(case["tau"])
-        hv, hS = pin(case["vel0"]), pin(case["S0"])
-        outs = {f: torch.empty(st.field_shape(f), dtype=torch.float64).pin_memory()
-                for f in ("U", "V", "S11", "S12", "S22")}
-        e2e_steps = max(1, min(a.steps, 3))
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            st.set_ice(hH, hA)
-            st.set_forcing(htau)
-            st.set_velocity(hv)
-            st.set_stress(hS)
-            st.begin_step()
-            st.run_subcycles(n_sub)
-            for f, o in outs.items():
-                mevp.mevp_read_field(st.state, f, o)
-        torch.cuda.synchronize()
-        barrier()
-        dt = time.perf_counter() - t0
+    # the headline arm (a.precision) and, unless --no-variants, the other
+    # precision, timed the same way on the same workload
+    arms = [a.precision] + ([] if a.no_variants else
+                            ["mixed" if a.precision == "fp64" else "fp64"])
+    res = {}
+    for prec in arms:
+        clocks = Clocks(dev)
+        clocks.start()
+        m = measure(mevp, torch, barrier, ws, case, prec, a.steps, a.warmup, flush)
+        clk = clocks.stop()
+        st = m["state"]
+        total_ms = m["total_ms"]
         if ws > 1:
-            dt = reduce_max(dt, dist, "cuda")
-        h2d = 8 * (2 * ne + 2 * nn + 2 * nn + 3 * ns * ne)
-        d2h = 8 * (2 * nn + 3 * ns * ne)
-        e2e = {"value": ws * ne * n_sub * e2e_steps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
-    st.close()
+            total_ms = reduce_max(total_ms, dist, "cuda")
+        r = {"value": whole_job_throughput(ne * n_sub * a.steps, ws, total_ms / 1e3),
+             "ms_per_step": total_ms / a.steps,
+             "begin_step_ms_per_step": m["begin_ms"] / a.steps,
+             "subcycles_ms_per_step": m["sub_ms"] / a.steps,
+             "roofline": roofline_for(prec, case, m, a.steps, clk),
+             "kernel_split": m["split"],
+             # per step: begin_step (3 kernels; mixed adds 2 conversions) +
+             # per subcycle 2 (FP64: element, node) or 1 (mixed: the fused tile)
+             "gpu_launches": a.steps * ((5 if prec == "mixed" else 3) +
+                                        (1 if prec == "mixed" else 2) * n_sub),
+             "dtype": "f64" if prec == "fp64" else "f32",
+             "clocks": clk, "wall_s": m["wall"], "e2e": None}
+        if not a.no_e2e:
+            e2e, dt = end_to_end(mevp, torch, barrier, ws, case, st, a.steps)
+            if ws > 1:
+                e2e["value"] = ws * ne * n_sub * e2e["steps"] / reduce_max(dt, dist, "cuda")
+            r["e2e"] = e2e
+        st.close()
+        res[prec] = r
 
-    variants = None
-    general = case.get("geometry", "uniform") != "uniform"
-    if not a.no_variants and ws == 1:
-        variants = {}
-        other = "mixed" if a.precision == "fp64" else "fp64"
-        mv = measure(mevp, torch, barrier, 1, case, other, a.steps, a.warmup, flush)
-        mv["state"].close()
-        variants[other] = {"workload": a.workload, "value": mv["value"],
-                           "ms_per_step": mv["total_ms"] / a.steps,
-                           "roofline": roofline_for(other, case, mv["kt"], mv["total_ms"],
-                                                    a.steps)}
-        stable_ab = max(300.0, 4e6 / (case["L"] / nx))  # stable when alpha*h >~ 4e6 m
-        variants["mixed_field_error"] = field_error(mevp, case, n_sub, stable_ab)
-        big_name = {"mesh256_dg2_wavy": "mesh1024_dg2_wavy",
-                    "mesh256_dg2_iso": "mesh1024_dg2_iso"}.get(
-                        a.workload, None if general else "mesh1024_dg2")
-        if big_name and a.workload != big_name:
-            big = W.make_case(big_name)
-            for prec in ("fp64", "mixed"):
-                mb = measure(mevp, torch, barrier, 1, big, prec, 2 if prec == "fp64" else 5, 3,
-                             flush)
-                mb["state"].close()
-                nsteps = 2 if prec == "fp64" else 5
-                variants[f"{prec}_{big_name}"] = {
-                    "workload": big_name, "value": mb["value"],
-                    "ms_per_step": mb["total_ms"] / nsteps,
-                    "roofline": roofline_for(prec, big, mb["kt"], mb["total_ms"], nsteps)}
-
+    head = res[a.precision]
     cpu = None
+    field_errors = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(case)
+        # the oracle leg: per-field errors of both paths against the oracle
+        field_errors = field_error_block(mevp, a.workload)
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if a.precision == "fp64" else "f32",
-            "data": "synthetic",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": head["dtype"], "data": "synthetic",
             "config": {"workload": a.workload, "nx": nx, "ny": ny, "n_stress": ns,
                        "n_sub": n_sub, "precision": a.precision,
                        "alpha": case["params"]["alpha"], "beta": case["params"]["beta"],
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            # per step: begin_step (3 kernels; mixed adds 2 conversions) + per
-            # subcycle 2 (FP64: element, node) or 1 (mixed: the fused tile kernel)
-            "gpu_launches": a.steps * ((5 if a.precision == "mixed" else 3) +
-                                       (1 if a.precision == "mixed" else 2) * n_sub),
-            "clocks": clk, "wall_s": m["wall"], "variants": variants,
+            "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+            "wall_s": head["wall_s"],
+            "begin_step_ms_per_step": head["begin_step_ms_per_step"],
+            "subcycles_ms_per_step": head["subcycles_ms_per_step"],
+            "kernel_split": head["kernel_split"],
+            "arms": {p: r for p, r in res.items() if p != a.precision},
+            "field_errors": field_errors,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -845,13 +953,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="mesh256_dg2",
+    ap.add_argument("--workload", default="mesh1024_dg2",
                     choices=sorted(W.CONFIGS) + sorted(W.ENSEMBLES))
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the other precision and the 1024^2 measurements")
+                    help="time only --precision, not the other precision's arm")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ours":
         ap.error("--warmup must be >= 3")

@@ -77,6 +77,7 @@ def _lib(openmp: bool = False):
             lib.orc_strain.argtypes = [i, i, dp, i, i, dp, dp]
             lib.orc_stress.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp, dp, dp]
             lib.orc_divergence.argtypes = [i, i, dp, i, i, dp, dp, dp]
+            lib.orc_delta.argtypes = [i, i, i, pp, dp, dp]
             lib.orc_lumped.argtypes = [i, i, dp, i, i, i, pp, dp, dp, dp]
             lib.orc_velocity.argtypes = [i, i, pp, dp, dp, dp, dp, dp, dp, dp, dp]
             lib.orc_element_map.argtypes = [i, i, dp, i, i, i, dp, dp]
@@ -170,11 +171,12 @@ def element_map(nx, ny, xy, n_s, K):
     return det, m.reshape(n_s, ng)
 
 
-def strain(nx, ny, xy, n_s, vel):
+def strain(nx, ny, xy, n_s, vel, openmp=False):
     ne, nn = sizes(nx, ny)
     E = np.zeros(3 * ne * n_s)
     g, mode = _geo(nx, ny, xy)
-    _check(_lib().orc_strain(nx, ny, _p(g), mode, n_s, _p(_c(vel).reshape(-1)), _p(E)), "strain")
+    _check(_lib(openmp).orc_strain(nx, ny, _p(g), mode, n_s, _p(_c(vel).reshape(-1)), _p(E)),
+           "strain")
     return _dg_out(E, n_s, ne)
 
 
@@ -200,13 +202,25 @@ def stress(nx, ny, xy, n_s, n_a, params, E, H, A, S, Pstar_K=None):
     return _dg_out(Sc, n_s, ne)
 
 
-def divergence(nx, ny, xy, n_s, S, return_element_forces=False):
+def delta(nx, ny, n_s, params, E):
+    """Delta of the rheology at every Gauss point, (N_e, n_g), of the strain
+    E (3, n_s, N_e)."""
+    ne, nn = sizes(nx, ny)
+    ng = ngp(n_s) ** 2
+    out = np.zeros(ne * ng)
+    prm = Params.from_dict(params)
+    _check(_lib().orc_delta(nx, ny, n_s, ctypes.byref(prm), _p(_dg_in(E, n_s, ne)), _p(out)),
+           "delta")
+    return out.reshape(ne, ng)
+
+
+def divergence(nx, ny, xy, n_s, S, return_element_forces=False, openmp=False):
     ne, nn = sizes(nx, ny)
     F = np.zeros(2 * nn)
     fel = np.zeros(18 * ne)
     g, mode = _geo(nx, ny, xy)
-    _check(_lib().orc_divergence(nx, ny, _p(g), mode, n_s, _p(_dg_in(S, n_s, ne)), _p(F), _p(fel)),
-           "divergence")
+    _check(_lib(openmp).orc_divergence(nx, ny, _p(g), mode, n_s, _p(_dg_in(S, n_s, ne)), _p(F),
+                                       _p(fel)), "divergence")
     if return_element_forces:
         return F.reshape(2, nn), fel.reshape(ne, 18)
     return F.reshape(2, nn)

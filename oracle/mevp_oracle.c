@@ -378,13 +378,21 @@ static int stage_strain(const mesh_t *M, const double *vel, double *Eout) {
  * strength P = P* h exp(-C(1-a)) by a per-element value, the field the
  * adjoint differentiates against; NULL takes params.Pstar everywhere.
  * ---------------------------------------------------------------------- */
-static int stage_stress(const mesh_t *M, const orc_params *p, const double *Ein,
-                        const double *H, const double *A, const double *PstarK, double *S) {
-  int ne = M->nx * M->ny, n_s = M->n_s, n_a = M->n_a, ng = M->ng;
+/* Delta = sqrt(Delta_min^2 + (1+e^-2)(e11^2+e22^2) + 2(1-e^-2) e11 e22
+ *              + 4 e^-2 e12^2): 5/4, 3/2 and 1 at e = 2 (Listing 1). */
+static double delta_of(const orc_params *p, double e11, double e12, double e22) {
   double ie2 = 1.0 / (p->e * p->e);
   double k_sq = 1.0 + ie2;          /* 5/4 at e = 2 */
   double k_mix = 2.0 * (1.0 - ie2); /* 3/2 */
   double k_sh = 4.0 * ie2;          /* 1   */
+  return sqrt(p->DeltaMin * p->DeltaMin + k_sq * (e11 * e11 + e22 * e22) +
+              k_mix * e11 * e22 + k_sh * e12 * e12);
+}
+
+static int stage_stress(const mesh_t *M, const orc_params *p, const double *Ein,
+                        const double *H, const double *A, const double *PstarK, double *S) {
+  int ne = M->nx * M->ny, n_s = M->n_s, n_a = M->n_a, ng = M->ng;
+  double ie2 = 1.0 / (p->e * p->e);
   double c_a = 0.5 * (1.0 + ie2);   /* 5/8 */
   double c_b = 0.5 * (1.0 - ie2);   /* 3/8 */
   double c_s = ie2;                 /* 1/4 */
@@ -413,8 +421,7 @@ static int stage_stress(const mesh_t *M, const orc_params *p, const double *Ein,
         e12 += Ein[(1 * (size_t)ne + K) * n_s + s] * M->psi_s[s][g];
         e22 += Ein[(2 * (size_t)ne + K) * n_s + s] * M->psi_s[s][g];
       }
-      double delta = sqrt(p->DeltaMin * p->DeltaMin + k_sq * (e11 * e11 + e22 * e22) +
-                          k_mix * e11 * e22 + k_sh * e12 * e12);
+      double delta = delta_of(p, e11, e12, e22);
       double PD = P / delta;
       s11[g] = alphaInv * (PD * (c_a * e11 + c_b * e22) - 0.5 * P);
       s12[g] = alphaInv * (PD * c_s * e12);
@@ -643,6 +650,28 @@ int orc_stress(int nx, int ny, const double *xy, int geo, int n_s, int n_a, cons
   int rc = mesh_init(&M, nx, ny, xy, geo, n_s, n_a);
   if (rc) return rc;
   return stage_stress(&M, p, E, H, A, Pstar_K, S);
+}
+
+/* Delta at every Gauss point, [N_e][n_g], of the strain E [3][N_e][n_s]
+ * (the rheology's Delta, Listing 1, for reports of where the ice is rigid). */
+int orc_delta(int nx, int ny, int n_s, const orc_params *p, const double *E, double *delta) {
+  mesh_t M;
+  double dummy[2] = {0.0, 0.0};
+  if (!p || !E || !delta) return ORC_ERR_ARG;
+  int rc = mesh_init(&M, nx, ny, dummy, 0, n_s, 1);
+  if (rc) return rc;
+  int ne = nx * ny, ng = M.ng;
+  for (int K = 0; K < ne; ++K)
+    for (int g = 0; g < ng; ++g) {
+      double e11 = 0.0, e12 = 0.0, e22 = 0.0;
+      for (int s = 0; s < n_s; ++s) {
+        e11 += E[(0 * (size_t)ne + K) * n_s + s] * M.psi_s[s][g];
+        e12 += E[(1 * (size_t)ne + K) * n_s + s] * M.psi_s[s][g];
+        e22 += E[(2 * (size_t)ne + K) * n_s + s] * M.psi_s[s][g];
+      }
+      delta[(size_t)K * ng + g] = delta_of(p, e11, e12, e22);
+    }
+  return ORC_OK;
 }
 
 int orc_divergence(int nx, int ny, const double *xy, int geo, int n_s, const double *S, double *F,

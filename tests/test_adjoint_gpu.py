@@ -277,3 +277,45 @@ def test_adjoint_mesh256_dg1_configuration():
     st.close()
     print(f"mesh256_dg1 adjoint vs central differences: worst relative error {worst:.2e}")
     assert worst <= 1e-4, worst
+
+
+@pytest.mark.parametrize("n_s,n_a", [(6, 1), (3, 3)])
+def test_adjoint_per_element_pstar_matches_oracle_finite_differences(n_s, n_a):
+    """dJ/dP*_K against central differences of the FP64 oracle run with a
+    per-element P* field: the five elements with the largest gradient one by
+    one, and five random directions over all elements (relative step 1e-6)."""
+    nx, ny = 8, 7
+    case = W.small_case(nx, ny, n_s, seed=85 + n_s)
+    ne, nn, _ = W.sizes(nx, ny)
+    n = 20
+    p0 = case["params"]
+    rng = np.random.default_rng(11 + n_a)
+    H, A = case["H"], case["A"]
+    if n_a > 1:
+        H = np.concatenate([H, rng.uniform(-0.2, 0.2, (n_a - 1, ne))])
+        A = np.concatenate([A * 0.95, rng.uniform(-0.03, 0.03, (n_a - 1, ne))])
+    field = p0["Pstar"] * rng.uniform(0.7, 1.3, ne)
+    st = mevp.State(nx, ny, n_s, vertex_xy=case["xy"], n_adv=n_a, params=p0)
+    st.set_ice(H, A)
+    st.set_forcing(case["tau"])
+    st.set_strength_field(field)
+    st.set_velocity(case["vel0"])
+    st.set_stress(case["S0"])
+    st.begin_step()
+    J, gP, _ = st.adjoint_kinetic_energy(n, checkpoint_every=6)
+    st.close()
+    m, _ = oracle.lumped(nx, ny, case["xy"], n_s, n_a, p0, H)
+
+    def J_orc(pk):
+        v, _ = oracle.subcycles(nx, ny, case["xy"], n_s, n_a, p0, H, A, case["tau"],
+                                case["vel0"], case["S0"], n, Pstar_K=pk)
+        return 0.5 * float(np.sum(m * (v[0] ** 2 + v[1] ** 2)))
+
+    assert abs(J_orc(field) - J) <= 1e-10 * abs(J)
+    dirs = [np.eye(ne)[K] for K in np.argsort(-np.abs(gP))[:5]]
+    dirs += [rng.standard_normal(ne) for _ in range(5)]
+    for d in dirs:
+        e = 1e-6 * field.mean() / np.abs(d).max()
+        fd = (J_orc(field + e * d) - J_orc(field - e * d)) / (2 * e)
+        ad = float(gP @ d)
+        assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)

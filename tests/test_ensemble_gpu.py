@@ -181,3 +181,42 @@ def test_ensemble_of_every_member_kind(precision):
                 for m, ((va, Sa), (vb, Sb)) in enumerate(zip(got, ref)):
                     assert np.array_equal(va, vb), (shape, graphs, m, "velocity")
                     assert np.array_equal(Sa, Sb), (shape, graphs, m, "stress")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble8_matches_the_oracle(precision):
+    """The 8-member ensemble (uneven sides 16..64, DG1/DG2 members), captured
+    as CUDA graphs, after autotuning, against the FP64 oracle member by member:
+    the FP64 parity bar (rel L2 1e-11, rel max 1e-10), or the mixed path's
+    stated per-field errors (velocity 5e-6 / 3e-5, stress 5e-5 / 2e-4)."""
+    import oracle
+    tol = ({"velocity": (1e-11, 1e-10), "stress": (1e-11, 1e-10)} if precision == "fp64"
+           else {"velocity": (5e-6, 3e-5), "stress": (5e-5, 2e-4)})
+    cases = W.make_ensemble("ensemble8")
+    n_sub = cases[0]["n_sub"]
+    side = torch.cuda.Stream()  # a non-default stream: graph replay is on
+    with torch.cuda.stream(side):
+        states = []
+        for c in cases:
+            st = mevp.State(c["nx"], c["ny"], c["n_s"], vertex_xy=c["xy"], precision=precision,
+                            params=c["params"])
+            st.set_ice(c["H"], c["A"])
+            st.set_forcing(c["tau"])
+            st.set_velocity(c["vel0"])
+            st.set_stress(c["S0"])
+            states.append(st)
+        with mevp.Ensemble(states) as ens:
+            ens.begin_step()
+            ens.autotune(4)
+            ens.run_subcycles(n_sub)
+            got = results(states)
+        for st in states:
+            st.close()
+    assert len({c["n_s"] for c in cases}) == 2  # DG1 and DG2 members both present
+    for m, (c, (v, S)) in enumerate(zip(cases, got)):
+        vo, So = oracle.subcycles(c["nx"], c["ny"], c["xy"], c["n_s"], 1, c["params"], c["H"],
+                                  c["A"], c["tau"], c["vel0"], c["S0"], n_sub, openmp=True)
+        for name, x, ref in (("velocity", v, vo), ("stress", S, So)):
+            l2 = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+            linf = np.abs(x - ref).max() / np.abs(ref).max()
+            assert l2 <= tol[name][0] and linf <= tol[name][1], (m, name, l2, linf)

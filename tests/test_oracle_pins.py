@@ -779,3 +779,18 @@ def test_whole_subcycle_with_dg_ice_ocean_and_strength_field_matches_bruteforce(
     v0, _ = oracle.subcycles(nx, ny, xy, n_s, n_a, p, H, A, case["tau"], case["vel0"],
                              case["S0"], n_sub, Pstar_K=field)
     assert rel(vel, v0) > 1e-3
+
+
+def test_delta_at_gauss_points_matches_printed_constants():
+    """Delta of Listing 1 with the printed 5/4, 3/2, 1 at every Gauss point of a
+    constant strain, and Delta = Delta_min exactly where the strain vanishes."""
+    d = GOLD["delta"]
+    for n_s in (3, 6, 8):
+        E = np.zeros((3, n_s, 2))
+        e11, e12, e22 = 3e-7, -1.1e-7, -2e-7
+        E[:, 0, 0] = (e11, e12, e22)  # element 0 strained, element 1 rigid
+        out = oracle.delta(2, 1, n_s, P0, E)
+        D = math.sqrt(P0["DeltaMin"] ** 2 + d["sq"] * (e11 ** 2 + e22 ** 2)
+                      + d["mix"] * e11 * e22 + d["shear"] * e12 ** 2)
+        assert np.allclose(out[0], D, rtol=1e-14)
+        assert np.all(out[1] == P0["DeltaMin"])
