@@ -84,7 +84,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: b
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
     tmp = lib + f".tmp{os.getpid()}"
-    subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], check=True)
+    subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"],
+                   check=True)
     os.replace(tmp, lib)
     return lib
 

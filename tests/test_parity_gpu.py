@@ -289,6 +289,24 @@ def test_device_inputs_and_outputs():
     assert_close(vg, vo, "velocity")
 
 
+def test_large_host_input_scanned_in_parallel_rejects_any_non_finite_value():
+    """Host inputs above 16 MB are scanned by several host threads: a NaN or an
+    Inf anywhere (first, middle or last entry) is still refused, and the state
+    keeps its previous values."""
+    nx = ny = 600  # velocity: 2 x 1201^2 doubles = 23 MB
+    ne, nn, _ = W.sizes(nx, ny)
+    with mevp.State(nx, ny, 3, L=512e3) as st:
+        good = np.full((2, nn), 0.25)
+        st.set_velocity(good)
+        for pos, val in ((0, np.nan), (nn + nn // 2, np.inf), (2 * nn - 1, -np.inf)):
+            bad = good.copy().reshape(-1)
+            bad[pos] = val
+            with pytest.raises(mevp.MevpError) as e:
+                st.set_velocity(bad.reshape(2, nn))
+            assert e.value.code == -5
+        assert np.array_equal(st.velocity(), good)
+
+
 def test_error_statuses():
     case = W.small_case(4, 4, 3, seed=1)
     with mevp.State(4, 4, 3, vertex_xy=case["xy"]) as st:
