@@ -220,3 +220,42 @@ def test_ensemble8_matches_the_oracle(precision):
             l2 = np.linalg.norm(x - ref) / np.linalg.norm(ref)
             linf = np.abs(x - ref).max() / np.abs(ref).max()
             assert l2 <= tol[name][0] and linf <= tol[name][1], (m, name, l2, linf)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble64_matches_the_oracle_over_two_subcycles(precision):
+    """The full 64-member ensemble workload (sides 64..512, 4.1 M elements, DG1
+    and DG2) in the configuration the benchmark times -- batched persistent
+    launches, CUDA graphs, autotuned shape -- against the oracle member by
+    member after 2 subcycles (the workload's alpha = 300 amplifies any
+    rounding difference on its finer members over longer horizons)."""
+    import oracle
+    tol = ({"velocity": (1e-11, 1e-10), "stress": (1e-11, 1e-10)} if precision == "fp64"
+           else {"velocity": (5e-6, 3e-5), "stress": (5e-5, 2e-4)})
+    cases = W.make_ensemble("ensemble64")
+    n_sub = 2
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        states = []
+        for c in cases:
+            st = mevp.State(c["nx"], c["ny"], c["n_s"], vertex_xy=c["xy"], precision=precision,
+                            params=c["params"])
+            st.set_ice(c["H"], c["A"])
+            st.set_forcing(c["tau"])
+            st.set_velocity(c["vel0"])
+            st.set_stress(c["S0"])
+            states.append(st)
+        with mevp.Ensemble(states) as ens:
+            ens.begin_step()
+            ens.autotune(2)
+            ens.run_subcycles(n_sub)
+            got = results(states)
+        for st in states:
+            st.close()
+    for m, (c, (v, S)) in enumerate(zip(cases, got)):
+        vo, So = oracle.subcycles(c["nx"], c["ny"], c["xy"], c["n_s"], 1, c["params"], c["H"],
+                                  c["A"], c["tau"], c["vel0"], c["S0"], n_sub, openmp=True)
+        for name, x, ref in (("velocity", v, vo), ("stress", S, So)):
+            l2 = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+            linf = np.abs(x - ref).max() / np.abs(ref).max()
+            assert l2 <= tol[name][0] and linf <= tol[name][1], (m, name, l2, linf)
