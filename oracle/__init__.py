@@ -238,7 +238,7 @@ def lumped(nx, ny, xy, n_s, n_a, params, H):
 
 def velocity(nx, ny, params, F, vprev, vn, tau, vo, m, l):
     ne, nn = sizes(nx, ny)
-    out = np.zeros(2 * nn)
+    out = np.full(2 * nn, np.nan)  # every entry must be written by the stage
     prm = Params.from_dict(params)
     _check(_lib().orc_velocity(nx, ny, ctypes.byref(prm), _p(_c(F).reshape(-1)),
                                _p(_c(vprev).reshape(-1)), _p(_c(vn).reshape(-1)),

@@ -112,6 +112,18 @@ def run_all():
             ens.close()
             for s_ in sts:
                 s_.close()
+        for n_s, ocean in ((3, False), (8, True)):  # the no-alloc entry point
+            nx, ny = 17, 12
+            case = W.small_case(nx, ny, n_s, seed=360 + n_s)
+            xy = case["xy"].reshape(ny + 1, nx + 1, 2)
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+            vo = dev(W.smooth_velocity(nx, ny, 361, amp=0.1, L=case["L"])) if ocean else None
+            vel, S = dev(case["vel0"]), dev(case["S0"])
+            mevp.mevp_run_subcycles_noalloc(nx, ny, n_s, case["params"], dev(xy[0, :, 0]),
+                                            dev(xy[:, 0, 1]), dev(case["H"][0]),
+                                            dev(case["A"][0]), dev(case["tau"]), vo, vel, S, 5)
+            torch.cuda.synchronize()
+            out[f"noalloc_{n_s}_v"], out[f"noalloc_{n_s}_S"] = vel.cpu().numpy(), S.cpu().numpy()
     torch.cuda.synchronize()
     return out
 

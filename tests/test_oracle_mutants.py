@@ -64,6 +64,12 @@ MUTANTS = [
      "double Pst = p->Pstar;"),
     ("P* of the neighbouring element", "PstarK ? PstarK[K] :",
      "PstarK ? PstarK[(K + 1) % (M->nx * M->ny)] :"),
+    ("singular node: y component not written",
+     "if (det == 0.0) {\n      vout[j] = 0.0;\n      vout[nn + j] = 0.0;",
+     "if (det == 0.0) {\n      vout[j] = 0.0;\n      vout[j] = 0.0;"),
+    ("singular node: y written to another node",
+     "if (det == 0.0) {\n      vout[j] = 0.0;\n      vout[nn + j] = 0.0;",
+     "if (det == 0.0) {\n      vout[j] = 0.0;\n      vout[nn - j] = 0.0;"),
 ]
 
 

@@ -794,3 +794,34 @@ def test_delta_at_gauss_points_matches_printed_constants():
                       + d["mix"] * e11 * e22 + d["shear"] * e12 ** 2)
         assert np.allclose(out[0], D, rtol=1e-14)
         assert np.all(out[1] == P0["DeltaMin"])
+
+
+def test_velocity_node_without_mass_or_drag_stays_at_rest():
+    """A node with no ice (m = 0) moving with the ocean (c = 0): the 2x2 system of
+    the velocity update is singular (a = b = 0) and the reading sets v = 0 there;
+    where the ice moves relative to the ocean, c > 0 and (with m = 0) the update
+    is the pure drag balance c (v - v_o) = F + l tau, v = v_o + (F + l tau) / c."""
+    nx = ny = 3
+    ne, nn, _ = W.sizes(nx, ny)
+    rng = np.random.default_rng(17)
+    p = dict(P0)
+    m = np.zeros(nn)
+    l = rng.uniform(1e5, 2e5, nn)
+    vo = rng.uniform(-0.2, 0.2, (2, nn))
+    vprev = vo.copy()
+    moving = rng.random(nn) < 0.5
+    vprev[:, moving] += rng.uniform(-0.1, 0.1, (2, int(moving.sum())))
+    F = rng.uniform(-50, 50, (2, nn))
+    tau = rng.uniform(-0.3, 0.3, (2, nn))
+    out = oracle.velocity(nx, ny, p, F, vprev, np.zeros((2, nn)), tau, vo, m, l)
+    nw = 2 * nx + 1
+    ix, iy = np.arange(nn) % nw, np.arange(nn) // nw
+    interior = (ix > 0) & (iy > 0) & (ix < nw - 1) & (iy < nw - 1)
+    rest = interior & ~moving
+    assert rest.any() and (interior & moving).any()
+    assert np.all(out[:, rest] == 0.0)
+    mv = interior & moving
+    c = l[mv] * p["Cw"] * p["rho_water"] * np.hypot(*(vo[:, mv] - vprev[:, mv]))
+    expect = vo[:, mv] + (F[:, mv] + l[mv] * tau[:, mv]) / c
+    assert np.allclose(out[:, mv], expect, rtol=1e-13)
+    assert np.all(out[:, ~interior] == 0.0)
