@@ -243,10 +243,18 @@ def run_reference(a):
     ne = case["nx"] * case["ny"]
     args = (case["nx"], case["ny"], case["xy"], case["n_s"], 1, case["params"], case["H"],
             case["A"], case["tau"], case["vel0"], case["S0"])
+    # a call of the oracle has a fixed cost (element geometry and the lumped
+    # mass, serial) besides its subcycles: size each step from the marginal
+    # cost of a subcycle, about 5 s of work per step
     t0 = time.perf_counter()
     oracle.subcycles(*args, 1, openmp=True)
     t1 = time.perf_counter() - t0
-    k_sub = int(max(1, min(case["n_sub"], 4.0 / max(t1, 1e-6))))  # ~4 s per step
+    t0 = time.perf_counter()
+    oracle.subcycles(*args, 3, openmp=True)
+    t3 = time.perf_counter() - t0
+    per_sub = max((t3 - t1) / 2, 1e-6)
+    fixed = max(t1 - per_sub, 0.0)
+    k_sub = int(max(1, min(case["n_sub"], (5.0 - fixed) / per_sub)))
     for _ in range(a.warmup):
         oracle.subcycles(*args, 1, openmp=True)
     times = []
@@ -582,9 +590,10 @@ def run_ours(a):
         return _run_ours(a, torch, dist, ws, rank)
 
 
-def run_ensemble(a, torch, dist, ws, rank):
+def run_ensemble(a, torch, dist, ws, rank, emit=True):
     """Ensemble workload: all members advanced together (one persistent
-    launch per subcycle in the mixed precision), tile shape autotuned."""
+    launch per subcycle in the mixed precision), tile shape autotuned.
+    Prints the line (emit) and returns it."""
     from paper_2402_00466_gb300 import mevp
 
     dev = torch.cuda.current_device()
@@ -677,9 +686,9 @@ def run_ensemble(a, torch, dist, ws, rank):
                                             1 + len({c["n_s"] for c in members}))),
         "clocks": clk, "cpu_baseline": None, "e2e": None,
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_advection(a, torch, dist, ws, rank):
@@ -764,7 +773,7 @@ def run_advection(a, torch, dist, ws, rank):
     return 0
 
 
-def run_adjoint(a, torch, dist, ws, rank):
+def run_adjoint(a, torch, dist, ws, rank, emit=True):
     """Adjoint workload: `steps` gradient evaluations (dJ/dP*, dJ/dtau of the
     kinetic energy after n_sub subcycles, checkpoints every k), device
     outputs, CUDA events on the launching stream."""
@@ -825,6 +834,7 @@ def run_adjoint(a, torch, dist, ws, rank):
     ach = per_es * ne * n_sub * a.steps / (total_ms / 1e3) / 1e12
     per_store, _ = work(n_sub)
     ach_store = per_store * ne * n_sub * a.steps / (store_ms / 1e3) / 1e12
+    line = None
     if rank == 0:
         line = {
             "metric": "adjoint of the mEVP subcycle: objective element-subcycles/s",
@@ -853,17 +863,19 @@ def run_adjoint(a, torch, dist, ws, rank):
                 "achieved_TFLOPs": ach_store, "frac": ach_store / fp64_peak_tflops(clk),
                 "flops_per_element_subcycle": per_store}},
         }
-        print(json.dumps(line), flush=True)
-    if ws > 1:
+        if emit:
+            print(json.dumps(line), flush=True)
+    if ws > 1 and emit:
         dist.destroy_process_group()
-    return 0
+    return line if not emit else 0
 
 
 def _run_ours(a, torch, dist, ws, rank):
     from paper_2402_00466_gb300 import mevp
 
     if a.workload in W.ENSEMBLES:
-        return run_ensemble(a, torch, dist, ws, rank)
+        run_ensemble(a, torch, dist, ws, rank)
+        return 0
     if W.CONFIGS[a.workload]["n_sub"] == 0:
         return run_advection(a, torch, dist, ws, rank)
     if "adjoint_every" in W.CONFIGS[a.workload]:
@@ -913,6 +925,29 @@ def _run_ours(a, torch, dist, ws, rank):
         st.close()
         res[prec] = r
 
+    # the other rows' workloads, a few steps each, so that the benchmark line
+    # carries their numbers too: batched ensembles (mixed and FP64) and the
+    # adjoint's gradient
+    extras = None
+    if not a.no_extras:
+        extras = {}
+        keep = ("value", "unit", "ms_per_step", "steps", "roofline", "config", "gpu_launches",
+                "clocks")
+        for prec in ("mixed", "fp64"):
+            b = argparse.Namespace(**vars(a))
+            b.workload, b.precision, b.steps, b.warmup = "ensemble64", prec, 3, 3
+            line = run_ensemble(b, torch, dist, ws, rank, emit=False)
+            extras[f"ensemble64_{prec}"] = dict(
+                {k: line[k] for k in keep},
+                speedup_vs_sequential=line["speedup_vs_sequential"])
+        b = argparse.Namespace(**vars(a))
+        b.workload, b.precision, b.steps, b.warmup = "adjoint256_dg1", "fp64", 5, 3
+        line = run_adjoint(b, torch, dist, ws, rank, emit=False)
+        if line is not None:
+            extras["adjoint256_dg1"] = dict({k: line[k] for k in keep},
+                                            gradients_per_s=line["gradients_per_s"],
+                                            variants=line["variants"])
+
     head = res[a.precision]
     cpu = None
     field_errors = None
@@ -940,6 +975,7 @@ def _run_ours(a, torch, dist, ws, rank):
             "kernel_split": head["kernel_split"],
             "arms": {p: r for p, r in res.items() if p != a.precision},
             "field_errors": field_errors,
+            "extra_workloads": extras,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -960,6 +996,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="time only --precision, not the other precision's arm")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ensemble and adjoint workloads of the default line")
     a = ap.parse_args()
     if a.warmup < 3 and a.impl == "ours":
         ap.error("--warmup must be >= 3")
