@@ -247,7 +247,7 @@ enum {
    * give bitwise identical results. */
   MEVP_OPT_FUSED = 1,
   /* 1 (default) = mevp_run_subcycles replays runs of 4 or more subcycles as
-   * CUDA graphs (chunks of up to 64, captured on the state's stream at first
+   * CUDA graphs (chunks of up to 512, captured on the state's stream at first
    * use and kept until the parameters, the ocean forcing or an option
    * change); 0 = one launch at a time.  States on the legacy default stream
    * (cuda_stream = NULL) always launch one at a time. */

@@ -59,9 +59,10 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Subcycle runs of at least kMinGraphChunk are replayed as CUDA graphs of up
-// to kMaxGraphChunk subcycles.
+// to kMaxGraphChunk subcycles: an outer step of up to 512 subcycles is one
+// graph launch.
 constexpr int kMinGraphChunk = 4;
-constexpr int kMaxGraphChunk = 64;
+constexpr int kMaxGraphChunk = 512;
 
 struct Layout {
   size_t xline, yline, xy, nxy, lines, pstar, flags, adv1, adv2, Pg, Pg32, map32ab, map32c, iso32, mfac, isoJ, mfac32, vel0, vel1, S, S32a, S32b, H, A, tau, vo, Pe, nodec, mass, fbuf, fbuf32, diag,

@@ -56,8 +56,9 @@ struct mevp_ensemble {
 
 namespace {
 
+// runs of 4 to 512 subcycles are one graph launch each
 constexpr int kMinGraphChunk = 4;
-constexpr int kMaxGraphChunk = 64;
+constexpr int kMaxGraphChunk = 512;
 
 int efail(int code, const char *fmt, ...) {
   char buf[512];
