@@ -116,9 +116,13 @@ def test_translation_of_polynomials_is_exact(n_a, deg, geometry):
         return sum(ci * t for ci, t in zip(c[:k], terms[:k]))
     dt, n = 120.0, 7
     H = coeffs_of(H0, nx, ny, xy, n_a)
-    H1, _ = oracle.advect(nx, ny, xy, n_a, vel, dt, n, H, H)
+    A0 = lambda x, y: 0.9 - 0.5 * H0(y, x)  # noqa: E731  (a second field, moved alike)
+    A = coeffs_of(A0, nx, ny, xy, n_a)
+    H1, A1 = oracle.advect(nx, ny, xy, n_a, vel, dt, n, H, A)
     exact = coeffs_of(lambda x, y: H0(x - U[0] * n * dt, y - U[1] * n * dt), nx, ny, xy, n_a)
+    exactA = coeffs_of(lambda x, y: A0(x - U[0] * n * dt, y - U[1] * n * dt), nx, ny, xy, n_a)
     assert np.abs(H1 - exact).max() <= 1e-12
+    assert np.abs(A1 - exactA).max() <= 1e-12
 
 
 @pytest.mark.parametrize("n_a", [1, 3, 6])
@@ -130,11 +134,13 @@ def test_mass_conserved_with_no_boundary_flow(n_a):
     vel = W.smooth_velocity(nx, ny, 3, amp=0.4, L=L)
     rng = np.random.default_rng(3)
     H = rng.uniform(0.3, 2.0, (n_a, nx * ny))
+    A = rng.uniform(0.5, 1.0, (n_a, nx * ny))
     bf = BF.Advection(nx, ny, xy, n_a)
-    m0 = bf.integral(H)
-    H1, _ = oracle.advect(nx, ny, xy, n_a, vel, 120.0, 20, H, H)
+    m0, a0 = bf.integral(H), bf.integral(A)
+    H1, A1 = oracle.advect(nx, ny, xy, n_a, vel, 120.0, 20, H, A)
     assert abs(bf.integral(H1) - m0) <= 1e-13 * abs(m0)
-    assert np.abs(H1 - H).max() > 1e-6  # the ice did move
+    assert abs(bf.integral(A1) - a0) <= 1e-13 * abs(a0)
+    assert np.abs(H1 - H).max() > 1e-6 and np.abs(A1 - A).max() > 1e-6  # the ice did move
 
 
 @pytest.mark.parametrize("n_a,order", [(1, 1), (3, 2), (6, 3)])
@@ -156,14 +162,17 @@ def test_runge_kutta_step_is_taylor_polynomial(n_a, order):
     dt = 600.0
     rng = np.random.default_rng(19)
     H = rng.uniform(0.5, 1.5, (n_a, ne))
+    A = rng.uniform(0.6, 1.0, (n_a, ne))
     step = np.eye(N)
     term = np.eye(N)
     for k in range(1, order + 1):
         term = term @ (dt * Lm) / k
         step = step + term
     ref = (step @ H.ravel()).reshape(n_a, ne)
-    H1, _ = oracle.advect(nx, ny, xy, n_a, vel, dt, 1, H, H)
+    refA = (step @ A.ravel()).reshape(n_a, ne)
+    H1, A1 = oracle.advect(nx, ny, xy, n_a, vel, dt, 1, H, A)
     assert np.abs(H1 - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(A1 - refA).max() <= 1e-12 * np.abs(refA).max()
 
 
 def test_first_order_upwind_closed_form():
@@ -174,12 +183,36 @@ def test_first_order_upwind_closed_form():
     ne, nn = oracle.sizes(nx, ny)
     vel = np.zeros((2, nn)); vel[0] = 0.5
     H = np.random.default_rng(0).uniform(0.5, 1.5, (1, ne))
-    H1, _ = oracle.advect(nx, ny, xy, 1, vel, 120.0, 1, H, H)
+    A = np.random.default_rng(1).uniform(0.5, 1.0, (1, ne))
+    H1, A1 = oracle.advect(nx, ny, xy, 1, vel, 120.0, 1, H, A)
     c = 0.5 * 120.0 / 1e3
-    g = H.reshape(ny, nx)
-    exp = g.copy()
-    exp[:, 1:] = g[:, 1:] - c * (g[:, 1:] - g[:, :-1])
-    assert np.array_equal(H1.reshape(ny, nx), exp) or np.abs(H1.reshape(ny, nx) - exp).max() < 1e-15
+    for F, F1 in ((H, H1), (A, A1)):
+        g = F.reshape(ny, nx)
+        exp = g.copy()
+        exp[:, 1:] = g[:, 1:] - c * (g[:, 1:] - g[:, :-1])
+        assert np.abs(F1.reshape(ny, nx) - exp).max() < 1e-15
+
+
+def test_first_order_upwind_on_a_one_element_wide_column():
+    """A mesh one element wide (nx = 1) with a uniform y velocity: the same
+    first-order upwind scheme along the column."""
+    nx, ny = 1, 6
+    xy = W.uniform_vertices(nx, ny, 1e3, 6e3)
+    ne, nn = oracle.sizes(nx, ny)
+    vel = np.zeros((2, nn)); vel[1] = -0.4  # flowing south: the upwind side is north
+    H = np.random.default_rng(2).uniform(0.5, 1.5, (1, ne))
+    H1, A1 = oracle.advect(nx, ny, xy, 1, vel, 120.0, 1, H, 2.0 * H)
+    c = 0.4 * 120.0 / 1e3
+    exp = H[0].copy()
+    exp[:-1] = H[0, :-1] - c * (H[0, :-1] - H[0, 1:])
+    assert np.abs(H1[0] - exp).max() < 1e-15 and np.abs(A1[0] - 2.0 * exp).max() < 1e-15
+    xy2 = W.uniform_vertices(ny, nx, 6e3, 1e3)  # and a row one element high (ny = 1)
+    ne2, nn2 = oracle.sizes(ny, nx)
+    vel2 = np.zeros((2, nn2)); vel2[0] = 0.4
+    H2, _ = oracle.advect(ny, nx, xy2, 1, vel2, 120.0, 1, H, H)
+    exp2 = H[0].copy()
+    exp2[1:] = H[0, 1:] - c * (H[0, 1:] - H[0, :-1])
+    assert np.abs(H2[0] - exp2).max() < 1e-15
 
 
 def test_advect_rejects_bad_arguments():

@@ -98,6 +98,18 @@ ADVECTION_MUTANTS = [
     ("Euler step sign", "H1[k] = H[k] + dt * LH[k];", "H1[k] = H[k] - dt * LH[k];"),
     ("isoparametric transport Jacobian transposed", "J[2 * c + 1] += xn[c] * deta[j];",
      "J[2 * c + 1] += xn[c] * dxi[j];"),
+    ('Euler step of A sign', 'A1[k] = A[k] + dt * LA[k]; }',
+     'A1[k] = A[k] - dt * LA[k]; }'),
+    ('Heun weights of A', 'A[k] = 0.5 * A[k] + 0.5 * (A1[k] + dt * LA[k]);',
+     'A[k] = 0.25 * A[k] + 0.5 * (A1[k] + dt * LA[k]);'),
+    ('RK3 second stage of A', 'A2[k] = 0.75 * A[k] + 0.25 * (A1[k] + dt * LA[k]);',
+     'A2[k] = 0.75 * A[k] + 0.25 * (A1[k] - dt * LA[k]);'),
+    ('RK3 last stage of A', 'A[k] = A[k] / 3.0 + 2.0 * (A2[k] + dt * LA[k]) / 3.0;',
+     'A[k] = A[k] / 3.0 + 2.0 * (A2[k] - dt * LA[k]) / 3.0;'),
+    ('forward Euler leaves A unchanged', 'memcpy(A, A1, sizeof(double) * n);',
+     'memcpy(A, A1, sizeof(double) / n);'),
+    ('one-element-wide meshes refused', 'if (nx < 1 || ny < 1 || !xy || !vel || !H || !A || n_steps < 0)',
+     'if (nx <= 1 || ny < 1 || !xy || !vel || !H || !A || n_steps < 0)'),
 ]
 
 
