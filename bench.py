@@ -37,10 +37,12 @@ UNIT = "element-subcycles/s"
 
 # Algorithmic work per element and subcycle of the element kernel, counted
 # from its operator sparsity (FMA = 2 flops, mul/add = 1, rsqrt = 1; zero
-# entries skipped, +-1 entries as adds).  DG2: projected derivatives 268,
-# Gauss evaluation 132, rheology 99, projection 240, update 62, element
-# forces 254.  DG1: 153, 36, 44, 63, 32, 146.
-ELEM_FLOPS = {3: 474, 6: 1055}
+# entries skipped, +-1 entries as adds).  The strain and force operators are
+# sum-factorised (two 1-D passes).  DG2: projected derivatives 204, Gauss
+# evaluation 132, rheology 99, projection 240, update 62, element forces 182.
+# DG1: 145, 36, 44, 63, 32, 130.  (Applied directly, without the
+# factorisation, the two operators cost 268 and 254 (DG2), 153 and 146 (DG1).)
+ELEM_FLOPS = {3: 450, 6: 919}
 # The same count for the general-quad element kernel k_element_gen (bilinear
 # map per element, Gauss-point strain, stress and forces with det J
 # cancelled; the L D L^T factor of the local mass matrix is read from the
@@ -80,9 +82,8 @@ HBM_BYTES = {("fp64", 6): 608, ("fp64", 3): 464}
 # is the launch's cold-cache traffic); keyed by (workload, precision, kernel)
 # and valid while that kernel is unchanged.  Summaries: profiles/.
 NCU_TRAFFIC = {
-    ("mesh256_dg2", "fp64", "k_element_f64<6>"): 14248448 + 768,
-    ("mesh1024_dg2", "fp64", "k_element_f64<6>"): 234245632 + 248352768,
-    ("mesh1024_dg2", "mixed", "k_subcycle_mix<6,32,8>"): 214122496 + 105039360,
+    ("mesh1024_dg2", "fp64", "k_element_f64<6>"): 234397440 + 248332032,
+    ("mesh1024_dg2", "mixed", "k_subcycle_mix<6,32,8>"): 214099456 + 105171968,
     ("mesh256_dg2_iso", "fp64", "k_element_iso<6>"): 44171776 + 55296000,
 }
 

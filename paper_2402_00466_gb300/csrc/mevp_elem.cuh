@@ -47,21 +47,51 @@ __device__ __forceinline__ T cmul_acc(double c, T x, T acc) {
   return c == 1.0 ? acc + x : (c == -1.0 ? acc - x : fma((T)c, x, acc));
 }
 
-// Projected reference derivatives of the 9 nodal values w:
-// Wxi[s] = sum_j dxi(s,j) w_j, Weta[s] = sum_j deta(s,j) w_j.
+// Projected reference derivatives of the 9 nodal values w (j = a + 3b):
+// Wxi[s] = sum_j dxi(s,j) w_j, Weta[s] = sum_j deta(s,j) w_j.  Both operators
+// are products of 1-D moments, dxi(s,j) = idr(kx,a) ib(ky,b) / mass_s with
+// (kx, ky) the degrees of DG function s, so they are applied in two 1-D
+// passes (sum factorisation): the derivative moments along the
+// differentiated direction, then the value moments along the other one.
 template <int NS, typename T>
 __device__ __forceinline__ void ref_derivs(const T w[9], T Wxi[NS], T Weta[NS]) {
+  // dx[k][b] = sum_a idr(k,a) w(a,b),  de[k][a] = sum_b idr(k,b) w(a,b);
+  // idr(2, .) = 0 (the derivative of a Q2 function is linear)
+  T dx[2][3], de[2][3];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T x = T(-0.0), y = T(-0.0);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const double c = idr(k, t);
+        if (c != 0.0) {
+          x = cmul_acc(c, w[t + 3 * i], x);
+          y = cmul_acc(c, w[i + 3 * t], y);
+        }
+      }
+      dx[k][i] = x;
+      de[k][i] = y;
+    }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    T a = T(-0.0), b = T(-0.0);
+    constexpr int K2 = 2;
+    const int kx = dgx(s), ky = dgy(s);
+    T x = T(-0.0), y = T(-0.0);
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      const double cx = dxi(s, j), ce = deta(s, j);
-      if (cx != 0.0) a = cmul_acc(cx, w[j], a);
-      if (ce != 0.0) b = cmul_acc(ce, w[j], b);
+    for (int t = 0; t < 3; ++t) {
+      if (kx < K2) {
+        const double c = ib(ky, t) / dgmass(s);
+        if (c != 0.0) x = cmul_acc(c, dx[kx < K2 ? kx : 0][t], x);
+      }
+      if (ky < K2) {
+        const double c = ib(kx, t) / dgmass(s);
+        if (c != 0.0) y = cmul_acc(c, de[ky < K2 ? ky : 0][t], y);
+      }
     }
-    Wxi[s] = a;
-    Weta[s] = b;
+    Wxi[s] = x;
+    Weta[s] = y;
   }
 }
 
@@ -170,7 +200,11 @@ __device__ __forceinline__ void relax_stress(T S11[NS], T S12[NS], T S22[NS], co
 }
 
 // Element forces f_j = -int sigma : grad phi_j on a rectangle hx x hy
-// (fx[j], fy[j] for the 9 local Q2 nodes).
+// (fx[j], fy[j] for the 9 local Q2 nodes j = a + 3b).  The moments
+// gxi(j,s) = idr(kx,a) ib(ky,b) and geta(j,s) = ib(kx,a) idr(ky,b) are
+// products of 1-D moments, so the sums over the DG functions are taken in
+// two passes (sum factorisation): along the undifferentiated direction
+// first, then the derivative moments along the differentiated one.
 template <int NS, typename T>
 __device__ __forceinline__ void element_forces_t(const T S11[NS], const T S12[NS],
                                                  const T S22[NS], T hx, T hy, T fx[9], T fy[9]) {
@@ -182,24 +216,57 @@ __device__ __forceinline__ void element_forces_t(const T S11[NS], const T S12[NS
     a12y[s] = -hy * S12[s];
     a22[s] = -hx * S22[s];
   }
+  // X*[k][b] = sum over the DG functions of degree k in xi of ib(ky_s, b) a*_s
+  // (xi-derivative terms); Y*[k][a] = sum over degree k in eta of
+  // ib(kx_s, a) a*_s (eta-derivative terms); k < 2 (idr(2, .) = 0)
+  T X11[2][3], X12[2][3], Y12[2][3], Y22[2][3];
 #pragma unroll
-  for (int j = 0; j < 9; ++j) {
-    T x = T(-0.0), y = T(-0.0);
+  for (int k = 0; k < 2; ++k)
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const double gx = gxi(j, s), ge = geta(j, s);
-      if (gx != 0.0) {
-        x = cmul_acc(gx, a11[s], x);
-        y = cmul_acc(gx, a12y[s], y);
+    for (int i = 0; i < 3; ++i) {
+      T p = T(-0.0), q = T(-0.0), r = T(-0.0), u = T(-0.0);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (dgx(s) == k) {
+          const double c = ib(dgy(s), i);
+          if (c != 0.0) {
+            p = cmul_acc(c, a11[s], p);
+            q = cmul_acc(c, a12y[s], q);
+          }
+        }
+        if (dgy(s) == k) {
+          const double c = ib(dgx(s), i);
+          if (c != 0.0) {
+            r = cmul_acc(c, a12x[s], r);
+            u = cmul_acc(c, a22[s], u);
+          }
+        }
       }
-      if (ge != 0.0) {
-        x = cmul_acc(ge, a12x[s], x);
-        y = cmul_acc(ge, a22[s], y);
-      }
+      X11[k][i] = p;
+      X12[k][i] = q;
+      Y12[k][i] = r;
+      Y22[k][i] = u;
     }
-    fx[j] = x;
-    fy[j] = y;
-  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T x = T(-0.0), y = T(-0.0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double cx = idr(k, a), ce = idr(k, b);
+        if (cx != 0.0) {
+          x = cmul_acc(cx, X11[k][b], x);
+          y = cmul_acc(cx, X12[k][b], y);
+        }
+        if (ce != 0.0) {
+          x = cmul_acc(ce, Y12[k][a], x);
+          y = cmul_acc(ce, Y22[k][a], y);
+        }
+      }
+      fx[a + 3 * b] = x;
+      fy[a + 3 * b] = y;
+    }
 }
 
 }  // namespace mevp
