@@ -28,7 +28,9 @@
  *   - Handles are created and freed by the library; destroying NULL is a
  *     no-op.  Input pointers are borrowed only for the duration of the call.
  *   - "on_device" = 0: the pointer is host memory; the data are copied on the
- *     state's stream and the call returns after the copy completed.
+ *     state's stream into a staging buffer and checked there for non-finite
+ *     values (MEVP_ERR_NAN, the state unchanged), and the call returns once
+ *     the host buffer has been read; the move into the state is enqueued.
  *     "on_device" = 1: the pointer is device memory of the state's device; the
  *     copy is enqueued on the state's stream (the caller keeps the buffer
  *     alive and unmodified until the stream reaches it).
@@ -187,12 +189,13 @@ MEVP_API int mevp_set_forcing(mevp_state *state, const double *tau, const double
 /* Velocity [2][N_n]: the CG2 velocity v of Eq. 2 and the iterate v^{p-1}
  * of the mEVP iteration (Eq. 3).  Boundary entries are stored as given but
  * every subcycle writes 0 there (Dirichlet).  Does not change v^n (that is
- * mevp_begin_step's).  MEVP_ERR_ARG for a non-finite host value. */
+ * mevp_begin_step's).  MEVP_ERR_NAN for a non-finite host value (the state
+ * keeps its previous velocity). */
 MEVP_API int mevp_set_velocity(mevp_state *state, const double *uv, int on_device);
 
 /* Stress [3][n_stress][N_e]: the DG coefficients of sigma, the iterate
- * sigma^{p-1} of Eq. 3 (Listing 1's S11, S12, S22).  MEVP_ERR_ARG for a
- * non-finite host value. */
+ * sigma^{p-1} of Eq. 3 (Listing 1's S11, S12, S22).  MEVP_ERR_NAN for a
+ * non-finite host value (the state keeps its previous stress). */
 MEVP_API int mevp_set_stress(mevp_state *state, const double *S, int on_device);
 
 /* Advect H and A by n_steps >= 0 steps of length params.dt with the

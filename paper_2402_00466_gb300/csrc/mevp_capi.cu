@@ -14,8 +14,6 @@
 #include <mutex>
 #include <new>
 #include <string>
-#include <thread>
-#include <vector>
 
 #include "mevp_internal.cuh"
 
@@ -125,35 +123,15 @@ Layout make_layout(const mevp_mesh *m, int ns, int na, int prec) {
   return L;
 }
 
-// True when no exponent field of p[a, b) is all ones (no Inf, no NaN).
-// Branch-free, so that the compiler vectorises the loop.
-bool finite_range(const double *p, size_t a, size_t b) {
-  uint64_t bad = 0;
-  for (size_t i = a; i < b; ++i) {
-    uint64_t bits;
-    std::memcpy(&bits, p + i, sizeof bits);
-    bad |= (uint64_t)(((bits >> 52) & 0x7ffu) == 0x7ffu);
+// Sets *bad when any of x[0, n) is not finite (exponent field all ones).
+__global__ void k_finite_check(const double *__restrict__ x, size_t n, int *bad) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  bool found = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x[i]);
+    found |= ((bits >> 52) & 0x7ffull) == 0x7ffull;
   }
-  return bad == 0;
-}
-
-// Host inputs are scanned before they are copied, so that a rejected call
-// leaves the state unchanged.  Large inputs (hundreds of MB per outer step on
-// big meshes) are split over several host threads: one thread reads far
-// below the host's memory bandwidth.
-bool finite_all(const double *p, size_t n) {
-  constexpr size_t kPerThread = size_t(1) << 21;  // 16 MB of doubles
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const size_t nt = std::min<size_t>(std::min<size_t>(hw, 16), (n + kPerThread - 1) / kPerThread);
-  if (nt <= 1) return finite_range(p, 0, n);
-  std::vector<char> ok(nt, 0);
-  std::vector<std::thread> pool;
-  pool.reserve(nt - 1);
-  for (size_t t = 1; t < nt; ++t)
-    pool.emplace_back([&, t] { ok[t] = finite_range(p, n * t / nt, n * (t + 1) / nt); });
-  ok[0] = finite_range(p, 0, n / nt);
-  for (auto &th : pool) th.join();
-  return std::all_of(ok.begin(), ok.end(), [](char c) { return c != 0; });
+  if (found) *bad = 1;  // every writer stores the same value
 }
 
 }  // namespace
@@ -172,17 +150,34 @@ namespace {
 
 int check_state(const mevp_state *s) { return mevp::api_check_state(s); }
 
-// Copy n doubles into device buffer dst on the state's stream.
+// Copy n doubles into device buffer dst on the state's stream.  A host input
+// is copied into the diagnostic buffer first (it holds max(3 n_stress N_e,
+// 2 N_n) doubles, as much as the largest input), checked there for
+// non-finite values by a kernel, and moved into dst only when it passed, so
+// that a refused input leaves the state unchanged.  The call returns once
+// the host buffer has been read and checked.
 int copy_in(mevp_state *s, double *dst, const double *src, size_t n, int on_device,
             const char *what) {
   if (!src) return fail(MEVP_ERR_ARG, "%s: NULL pointer", what);
-  if (!on_device && !finite_all(src, n))
-    return fail(MEVP_ERR_NAN, "%s: non-finite value in host input", what);
-  MEVP_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            s->stream),
+  if (on_device) {
+    MEVP_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream),
+              what);
+    return MEVP_OK;
+  }
+  double *stage = s->d.diag;
+  int *flag = s->d.flags + 3;
+  MEVP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s->stream), what);
+  MEVP_CUDA(cudaMemcpyAsync(stage, src, n * sizeof(double), cudaMemcpyHostToDevice, s->stream),
             what);
-  if (!on_device) MEVP_CUDA(cudaStreamSynchronize(s->stream), what);
+  const size_t blocks = std::min<size_t>((n + 255) / 256, (size_t)s->d.nsm * 8);
+  k_finite_check<<<(unsigned)std::max<size_t>(blocks, 1), 256, 0, s->stream>>>(stage, n, flag);
+  MEVP_CUDA(cudaGetLastError(), what);
+  int bad = 0;
+  MEVP_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream), what);
+  MEVP_CUDA(cudaStreamSynchronize(s->stream), what);
+  if (bad) return fail(MEVP_ERR_NAN, "%s: non-finite value in host input", what);
+  MEVP_CUDA(cudaMemcpyAsync(dst, stage, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream),
+            what);
   return MEVP_OK;
 }
 
